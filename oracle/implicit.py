@@ -1,0 +1,370 @@
+"""Implicit machinery of Sec. 3.2 and Sec. 4.2.2: the Jacobian-free product,
+restarted right-preconditioned GMRES, the block relaxed Jacobi preconditioner
+BRJ(J), Newton's method and SDIRK time stepping (App. A).
+
+Norms are the Euclidean norm of the full coefficient vector.
+"""
+from dataclasses import dataclass, field
+import numpy as np
+from . import physics as phy
+
+EPS_HAT = 2.0 ** -52          # machine epsilon of IEEE double (2.22e-16)
+
+
+def norm(x):
+    return float(np.sqrt(np.sum(x * x)))
+
+
+# ------------------------------------------------------------------- JFNK (Eq. 24-25)
+
+def jfnk_eps(u, v):
+    """epsilon = sqrt(eps_hat) ||u|| / ||v||  (Eq. eps-JF scaled by ||v||, so
+    that it equals the paper's value for unit-norm v; sqrt(eps_hat)/||v|| when
+    u = 0)."""
+    nu, nv = norm(u), norm(v)
+    return np.sqrt(EPS_HAT) * (nu if nu > 0 else 1.0) / nv
+
+
+def jvp(dg, u, r_u, t, v, alpha, beta):
+    """alpha v + beta (R(u + eps v) - R(u)) / eps  (Eq. Jacobian-free-matrix).
+    With alpha = 1, beta = -dt a_mm this is dN/du . v of Eq. Newton-Iteration."""
+    nv = norm(v)
+    if nv == 0.0:
+        return alpha * v
+    eps = jfnk_eps(u, v)
+    return alpha * v + beta * (dg.residual(u + eps * v, t) - r_u) / eps
+
+
+# ------------------------------------------------------------------- GMRES
+
+@dataclass
+class GmresConfig:
+    restart: int = 30
+    rtol: float = 5e-2
+    max_cycles: int = 10
+    ortho: str = "cgs2"       # or "mgs"
+
+
+@dataclass
+class GmresStats:
+    iters: int = 0
+    cycles: int = 0
+    converged: bool = False
+    res: float = 0.0
+    res0: float = 0.0
+
+
+def gmres(apply_A, b, precond=None, cfg=None):
+    """Restarted GMRES (Saad & Schultz) with right preconditioning
+    (Eq. preconditioning): solves A x = b from x0 = 0, stopping when the
+    residual estimate drops below rtol * ||b||; Arnoldi by classical
+    Gram-Schmidt applied twice (cgs2) or modified Gram-Schmidt (mgs); the
+    least-squares problem is reduced by Givens rotations."""
+    cfg = cfg if cfg is not None else GmresConfig()
+    Pinv = precond if precond is not None else (lambda z: z)
+    x = np.zeros_like(b)
+    st = GmresStats()
+    bn = norm(b)
+    st.res0 = bn
+    if bn == 0.0:
+        st.converged = True
+        return x, st
+    m = cfg.restart
+    for cyc in range(cfg.max_cycles):
+        r = b if cyc == 0 else b - apply_A(x)
+        beta = norm(r)
+        st.res = beta
+        if beta <= cfg.rtol * bn:
+            st.converged = True
+            break
+        st.cycles += 1
+        V = [r / beta]
+        H = np.zeros((m + 1, m))
+        cs = np.zeros(m)
+        sn = np.zeros(m)
+        gvec = np.zeros(m + 1)
+        gvec[0] = beta
+        k_used = 0
+        for k in range(m):
+            w = apply_A(Pinv(V[k]))
+            st.iters += 1
+            if cfg.ortho == "cgs2":
+                Vm = np.stack([v.ravel() for v in V])
+                h = Vm @ w.ravel()
+                w = w - (Vm.T @ h).reshape(w.shape)
+                h2 = Vm @ w.ravel()
+                w = w - (Vm.T @ h2).reshape(w.shape)
+                h = h + h2
+            else:
+                h = np.zeros(k + 1)
+                for i in range(k + 1):
+                    h[i] = np.sum(V[i] * w)
+                    w = w - h[i] * V[i]
+            hn = norm(w)
+            H[:k + 1, k] = h
+            H[k + 1, k] = hn
+            V.append(w / hn if hn > 0 else w)
+            for i in range(k):
+                t0 = cs[i] * H[i, k] + sn[i] * H[i + 1, k]
+                H[i + 1, k] = -sn[i] * H[i, k] + cs[i] * H[i + 1, k]
+                H[i, k] = t0
+            den = np.hypot(H[k, k], H[k + 1, k])
+            cs[k], sn[k] = H[k, k] / den, H[k + 1, k] / den
+            H[k, k] = den
+            H[k + 1, k] = 0.0
+            gvec[k + 1] = -sn[k] * gvec[k]
+            gvec[k] = cs[k] * gvec[k]
+            k_used = k + 1
+            st.res = abs(gvec[k + 1])
+            if st.res <= cfg.rtol * bn or hn == 0.0:
+                break
+        y = np.zeros(k_used)
+        for i in range(k_used - 1, -1, -1):
+            y[i] = (gvec[i] - H[i, i + 1:k_used] @ y[i + 1:k_used]) / H[i, i]
+        x = x + Pinv(sum(y[i] * V[i] for i in range(k_used)))
+        if st.res <= cfg.rtol * bn:
+            st.converged = True
+            break
+    return x, st
+
+
+
+# ------------------------------------------------------------------- BRJ (Sec. 4.2.2)
+
+def trace_fd_steps(u):
+    """chi_k = sqrt(eps_hat) * ||u_k|| with ||u_k|| the coefficient norm of
+    variable k over the mesh (sqrt(eps_hat) when that norm is zero)."""
+    nk = np.sqrt(np.sum(u * u, axis=(0, 2)))
+    nk[nk == 0] = 1.0
+    return np.sqrt(EPS_HAT) * nk
+
+
+class BRJ:
+    """Block relaxed Jacobi preconditioner for dN/du = I - dt_a M^-1 dL/du
+    (Eq. Jacobian-matrix-form), split into element blocks L + D + U
+    (Eq. L+D+U) and applied by the iteration of Eq. precond-Jacobi.
+
+    Kept terms of Eq. Jacobian-matrix-form2: the two element-volume terms
+    (exact flux Jacobians, by complex-step differentiation of F and linearity
+    of G in grad Q) and the trace term with the numerical flux Jacobians
+    dH^n/dQ^+- taken by the one-sided finite difference of
+    Eq. numerical-Jac-on-traces (boundary states re-evaluated).  The two
+    terms with the trace-gradient and symmetric-flux Jacobians are neglected.
+    """
+
+    def __init__(self, dg, u, t, dt_a, J=7, omega=1.0):
+        self.dg, self.J, self.omega, self.dt_a = dg, J, omega, dt_a
+        d, nv, nm, E = dg.dim, dg.nv, dg.nm, dg.E
+        self.nb = nv * nm
+        dLdu = self._volume_jacobian(u)                            # [E][v m][l n]
+        self.off = []
+        chi = trace_fd_steps(u)
+        for g in dg.groups:
+            JL, JR = self._trace_jacobians(g, u, t, chi)           # [f][p][k][l]
+            wJ = g["wJ"]
+            BL = dg.Bf[g["fL"]]
+            blk = -np.einsum("pm,fp,fpkl,pn->fkmln", BL, wJ, JL, BL)
+            np.add.at(dLdu, g["eL"], blk.reshape(-1, self.nb, self.nb))
+            if g["bctype"] is None:
+                BR = dg.Bf[g["fR"]]
+                blk = np.einsum("pm,fp,fpkl,pn->fkmln", BR, wJ, JR, BR)
+                np.add.at(dLdu, g["eR"], blk.reshape(-1, self.nb, self.nb))
+                self.off.append((g, JL, JR))
+        # D = I - dt_a M^-1 dL/du (diagonal blocks), then invert
+        Minv = dg.Minv
+        MdL = np.einsum("emn,eknlo->ekmlo", Minv, dLdu.reshape(E, nv, nm, nv, nm))
+        D = np.eye(self.nb)[None] - dt_a * MdL.reshape(E, self.nb, self.nb)
+        self.D = D
+        self.Dinv = np.linalg.inv(D)
+
+    def _volume_jacobian(self, u):
+        dg, ph = self.dg, self.dg.ph
+        d, nv, nm, E = dg.dim, dg.nv, dg.nm, dg.E
+        Qv = dg.values(u, dg.B)
+        dQ = dg.gradients(u, dg.D, dg.ginv)
+        h = 1e-30
+        # A0[e,q,j,k,l] = dH_jk/dQ_l at fixed grad Q (complex step)
+        A0 = np.zeros(Qv.shape[:2] + (d, nv, nv))
+        for l in range(nv):
+            Qc = Qv.astype(complex)
+            Qc[..., l] += 1j * h
+            Hc = phy.euler_flux(Qc, ph)
+            if ph.viscous:
+                Hc = Hc - phy.viscous_flux(Qc, dQ.astype(complex), ph)
+            A0[..., l] = Hc.imag / h
+        # A1[e,q,j,i,k,l] = dH_jk / d(grad_i Q_l) = -G_jk(Q, e_i (x) e_l)
+        A1 = np.zeros(Qv.shape[:2] + (d, d, nv, nv))
+        if ph.viscous:
+            for i in range(d):
+                for l in range(nv):
+                    gu = np.zeros(dQ.shape)
+                    gu[..., i, l] = 1.0
+                    A1[..., :, i, :, l] = -phy.viscous_flux(Qv, gu, ph)
+        # physical derivative tables DB[e,j,q,m] = sum_r ginv[e,q,r,j] D_r[q,m]
+        DB = np.einsum("eqrj,rqm->ejqm", dg.ginv, dg.D)
+        wJ = dg.wJ
+        # volume terms 1 and 2 of Eq. Jacobian-matrix-form2
+        T = np.einsum("eq,ejqm,eqjkl,qn->ekmln", wJ, DB, A0, dg.B)
+        T += np.einsum("eq,ejqm,eqjikl,eiqn->ekmln", wJ, DB, A1, DB)
+        return T.reshape(E, nv * nm, nv * nm)
+
+    def _flux_only(self, g, QL, QR, dQa, t):
+        """H^n on group g as a function of the two traces at fixed gradients;
+        on boundary faces QR is recomputed from QL by the boundary condition."""
+        dg = self.dg
+        if g["bctype"] is None:
+            Qa = 0.5 * (QL + QR)
+        else:
+            QR = phy.boundary_state(dg.ph, g["bctype"], g["x"], t, QL, g["n"])
+            Qa = QR
+        Hh, _ = dg.face_flux(g, QL, QR, Qa, dQa, t)
+        return Hh
+
+    def _trace_jacobians(self, g, u, t, chi):
+        dg = self.dg
+        nv = dg.nv
+        QL, QR, Qa, dQa, _, _ = dg.face_states(g, u, t)
+        H0 = self._flux_only(g, QL, QR, dQa, t)
+        JL = np.zeros(QL.shape + (nv,))
+        JR = np.zeros(QL.shape + (nv,))
+        for l in range(nv):
+            Qp = QL.copy()
+            Qp[..., l] += chi[l]
+            JL[..., l] = (self._flux_only(g, Qp, QR, dQa, t) - H0) / chi[l]
+            if g["bctype"] is None:
+                Qp = QR.copy()
+                Qp[..., l] += chi[l]
+                JR[..., l] = (self._flux_only(g, QL, Qp, dQa, t) - H0) / chi[l]
+        return JL, JR
+
+    def offdiag(self, q):
+        """(L + U) q: the neighbour coupling of the trace term, times
+        -dt_a M^-1."""
+        dg = self.dg
+        out = np.zeros_like(q)
+        for g, JL, JR in self.off:
+            wJ = g["wJ"]
+            qL = dg.values(q, dg.Bf[g["fL"]], g["eL"])
+            qR = dg.values(q, dg.Bf[g["fR"]], g["eR"])
+            # dL_L/du_R q_R = -B_L^T wJ JR qR ; dL_R/du_L q_L = +B_R^T wJ JL qL
+            out[g["eL"]] -= np.einsum("pm,fp,fpkl,fpl->fkm", dg.Bf[g["fL"]], wJ, JR, qR)
+            out[g["eR"]] += np.einsum("pm,fp,fpkl,fpl->fkm", dg.Bf[g["fR"]], wJ, JL, qL)
+        return -self.dt_a * dg.apply_minv(out)
+
+    def diag_solve(self, y):
+        E = self.dg.E
+        return np.einsum("eab,eb->ea", self.Dinv, y.reshape(E, -1)).reshape(y.shape)
+
+    def apply(self, q):
+        """q^J of Eq. precond-Jacobi from q^0 = 0."""
+        qh = np.zeros_like(q)
+        for j in range(self.J):
+            y = q if j == 0 else q - self.offdiag(qh)
+            qh = self.omega * self.diag_solve(y) + (1.0 - self.omega) * qh
+        return qh
+
+    def memory_bytes_paper_layout(self, value_bytes=4):
+        """Per-element storage in the paper's accounting (Tab. BRJ memory):
+        the diagonal inverse block (N_v N_m)^2 and, for each of the 2d faces of
+        the element, the two N_v x N_v trace Jacobians at each face point."""
+        dg = self.dg
+        diag = self.nb ** 2 * value_bytes
+        off = 2 * dg.dim * 2 * dg.nf * dg.nv * dg.nv * value_bytes
+        return diag, off
+
+
+# ------------------------------------------------------------------- Newton + SDIRK
+
+@dataclass
+class NewtonConfig:
+    alpha: float = 1e-3          # relative tolerance of Eq. nonlinear-critria
+    abs_tol: float = 0.0         # > 0: absolute tolerance instead
+    max_iters: int = 20
+    gmres: GmresConfig = field(default_factory=GmresConfig)
+
+
+@dataclass
+class NewtonStats:
+    iters: int = 0
+    gmres_iters: int = 0
+    res0: float = 0.0
+    res: float = 0.0
+    converged: bool = False
+
+
+def newton(dg, S, t, dt_a, u0, precond=None, cfg=None):
+    """Newton's method (Eq. Newton-initial-guess, Newton-Iteration) on
+    N(u) = u - S - dt_a R(u, t) (Eq. nonlinear-equation-system), each linear
+    step solved by JFNK GMRES.  Returns (u, R(u), stats)."""
+    cfg = cfg if cfg is not None else NewtonConfig()
+    u = u0.copy()
+    R = dg.residual(u, t)
+    N = u - S - dt_a * R
+    st = NewtonStats()
+    st.res0 = st.res = norm(N)
+    tol = cfg.abs_tol if cfg.abs_tol > 0 else cfg.alpha * st.res0
+    while True:
+        if st.res <= 0.0 or (st.iters > 0 or cfg.abs_tol > 0) and st.res < tol:
+            st.converged = True
+            break
+        if st.iters >= cfg.max_iters:
+            break
+        Ru = R
+
+        def A(v, u=u, Ru=Ru):
+            return jvp(dg, u, Ru, t, v, 1.0, -dt_a)
+
+        dx, gs = gmres(A, -N, precond, cfg.gmres)
+        st.gmres_iters += gs.iters
+        u = u + dx
+        st.iters += 1
+        R = dg.residual(u, t)
+        N = u - S - dt_a * R
+        st.res = norm(N)
+    return u, R, st
+
+
+def sdirk_tableau(name):
+    """Butcher tableaus of App. A (Tab. RK-coeff): SDIRK2 with
+    lambda = 1 - sqrt(2)/2 and SDIRK3 with lambda = 0.4358665215."""
+    if name == "sdirk2":
+        lam = 1.0 - np.sqrt(2.0) / 2.0
+        A = np.array([[lam, 0.0], [1.0 - lam, lam]])
+        b = np.array([1.0 - lam, lam])
+    elif name == "sdirk3":
+        lam = 0.4358665215
+        b1 = (-6 * lam ** 2 + 16 * lam - 1) / 4
+        b2 = (6 * lam ** 2 - 20 * lam + 5) / 4
+        A = np.array([[lam, 0, 0], [(1 - lam) / 2, lam, 0], [b1, b2, lam]])
+        b = np.array([b1, b2, lam])
+    else:
+        raise ValueError(name)
+    return A, b, A.sum(axis=1)
+
+
+@dataclass
+class StepStats:
+    newton_iters: int = 0
+    gmres_iters: int = 0
+    stages: list = None
+
+
+def sdirk_step(dg, u_n, t, dt, tableau="sdirk2", precond=None, cfg=None,
+               guess=None):
+    """One step of Eq. rk-stage / rk-final: each stage solves
+    N(u^m) = u^m - S_m - dt a_mm R(u^m, t + c_m dt) = 0 by Newton from
+    S_m (or guess(m, S_m)); E^m = dt R(u^m) is taken from the residual of the
+    converged iterate; u^{n+1} = u^n + sum_i b_i E^i."""
+    A, b, c = sdirk_tableau(tableau)
+    M = len(b)
+    E = []
+    st = StepStats(stages=[])
+    for m in range(M):
+        S = u_n + sum(A[m, i] * E[i] for i in range(m))
+        u0 = S if guess is None else guess(m, S)
+        um, Rm, ns = newton(dg, S, t + c[m] * dt, dt * A[m, m], u0, precond, cfg)
+        st.newton_iters += ns.iters
+        st.gmres_iters += ns.gmres_iters
+        st.stages.append(ns)
+        E.append(dt * Rm)
+    return u_n + sum(b[i] * E[i] for i in range(M)), st

@@ -1,0 +1,255 @@
+"""Governing equations (Sec. 2.1), numerical fluxes (Sec. 3.1), analytic
+fields of the verification cases (Sec. 6.1, App. B) and boundary states.
+
+State layout: U[..., v] with v = (rho, rho u_1..rho u_d, E); fluxes
+F[..., i, v] with i the flux direction.  All functions are vectorised over
+leading axes.  euler_flux and viscous_flux use no abs/max/sqrt of the state,
+so they accept complex arrays (complex-step differentiation).
+"""
+import numpy as np
+
+# identifiers shared with the workloads package (plain integers)
+BC_DIRICHLET, BC_ISO_WALL, BC_ADIA_WALL, BC_FARFIELD = 1, 2, 3, 4
+FIELD_UNIFORM, FIELD_VORTEX, FIELD_POISEUILLE, FIELD_TGV, FIELD_CYLINDER = 0, 1, 2, 3, 4
+RIEMANN_ROE, RIEMANN_HLLC = 0, 1
+FORCING_NONE, FORCING_POISEUILLE = 0, 1
+
+
+def primitives(U, ph):
+    """rho, velocity [..., d], pressure p = (gamma-1)(E - rho|u|^2/2) and
+    temperature T = gamma Ma^2 p / rho (equation of state, Sec. 2.1)."""
+    d = U.shape[-1] - 2
+    rho = U[..., 0]
+    vel = U[..., 1:1 + d] / rho[..., None]
+    E = U[..., -1]
+    p = (ph.gamma - 1.0) * (E - 0.5 * np.sum(U[..., 1:1 + d] * vel, axis=-1))
+    T = ph.gamma * ph.Ma ** 2 * p / rho
+    return rho, vel, p, T
+
+
+def conservative(rho, vel, p, ph):
+    E = p / (ph.gamma - 1.0) + 0.5 * rho * np.sum(vel * vel, axis=-1)
+    return np.concatenate([rho[..., None], rho[..., None] * vel, E[..., None]], axis=-1)
+
+
+def euler_flux(U, ph):
+    """Advection flux F_i = (rho u_i, rho u_i u + p e_i, u_i (E + p))."""
+    d = U.shape[-1] - 2
+    rho, vel, p, _ = primitives(U, ph)
+    F = np.zeros(U.shape[:-1] + (d, d + 2), dtype=U.dtype)
+    for i in range(d):
+        F[..., i, 0] = U[..., 1 + i]
+        for k in range(d):
+            F[..., i, 1 + k] = U[..., 1 + i] * vel[..., k]
+        F[..., i, 1 + i] += p
+        F[..., i, -1] = vel[..., i] * (U[..., -1] + p)
+    return F
+
+
+def viscosity(T, ph):
+    """Constant mu = 1/Re, or Sutherland's law with T_inf in kelvin (Sec. 2.1)."""
+    if ph.mu_law == 0:
+        return np.full_like(T, 1.0 / ph.Re)
+    s = 110.0 / ph.T_inf_K
+    return T ** 1.5 / ph.Re * (1.0 + s) / (T + s)
+
+
+def viscous_flux(U, dU, ph):
+    """Diffusion flux G_i = (0, tau_i1..tau_id, u_j tau_ij - q_i) with the
+    Stokes stress tau_ij = mu (du_i/dx_j + du_j/dx_i) - 2/3 mu div(u) delta_ij and
+    Fourier heat flux q_i = -mu / (Ma^2 Pr (gamma-1)) dT/dx_i.  dU[..., j, v]
+    is the gradient of the conservative variables; G is linear in dU."""
+    d = U.shape[-1] - 2
+    g, Ma = ph.gamma, ph.Ma
+    rho, vel, p, T = primitives(U, ph)
+    mu = viscosity(T, ph)
+    drho = dU[..., 0]                                  # [..., j]
+    dvel = (dU[..., 1:1 + d] - vel[..., None, :] * drho[..., :, None]) / rho[..., None, None]
+    # dvel[..., j, k] = d u_k / d x_j
+    e = U[..., -1] / rho
+    de = (dU[..., -1] - e[..., None] * drho) / rho[..., None]
+    dT = g * Ma ** 2 * (g - 1.0) * (de - np.einsum("...jk,...k->...j", dvel, vel))
+    div = np.einsum("...jj->...", dvel)
+    kappa = mu / (Ma ** 2 * ph.Pr * (g - 1.0))
+    G = np.zeros(U.shape[:-1] + (d, d + 2), dtype=np.result_type(U, dU))
+    for i in range(d):
+        for k in range(d):
+            tau = mu * (dvel[..., k, i] + dvel[..., i, k])
+            if i == k:
+                tau = tau - 2.0 / 3.0 * mu * div
+            G[..., i, 1 + k] = tau
+            G[..., i, -1] += vel[..., k] * tau
+        G[..., i, -1] += kappa * dT[..., i]
+    return G
+
+
+def roe_flux(UL, UR, n, ph):
+    """Roe's approximate Riemann flux without entropy fix (Toro, Ch. 11),
+    normal n pointing from L to R."""
+    g = ph.gamma
+    rL, vL, pL, _ = primitives(UL, ph)
+    rR, vR, pR, _ = primitives(UR, ph)
+    HL = (UL[..., -1] + pL) / rL
+    HR = (UR[..., -1] + pR) / rR
+    sL, sR = np.sqrt(rL), np.sqrt(rR)
+    rt = sL * sR
+    ut = (sL[..., None] * vL + sR[..., None] * vR) / (sL + sR)[..., None]
+    Ht = (sL * HL + sR * HR) / (sL + sR)
+    q2 = np.sum(ut * ut, axis=-1)
+    c2 = (g - 1.0) * (Ht - 0.5 * q2)
+    c = np.sqrt(c2)
+    unt = np.sum(ut * n, axis=-1)
+    dr, dp = rR - rL, pR - pL
+    du = vR - vL
+    dun = np.sum(du * n, axis=-1)
+    a1 = (dp - rt * c * dun) / (2 * c2)
+    a5 = (dp + rt * c * dun) / (2 * c2)
+    a2 = dr - dp / c2
+    l1, l2, l5 = np.abs(unt - c), np.abs(unt), np.abs(unt + c)
+    one = np.ones_like(unt)
+
+    def vec(s, m, e):
+        return np.concatenate([s[..., None], m, e[..., None]], axis=-1)
+
+    w1 = (l1 * a1)[..., None] * vec(one, ut - c[..., None] * n, Ht - unt * c)
+    w5 = (l5 * a5)[..., None] * vec(one, ut + c[..., None] * n, Ht + unt * c)
+    w2 = l2[..., None] * (a2[..., None] * vec(one, ut, 0.5 * q2)
+                          + rt[..., None] * vec(0 * one, du - dun[..., None] * n,
+                                                np.sum(ut * du, axis=-1) - unt * dun))
+    FL = np.einsum("...iv,...i->...v", euler_flux(UL, ph), n)
+    FR = np.einsum("...iv,...i->...v", euler_flux(UR, ph), n)
+    return 0.5 * (FL + FR) - 0.5 * (w1 + w2 + w5)
+
+
+def hllc_flux(UL, UR, n, ph):
+    """HLLC flux (Toro, Ch. 10) with Einfeldt (Roe-averaged) wave-speed
+    estimates S_L = min(u_nL - c_L, u~_n - c~), S_R = max(u_nR + c_R, u~_n + c~)."""
+    g = ph.gamma
+    rL, vL, pL, _ = primitives(UL, ph)
+    rR, vR, pR, _ = primitives(UR, ph)
+    cL, cR = np.sqrt(g * pL / rL), np.sqrt(g * pR / rR)
+    HL = (UL[..., -1] + pL) / rL
+    HR = (UR[..., -1] + pR) / rR
+    sL, sR = np.sqrt(rL), np.sqrt(rR)
+    ut = (sL[..., None] * vL + sR[..., None] * vR) / (sL + sR)[..., None]
+    Ht = (sL * HL + sR * HR) / (sL + sR)
+    ct = np.sqrt((g - 1.0) * (Ht - 0.5 * np.sum(ut * ut, axis=-1)))
+    unL, unR = np.sum(vL * n, -1), np.sum(vR * n, -1)
+    unt = np.sum(ut * n, -1)
+    SL = np.minimum(unL - cL, unt - ct)
+    SR = np.maximum(unR + cR, unt + ct)
+    Ss = (pR - pL + rL * unL * (SL - unL) - rR * unR * (SR - unR)) / (rL * (SL - unL) - rR * (SR - unR))
+    FL = np.einsum("...iv,...i->...v", euler_flux(UL, ph), n)
+    FR = np.einsum("...iv,...i->...v", euler_flux(UR, ph), n)
+
+    def star(U, r, v, p, un, S):
+        f = r * (S - un) / (S - Ss)
+        m = f[..., None] * (v + (Ss - un)[..., None] * n)
+        e = f * (U[..., -1] / r + (Ss - un) * (Ss + p / (r * (S - un))))
+        return np.concatenate([f[..., None], m, e[..., None]], axis=-1)
+
+    FsL = FL + SL[..., None] * (star(UL, rL, vL, pL, unL, SL) - UL)
+    FsR = FR + SR[..., None] * (star(UR, rR, vR, pR, unR, SR) - UR)
+    out = np.where((SL >= 0)[..., None], FL,
+                   np.where((Ss >= 0)[..., None], FsL,
+                            np.where((SR > 0)[..., None], FsR, FR)))
+    return out
+
+
+def riemann_flux(UL, UR, n, ph):
+    return roe_flux(UL, UR, n, ph) if ph.riemann == RIEMANN_ROE else hllc_flux(UL, UR, n, ph)
+
+
+# ---------------------------------------------------------------- analytic fields
+
+def exact_state(ph, x, t):
+    """Conservative state of the workload's analytic field at points x[..., d]."""
+    d = x.shape[-1]
+    g, Ma = ph.gamma, ph.Ma
+    shp = x.shape[:-1]
+    if ph.fid in (FIELD_UNIFORM, FIELD_CYLINDER):
+        rho = np.ones(shp)
+        vel = np.zeros(shp + (d,))
+        vel[..., 0] = 1.0
+        T = np.ones(shp)
+    elif ph.fid == FIELD_VORTEX:
+        # isentropic vortex (Sec. 6.1) on [0,1]^2 = [0,10]^2 scaled by 1/s, with the
+        # sign of the u perturbation that makes it a vortex, and T from the radial
+        # momentum balance in the p = rho T/(gamma Ma^2) non-dimensionalisation
+        u0, v0, phi, xc, yc, s = ph.fpar
+        cx = xc + u0 * t
+        cy = yc + v0 * t
+        dx = x[..., 0] - cx
+        dy = x[..., 1] - cy
+        dx = dx - np.round(dx)        # nearest periodic image (period 1)
+        dy = dy - np.round(dy)
+        X, Y = s * dx, s * dy
+        ex = np.exp(1.0 - X * X - Y * Y)
+        vel = np.stack([u0 - phi / (2 * np.pi) * Y * ex, v0 + phi / (2 * np.pi) * X * ex], -1)
+        T = 1.0 - (g - 1.0) * Ma ** 2 * phi ** 2 / (16 * np.pi ** 2) * ex * ex
+        rho = T ** (1.0 / (g - 1.0))
+    elif ph.fid == FIELD_POISEUILLE:
+        theta, L, dpdx = ph.fpar
+        mu = 1.0 / ph.Re
+        y = x[..., 1]
+        rho = np.ones(shp)
+        vel = np.zeros(shp + (d,))
+        vel[..., 0] = -dpdx / (2 * mu) * (y * (L - y) + theta * y * y * (L - y) ** 2)
+        p = 1.0 / (g * Ma ** 2) + dpdx * x[..., 0]
+        T = g * Ma ** 2 * p / rho
+    elif ph.fid == FIELD_TGV:
+        X, Y, Z = x[..., 0], x[..., 1], x[..., 2]
+        vel = np.stack([np.sin(X) * np.cos(Y) * np.cos(Z), -np.cos(X) * np.sin(Y) * np.cos(Z),
+                        np.zeros(shp)], -1)
+        pinf = 1.0 / (g * Ma ** 2)
+        p = pinf + (np.cos(2 * X) + np.cos(2 * Y)) * (np.cos(2 * Z) + 2.0) / 16.0
+        rho = p / pinf
+        T = np.ones(shp)
+    else:
+        raise ValueError(ph.fid)
+    p = rho * T / (g * Ma ** 2)
+    return conservative(rho, vel, p, ph)
+
+
+def forcing(ph, x, t):
+    """Manufactured source of the compressible Poiseuille case (App. B), with
+    f_4 built on h(y) = y(L-y) + theta y^2 (L-y)^2 (the printed f_4 has y(L-y)
+    and an unmatched parenthesis; this form makes the steady residual of the
+    exact solution vanish identically with constant mu)."""
+    f = np.zeros(x.shape[:-1] + (x.shape[-1] + 2,))
+    if ph.forcing == FORCING_NONE:
+        return f
+    theta, L, dpdx = ph.fpar
+    mu = 1.0 / ph.Re
+    g = ph.gamma
+    y = x[..., 1]
+    c = L * L - 6 * y * L + 6 * y * y
+    h = y * (L - y) + theta * y * y * (L - y) ** 2
+    f[..., 1] = dpdx * theta * c
+    f[..., -1] = (dpdx ** 2 / (2 * mu) * h * (1 - theta * c - g / (g - 1))
+                  - dpdx ** 2 / (4 * mu) * (L - 2 * y) ** 2 * (2 * theta * y * L - 2 * theta * y * y + 1) ** 2)
+    return f
+
+
+def wall_temperature(ph, x):
+    if ph.fid == FIELD_POISEUILLE:
+        _, _, dpdx = ph.fpar
+        return 1.0 + ph.gamma * ph.Ma ** 2 * dpdx * x[..., 0]
+    return np.ones(x.shape[:-1])
+
+
+def boundary_state(ph, bctype, x, t, UL, n):
+    """Weakly imposed boundary state U_b used as the exterior state of the
+    Riemann flux and as the state of the viscous boundary flux."""
+    g, Ma = ph.gamma, ph.Ma
+    d = x.shape[-1]
+    if bctype == BC_DIRICHLET:
+        return exact_state(ph, x, t)
+    if bctype == BC_ISO_WALL:
+        Tw = wall_temperature(ph, x)
+        rho = UL[..., 0]
+        Ub = np.zeros_like(UL)
+        Ub[..., 0] = rho
+        Ub[..., -1] = rho * Tw / (g * (g - 1.0) * Ma ** 2)
+        return Ub
+    raise NotImplementedError(f"boundary type {bctype}")

@@ -1,0 +1,264 @@
+"""Pins of the oracle's implicit machinery (Sec. 3.2, Sec. 4.2.2, App. A):
+GMRES against direct solves, the JFNK product against central differences,
+the BRJ Jacobian against dense finite-difference Jacobians, JFNK-Newton
+against brute-force dense Newton, SDIRK against its closed-form stability
+function and order, the memory table of Sec. 5.2, and the manufactured
+Poiseuille order of accuracy (Sec. 6.1)."""
+import os
+import numpy as np
+import pytest
+
+import workloads as w
+from oracle.dg import DG
+from oracle import physics as phy
+from oracle import implicit as im
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def perturbed_exact(dg, seed=0, amp=0.01):
+    u = dg.project_exact()
+    rng = np.random.default_rng(seed)
+    return u * (1 + amp * rng.standard_normal(u.shape))
+
+
+# ------------------------------------------------------------------ GMRES
+
+@pytest.mark.parametrize("ortho", ["cgs2", "mgs"])
+def test_gmres_solves_dense_system(ortho):
+    rng = np.random.default_rng(0)
+    n = 40
+    A = np.eye(n) * 3 + rng.standard_normal((n, n)) / np.sqrt(n)
+    b = rng.standard_normal(n)
+    x, st = im.gmres(lambda v: A @ v, b, None, im.GmresConfig(restart=15, rtol=1e-12, max_cycles=50, ortho=ortho))
+    assert st.converged
+    assert np.allclose(x, np.linalg.solve(A, b), rtol=1e-10, atol=1e-10)
+
+
+def test_gmres_cgs2_and_mgs_same_iterations_with_preconditioner():
+    rng = np.random.default_rng(1)
+    n = 60
+    A = np.eye(n) * 2 + rng.standard_normal((n, n)) / np.sqrt(n)
+    Pinv = np.linalg.inv(np.diag(np.diag(A)) + np.triu(A, 1) * 0.5)
+    b = rng.standard_normal(n)
+    its = []
+    for ortho in ("cgs2", "mgs"):
+        x, st = im.gmres(lambda v: A @ v, b, lambda v: Pinv @ v,
+                         im.GmresConfig(restart=10, rtol=1e-8, max_cycles=30, ortho=ortho))
+        its.append(st.iters)
+        assert np.linalg.norm(A @ x - b) <= 1e-8 * np.linalg.norm(b) * 1.0001
+    assert its[0] == its[1]
+
+
+# ------------------------------------------------------------------ JFNK
+
+def test_jvp_matches_central_difference_and_is_linear():
+    c = w.vortex_case(n=3, P=2)
+    dg = DG(c.mesh, c.P, c.Q, c.phys)
+    u = perturbed_exact(dg)
+    R = dg.residual(u)
+    v1 = w.random_direction(u, 1)
+    v2 = w.random_direction(u, 2)
+    j1 = im.jvp(dg, u, R, 0.0, v1, 0.0, 1.0)
+    h = 1e-4 * np.linalg.norm(u) / np.linalg.norm(v1)
+    cd = (dg.residual(u + h * v1) - dg.residual(u - h * v1)) / (2 * h)
+    assert np.linalg.norm(j1 - cd) < 1e-6 * np.linalg.norm(cd)
+    j2 = im.jvp(dg, u, R, 0.0, v2, 0.0, 1.0)
+    j12 = im.jvp(dg, u, R, 0.0, v1 + v2, 0.0, 1.0)
+    assert np.linalg.norm(j12 - j1 - j2) < 1e-6 * np.linalg.norm(j12)
+    # alpha/beta combination used by Newton: dN/du v = v - dt_a dR/du v
+    jn = im.jvp(dg, u, R, 0.0, v1, 1.0, -0.01)
+    assert np.allclose(jn, v1 - 0.01 * j1, rtol=1e-12, atol=1e-12 * np.abs(jn).max())
+
+
+def dense_jacobian(fn, u, h=1e-6):
+    n = u.size
+    J = np.zeros((n, n))
+    for k in range(n):
+        e = np.zeros(n)
+        e[k] = h * max(1.0, abs(u.ravel()[k]))
+        J[:, k] = (fn(u + e.reshape(u.shape)) - fn(u - e.reshape(u.shape))).ravel() / (2 * e[k])
+    return J
+
+
+def assemble_brj(pc, shape):
+    n = int(np.prod(shape))
+    Pm = np.zeros((n, n))
+    nb = pc.nb
+    for e in range(pc.dg.E):
+        Pm[e * nb:(e + 1) * nb, e * nb:(e + 1) * nb] = pc.D[e]
+    for k in range(n):
+        ek = np.zeros(n)
+        ek[k] = 1.0
+        Pm[:, k] += pc.offdiag(ek.reshape(shape)).ravel()
+    return Pm
+
+
+@pytest.mark.parametrize("mk", [lambda: w.vortex_case(n=3, P=1, viscous=False),
+                                lambda: w.vortex_case(n=2, P=2, viscous=False, riemann=phy.RIEMANN_HLLC),
+                                lambda: w.small_tgv_case((2, 2, 1), P=1)])
+def test_brj_equals_true_jacobian_when_inviscid(mk):
+    """Without viscosity the two neglected terms vanish, so the kept-term
+    block matrix D + (L + U) equals dN/du = I - dt_a dR/du."""
+    c = mk()
+    c.phys.viscous = False
+    dg = DG(c.mesh, c.P, c.Q, c.phys)
+    # additive noise keeps every normal velocity away from 0, where the Roe
+    # flux's |u_n| has a kink (one-sided and central differences disagree)
+    u = perturbed_exact(dg) + 0.02 * w.random_direction(dg.project_exact(), 5)
+    dt_a = 0.01
+    Nj = np.eye(u.size) - dt_a * dense_jacobian(lambda x: dg.residual(x), u)
+    pc = im.BRJ(dg, u, 0.0, dt_a, J=7)
+    Pm = assemble_brj(pc, u.shape)
+    # tolerance: the one-sided trace difference with chi = sqrt(eps) ||u_k|| has a
+    # rounding error ~ eps |H| / chi, large where a variable's norm is small
+    # next to the flux (the w-momentum of the 3-D case); sign or assembly
+    # mistakes give O(1) differences
+    assert np.abs(Pm - Nj).max() < 1e-4 * np.abs(Nj - np.eye(u.size)).max()
+
+
+def test_brj_volume_terms_exact_with_viscosity():
+    """Terms 1-2 of Eq. Jacobian-matrix-form2 equal the Jacobian of the volume
+    integral alone (viscous, including the grad-Q dependence)."""
+    c = w.vortex_case(n=2, P=2, Re=5.0)
+    dg = DG(c.mesh, c.P, c.Q, c.phys)
+    u = perturbed_exact(dg)
+    Jv = dense_jacobian(lambda x: dg.rhs(x, 0.0, faces=False), u)
+    pc = im.BRJ.__new__(im.BRJ)
+    pc.dg = dg
+    T = pc._volume_jacobian(u)
+    nb = dg.nv * dg.nm
+    for e in range(dg.E):
+        blk = Jv[e * nb:(e + 1) * nb, e * nb:(e + 1) * nb]
+        assert np.abs(T[e] - blk).max() < 1e-7 * np.abs(blk).max()
+
+
+def test_brj_iteration_converges_to_kept_term_solve():
+    c = w.vortex_case(n=3, P=1, Re=20.0)
+    dg = DG(c.mesh, c.P, c.Q, c.phys)
+    u = perturbed_exact(dg)
+    pc = im.BRJ(dg, u, 0.0, 0.005, J=80)
+    Pm = assemble_brj(pc, u.shape)
+    q = w.random_direction(u, 4)
+    ref = np.linalg.solve(Pm, q.ravel())
+    assert np.linalg.norm(pc.apply(q).ravel() - ref) < 1e-10 * np.linalg.norm(ref)
+    # J = 1 is plain block Jacobi
+    pc.J = 1
+    assert np.allclose(pc.apply(q), pc.diag_solve(q))
+
+
+def test_brj_memory_table():
+    """Per-element storage in the paper's accounting reproduces Tab.
+    BRJ-Memory-consumption with Q = ceil(3(P+1)/2) face points per direction
+    (single-precision blocks), and Jacobian-Dense = 7 blocks in double."""
+    rows = [l.split() for l in open(os.path.join(HERE, "golden", "brj_memory_table.txt"))
+            if l.strip() and not l.startswith("#")]
+    for P, diag, off, tot, dense in ([int(v) for v in r] for r in rows):
+        Q = int(np.ceil(3 * (P + 1) / 2))
+        nb = 5 * (P + 1) ** 3
+        pc = im.BRJ.__new__(im.BRJ)
+        pc.nb = nb
+        pc.dg = type("G", (), {"dim": 3, "nf": Q * Q, "nv": 5})()
+        dsz, osz = pc.memory_bytes_paper_layout(4)
+        assert (dsz, osz, dsz + osz) == (diag, off, tot)
+        assert 7 * nb * nb * 8 == dense
+
+
+# ------------------------------------------------------------------ Newton
+
+def test_jfnk_newton_matches_dense_newton():
+    c = w.vortex_case(n=2, P=1, Re=50.0)
+    dg = DG(c.mesh, c.P, c.Q, c.phys)
+    u0 = perturbed_exact(dg, amp=0.02)
+    dt_a = 0.02
+    S = u0.copy()
+    cfg = im.NewtonConfig(abs_tol=1e-11, max_iters=30,
+                          gmres=im.GmresConfig(restart=80, rtol=1e-10, max_cycles=5))
+    pc = im.BRJ(dg, u0, 0.0, dt_a, J=3)
+    uj, _, st = im.newton(dg, S, 0.0, dt_a, S, pc.apply, cfg)
+    assert st.converged
+    # brute force: dense FD Jacobian + LU at every Newton step
+    N = lambda x: x - S - dt_a * dg.residual(x)
+    ud = S.copy()
+    for _ in range(10):
+        J = dense_jacobian(N, ud)
+        ud = ud - np.linalg.solve(J, N(ud).ravel()).reshape(ud.shape)
+    assert np.linalg.norm(uj - ud) < 1e-10 * np.linalg.norm(ud)
+
+
+# ------------------------------------------------------------------ SDIRK
+
+class ScalarODE:
+    """y' = f(y, t) posed as a 1-coefficient 'mesh' for the oracle's
+    Newton/SDIRK drivers."""
+    def __init__(self, f):
+        self.f = f
+
+    def residual(self, u, t):
+        return self.f(u, t)
+
+
+@pytest.mark.parametrize("name", ["sdirk2", "sdirk3"])
+def test_sdirk_stability_function(name):
+    A, b, c = im.sdirk_tableau(name)
+    cfg = im.NewtonConfig(abs_tol=1e-15, gmres=im.GmresConfig(restart=2, rtol=1e-14))
+    for z in (-0.5, -3.0, -40.0, 0.3):
+        ode = ScalarODE(lambda u, t: z * u)
+        y1, _ = im.sdirk_step(ode, np.ones((1, 1, 1)), 0.0, 1.0, name, None, cfg)
+        Rz = 1 + z * b @ np.linalg.solve(np.eye(len(b)) - z * A, np.ones(len(b)))
+        assert abs(y1.item() - Rz) < 1e-13 * max(1, abs(Rz))
+
+
+def test_butcher_order_conditions():
+    A, b, c = im.sdirk_tableau("sdirk2")
+    assert abs(b.sum() - 1) < 1e-15 and abs(b @ c - 0.5) < 1e-15
+    A, b, c = im.sdirk_tableau("sdirk3")
+    assert abs(b.sum() - 1) < 1e-10 and abs(b @ c - 0.5) < 1e-10
+    assert abs(b @ c ** 2 - 1 / 3) < 1e-10 and abs(b @ A @ c - 1 / 6) < 1e-10
+    lam = A[0, 0]
+    assert abs(lam ** 3 - 3 * lam ** 2 + 1.5 * lam - 1 / 6) < 1e-10
+
+
+@pytest.mark.parametrize("name,order", [("sdirk2", 2), ("sdirk3", 3)])
+def test_sdirk_order_on_nonlinear_ode(name, order):
+    f = lambda u, t: -u * u + np.cos(t)
+    cfg = im.NewtonConfig(abs_tol=1e-15, max_iters=30, gmres=im.GmresConfig(restart=2, rtol=1e-14))
+    ode = ScalarODE(f)
+
+    def run(n):
+        y, dt = np.full((1, 1, 1), 0.5), 1.0 / n
+        for k in range(n):
+            y, _ = im.sdirk_step(ode, y, k * dt, dt, name, None, cfg)
+        return y.item()
+
+    ref = run(512)
+    e1, e2 = abs(run(16) - ref), abs(run(32) - ref)
+    assert np.log2(e1 / e2) > order - 0.3
+
+
+# ------------------------------------------------------------------ order of accuracy
+
+@pytest.mark.slow
+def test_poiseuille_steady_order_of_accuracy():
+    """Steady implicit solves of the manufactured Poiseuille flow (weak
+    Dirichlet inflow/outflow, isothermal walls, App. B forcing) converge at
+    the design order P+1 in L2 (Sec. 6.1)."""
+    for P in (1, 2):
+        errs = []
+        for nx, ny in ((4, 2), (8, 4)):
+            c = w.poiseuille_case(P, nx=nx, ny=ny)
+            dg = DG(c.mesh, c.P, c.Q, c.phys)
+            u = dg.project_exact()
+            dt = 1.0
+            cfg = im.NewtonConfig(abs_tol=1e-10, max_iters=8,
+                                  gmres=im.GmresConfig(restart=40, rtol=1e-3, max_cycles=20))
+            for _ in range(8):
+                pc = im.BRJ(dg, u, 0.0, dt, J=7)
+                u, R, st = im.newton(dg, u, 0.0, dt, u, pc.apply, cfg)
+                if np.linalg.norm(R) < 1e-9:
+                    break
+                dt *= 10
+            assert np.linalg.norm(dg.residual(u)) < 1e-8
+            e = dg.l2_error(u, lambda x: phy.exact_state(c.phys, x, 0.0))
+            errs.append(np.linalg.norm(e[:3]))
+        assert np.log2(errs[0] / errs[1]) > P + 1 - 0.3, (P, errs)

@@ -1,0 +1,120 @@
+"""Physical parameters and meshes of the synthetic workloads.
+
+Every workload is defined by a mesh, a Physics record and an analytic field
+id; the analytic formulas themselves (initial fields, exact solutions,
+forcing) are implemented separately by the oracle and by the CUDA library.
+"""
+from dataclasses import dataclass, field as dc_field
+import numpy as np
+from .mesh import box_mesh, clustered_spacing, ogrid_mesh
+
+# boundary-condition types (entry of the per-boundary table)
+BC_PERIODIC = 0      # never in the table: periodic faces are interior faces
+BC_DIRICHLET = 1     # weak Dirichlet state from the workload's exact solution
+BC_ISO_WALL = 2      # isothermal no-slip wall, T from the exact solution
+BC_ADIA_WALL = 3     # adiabatic no-slip wall
+BC_FARFIELD = 4      # characteristic (Riemann-invariant) far field
+
+# analytic fields
+FIELD_UNIFORM = 0
+FIELD_VORTEX = 1
+FIELD_POISEUILLE = 2
+FIELD_TGV = 3
+FIELD_CYLINDER = 4   # uniform stream (1, 0, 0) at T = 1, rho = 1
+
+RIEMANN_ROE = 0
+RIEMANN_HLLC = 1
+FORCING_NONE = 0
+FORCING_POISEUILLE = 1
+
+
+@dataclass
+class Physics:
+    gamma: float = 1.4
+    Pr: float = 0.72
+    Ma: float = 0.1
+    Re: float = 100.0
+    viscous: bool = True
+    mu_law: int = 0            # 0 constant mu = 1/Re, 1 Sutherland
+    T_inf_K: float = 288.15    # reference temperature for Sutherland's law
+    riemann: int = RIEMANN_ROE
+    beta_s: float = 1.0
+    forcing: int = FORCING_NONE
+    fid: int = FIELD_UNIFORM   # analytic field id
+    # field parameters (vortex: u0, v0, phi, xc, yc, scale;
+    # Poiseuille: theta, L, dpdx; uniform: rho, u, v, w, T)
+    fpar: tuple = ()
+    bc: list = dc_field(default_factory=list)   # bc[id] = type
+
+    @property
+    def mu(self):
+        return 1.0 / self.Re
+
+
+@dataclass
+class Case:
+    name: str
+    mesh: object
+    P: int
+    Q: int
+    phys: Physics
+
+
+def vortex_case(n=8, P=2, Q=None, Ma=0.1, Re=100.0, viscous=True, riemann=RIEMANN_ROE):
+    """Isentropic vortex on the periodic unit square, n x n quads."""
+    Q = P + 2 if Q is None else Q
+    lines = [np.linspace(0.0, 1.0, n + 1)] * 2
+    m = box_mesh(lines, (True, True))
+    ph = Physics(Ma=Ma, Re=Re, viscous=viscous, riemann=riemann, fid=FIELD_VORTEX,
+                 fpar=(1.0, 0.5, 5.0, 0.5, 0.5, 10.0))
+    return Case(f"vortex{n}x{n}_P{P}", m, P, Q, ph)
+
+
+def poiseuille_case(P, nx=16, ny=8, ratio=1.1, Q=None, Ma=0.2, Re=100.0, theta=0.01,
+                    x_bc=BC_DIRICHLET, y_bc=BC_ISO_WALL):
+    """Manufactured compressible Poiseuille channel [0,2]x[0,1], wall-clustered
+    in y (geometric ratio from each wall), Dirichlet at x = 0, 2 and
+    isothermal walls at y = 0, 1."""
+    Q = P + 2 if Q is None else Q
+    xl = np.linspace(0.0, 2.0, nx + 1)
+    yl = clustered_spacing(ny // 2, ratio, 1.0)
+    m = box_mesh([xl, yl], (False, False), side_bc=[0, 0, 1, 1])
+    mu = 1.0 / Re
+    ph = Physics(Ma=Ma, Re=Re, fid=FIELD_POISEUILLE, forcing=FORCING_POISEUILLE,
+                 fpar=(theta, 1.0, -8.0 * mu), bc=[x_bc, y_bc])
+    return Case(f"poiseuille{nx}x{ny}_P{P}", m, P, Q, ph)
+
+
+def tgv_case(n=16, P=3, Q=None, Re=1600.0, Ma=0.1, riemann=RIEMANN_ROE):
+    """Taylor-Green vortex on the periodic box [-pi, pi]^3, n^3 hexes."""
+    Q = int(np.ceil(3 * (P + 1) / 2)) if Q is None else Q
+    lines = [np.linspace(-np.pi, np.pi, n + 1)] * 3
+    m = box_mesh(lines, (True, True, True))
+    ph = Physics(Ma=Ma, Re=Re, fid=FIELD_TGV, riemann=riemann)
+    return Case(f"tgv{n}^3_P{P}", m, P, Q, ph)
+
+
+def small_tgv_case(shape=(4, 3, 2), P=2, Q=None, Re=1600.0, Ma=0.1, riemann=RIEMANN_ROE,
+                   stretch=False):
+    """A small periodic 3-D box with an anisotropic element count (and
+    optionally non-uniform spacing), used for parity cases."""
+    Q = int(np.ceil(3 * (P + 1) / 2)) if Q is None else Q
+    lines = []
+    for r, n in enumerate(shape):
+        l = np.linspace(-np.pi, np.pi, n + 1)
+        if stretch:
+            s = np.linspace(0, 1, n + 1)
+            l = -np.pi + 2 * np.pi * (s + 0.08 * np.sin(2 * np.pi * s) * (r + 1) / 3)
+        lines.append(l)
+    m = box_mesh(lines, (True, True, True))
+    ph = Physics(Ma=Ma, Re=Re, fid=FIELD_TGV, riemann=riemann)
+    return Case(f"box{shape}_P{P}", m, P, Q, ph)
+
+
+def cylinder_case(n_r=64, n_theta=96, n_z=12, P=3, Q=None, Re=3900.0, Ma=0.2):
+    """Curved O-grid around a unit-diameter cylinder (radius 0.5), outer
+    radius 20, radial growth 1.08, span pi: adiabatic wall and far field."""
+    Q = int(np.ceil(3 * (P + 1) / 2)) if Q is None else Q
+    m = ogrid_mesh(n_r, n_theta, n_z, 0.5, 20.0, 1.08, np.pi)
+    ph = Physics(Ma=Ma, Re=Re, fid=FIELD_CYLINDER, bc=[BC_ADIA_WALL, BC_FARFIELD])
+    return Case(f"cylinder{n_r}x{n_theta}x{n_z}_P{P}", m, P, Q, ph)
