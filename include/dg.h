@@ -1,0 +1,195 @@
+/*
+ * dg.h - C ABI of a GB300 (sm_103a) implementation of the implicit
+ * spectral/hp discontinuous Galerkin compressible Navier-Stokes solver hot
+ * path: the DG residual, the Jacobian-free Newton-Krylov product, restarted
+ * GMRES, the block relaxed Jacobi (BRJ) preconditioner, Newton and SDIRK
+ * time stepping (arXiv 2002.04222, Sec. 3-4).
+ *
+ * Conventions for every entry point
+ *  - Vectors are caller-owned DEVICE buffers of doubles in the layout
+ *    u[e][v][m]: element e (0..n_elem-1), conservative variable
+ *    v = (rho, rho u_1..rho u_d, E) (n_var = dim+2), modal coefficient m of the
+ *    tensor-product modified basis (n_mode = (P+1)^dim, first direction
+ *    fastest; 1-D mode 0 = (1-x)/2, mode P = (1+x)/2, 0<p<P the bubble
+ *    (1-x)(1+x)/4 P_{p-1}^{(1,1)}(x)).  Length n_dof = n_elem*n_var*n_mode.
+ *  - Descriptors (dg_mesh_desc, dg_physics, configs) are HOST memory and are
+ *    copied; the library never frees caller memory.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls are
+ *    stream-ordered; dg_gmres and sdirk_step synchronise the stream before
+ *    returning (their statistics are host values).
+ *  - Errors: a dg_status is returned, nothing is thrown across the ABI.
+ *    DG_ERR_ARG for invalid arguments, DG_ERR_UNSUPPORTED for a
+ *    (dim, P, Q) or feature this build does not provide, DG_ERR_CUDA for a
+ *    CUDA failure (sticky errors included), DG_ERR_OOM when device memory
+ *    runs out, DG_ERR_NONFINITE when a norm is not finite,
+ *    DG_ERR_NOT_CONVERGED when an iteration cap is hit (stats are filled and
+ *    the output holds the last iterate).
+ *  - Handles are not thread-safe; one handle may be used by one host thread
+ *    at a time.  All work of one handle must be on one stream at a time.
+ */
+#ifndef DG_JFNK_H
+#define DG_JFNK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DG_OK = 0,
+  DG_ERR_ARG = -1,
+  DG_ERR_CUDA = -2,
+  DG_ERR_OOM = -3,
+  DG_ERR_NONFINITE = -4,
+  DG_ERR_NOT_CONVERGED = -5,
+  DG_ERR_UNSUPPORTED = -6,
+  DG_ERR_TIMEOUT = -7
+} dg_status;
+
+typedef struct dg_mesh_s* dg_mesh_t;       /* geometry, tables, workspaces */
+typedef struct dg_precond_s* dg_precond_t; /* BRJ blocks + trace Jacobians */
+
+/* Mesh of quadrilaterals (dim 2) or hexahedra (dim 3), Sec. 3.1.
+ * nodes[e][a][x]: geometry nodes of element e, a = tensor index of the
+ *   (geom_order+1)^dim equispaced reference nodes (first direction fastest).
+ *   This build accepts geom_order = 1 with axis-aligned elements (others:
+ *   DG_ERR_UNSUPPORTED).
+ * faces[f][6] = (eL, fL, eR, fR, orient, bc): local face 2r is xi_r = -1,
+ *   2r+1 is xi_r = +1; interior and periodic faces have eR >= 0 and bc = -1,
+ *   physical boundary faces eR = fR = -1 and bc = index into dg_physics.bc.
+ *   orient must be 0 (face points of both sides coincide in order).
+ * Q: Gauss-Legendre points per direction (volume and faces). */
+typedef struct {
+  int dim, P, Q, n_elem, geom_order, n_faces;
+  const double* nodes;  /* host, n_elem*(geom_order+1)^dim*dim */
+  const int32_t* faces; /* host, n_faces*6 */
+} dg_mesh_desc;
+
+enum { DG_RIEMANN_ROE = 0, DG_RIEMANN_HLLC = 1 };
+enum { DG_BC_DIRICHLET = 1, DG_BC_ISO_WALL = 2, DG_BC_ADIA_WALL = 3, DG_BC_FARFIELD = 4 };
+enum { DG_FIELD_UNIFORM = 0, DG_FIELD_VORTEX = 1, DG_FIELD_POISEUILLE = 2, DG_FIELD_TGV = 3,
+       DG_FIELD_CYLINDER = 4 };
+enum { DG_FORCING_NONE = 0, DG_FORCING_POISEUILLE = 1 };
+
+/* Physical model, Sec. 2.1: p = rho T / (gamma Ma^2), constant mu = 1/Re
+ * (mu_law 0) or Sutherland's law with T_inf_K kelvin (mu_law 1), heat flux
+ * -mu/(Ma^2 Pr (gamma-1)) grad T.  viscous = 0 gives the Euler equations.
+ * field / fpar select the analytic field used by dg_project, by Dirichlet
+ * boundaries and by the wall temperature (vortex: u0, v0, phi, xc, yc,
+ * scale; Poiseuille: theta, L, dp/dx).  bc[i] is the type of boundary i. */
+typedef struct {
+  double gamma, Pr, Ma, Re, T_inf_K, beta_s;
+  int viscous, mu_law, riemann, forcing, field;
+  double fpar[8];
+  int n_bc;
+  int bc[8];
+} dg_physics;
+
+typedef struct {
+  int dim, P, Q, n_elem, n_var, n_mode, n_quad, n_faces;
+  long long n_dof;
+} dg_mesh_info_t;
+
+/* Create a mesh handle: uploads geometry and connectivity, builds the 1-D
+ * tables, element metrics and the forcing vector on `stream`.  *out owns all
+ * device workspaces of the residual; free it with dg_mesh_destroy. */
+dg_status dg_mesh_create(const dg_mesh_desc* mesh, const dg_physics* phys, void* stream,
+                         dg_mesh_t* out);
+dg_status dg_mesh_destroy(dg_mesh_t m);
+dg_status dg_mesh_info(dg_mesh_t m, dg_mesh_info_t* info);
+
+/* u = L2 projection of the workload's analytic field at time t (Sec. 3.1,
+ * Eq. coeff: M u = B^T Lambda(wJ) U(x_q)). */
+dg_status dg_project(dg_mesh_t m, double t, double* u, void* stream);
+
+/* r = R(u, t) = M^-1 L(u, t), the right-hand side of M du/dt = L
+ * (Sec. 3.1, Eq. matrix-form-equations; Sec. 3.2, Eq. ode).  u and r must
+ * not alias. */
+dg_status dg_residual(dg_mesh_t m, const double* u, double t, double* r, void* stream);
+
+/* Jacobian-free product (Sec. 4.2.2, Eq. Jacobian-free-matrix, eps-JF):
+ *   out = alpha*v + beta*(R(u + eps v, t) - r_u)/eps,
+ *   eps = sqrt(2^-52) * ||u||_2 / ||v||_2  (sqrt(2^-52)/||v|| if u = 0),
+ * where r_u = R(u, t) was computed by the caller.  Newton use:
+ * alpha = 1, beta = -dt*a_mm gives dN/du . v; alpha = 0, beta = 1 gives
+ * dR/du . v.  If v = 0, out = 0.  out must not alias u, r_u or v. */
+dg_status dg_jvp(dg_mesh_t m, const double* u, const double* r_u, double t, const double* v,
+                 double alpha, double beta, double* out, void* stream);
+
+enum { DG_PREC_FP64 = 0, DG_PREC_FP32 = 1, DG_PREC_BF16 = 2 };
+/* BRJ(J) settings (Sec. 4.2.2, Eq. precond-Jacobi): J sweeps (>= 1),
+ * relaxation omega, storage/arithmetic precision of the blocks. */
+typedef struct {
+  int J;
+  int precision;
+  double omega;
+} dg_prec_cfg;
+
+/* Build (or rebuild in place, when *inout is not NULL and was built for the
+ * same mesh) the BRJ preconditioner of dN/du = I - dt_a M^-1 dL/du at (u, t)
+ * (Sec. 4.2.2, Eq. Jacobian-matrix-form/-form2, numerical-Jac-on-traces):
+ * element-volume Jacobians from the exact flux derivatives, trace flux
+ * Jacobians by one-sided differences with chi_k = sqrt(2^-52)*||u_k||_2,
+ * the trace-gradient and symmetric-flux terms neglected; the diagonal
+ * blocks are inverted and stored, the trace Jacobians kept for the
+ * off-diagonal product. */
+dg_status dg_precond_build(dg_mesh_t m, const double* u, double t, double dt_a,
+                           const dg_prec_cfg* cfg, dg_precond_t* inout, void* stream);
+/* out = P^-1 q by the BRJ(J) iteration from q^0 = 0 (Eq. precond-Jacobi).
+ * out must not alias q. */
+dg_status dg_precond_apply(dg_precond_t p, const double* q, double* out, void* stream);
+dg_status dg_precond_destroy(dg_precond_t p);
+
+/* Restarted right-preconditioned GMRES (Sec. 3.2; Saad & Schultz) for
+ * (I - dt_a dR/du(u)) x = b with the Jacobian-free product at (u, r_u):
+ * x0 = 0, Arnoldi by classical Gram-Schmidt applied twice with fixed-order
+ * FP64 reductions, Givens rotations, stop when the residual estimate is
+ * <= rtol*||b||, at most max_cycles restarts of length restart.  p may be
+ * NULL (no preconditioner). */
+typedef struct {
+  int restart;
+  int max_cycles;
+  double rtol;
+} dg_gmres_cfg;
+typedef struct {
+  int iters, cycles, converged;
+  double res0, res;
+} dg_gmres_stats;
+dg_status dg_gmres(dg_mesh_t m, dg_precond_t p, const double* u, const double* r_u, double t,
+                   double dt_a, const double* b, double* x, const dg_gmres_cfg* cfg,
+                   dg_gmres_stats* stats, void* stream);
+
+/* One SDIRK step (Sec. 3.2, Eq. rk-stage, rk-final; App. A tableaus): each
+ * stage solves N(u) = u - S_m - dt a_mm R(u, t + c_m dt) = 0 by Newton
+ * (Eq. Newton-Iteration) from u = S_m, stopping when ||N|| < alpha ||N(S_m)||
+ * (Eq. nonlinear-critria) or, if abs_tol > 0, when ||N|| < abs_tol.  The
+ * preconditioner in *p_inout is built at (u^n, t) when *p_inout is NULL or
+ * rebuild != 0, and reused otherwise (freezing, Sec. 4.2.2); it is left in
+ * *p_inout for the next step. */
+enum { DG_SDIRK2 = 2, DG_SDIRK3 = 3 };
+typedef struct {
+  int tableau;
+  double alpha;
+  double abs_tol;
+  int max_newton;
+  int rebuild;
+  int use_precond;
+  dg_gmres_cfg gmres;
+  dg_prec_cfg prec;
+} dg_sdirk_cfg;
+typedef struct {
+  int newton_iters, gmres_iters, stages, precond_built;
+  int stage_newton[4], stage_gmres[4];
+  double stage_res0[4], stage_res[4];
+} dg_step_stats;
+dg_status sdirk_step(dg_mesh_t m, const dg_sdirk_cfg* cfg, double* u_inout, double t, double dt,
+                     dg_precond_t* p_inout, dg_step_stats* stats, void* stream);
+
+/* Static description of a status code. */
+const char* dg_status_string(dg_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DG_JFNK_H */

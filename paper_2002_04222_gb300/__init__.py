@@ -1,0 +1,159 @@
+"""GB300 (sm_103a) implementation of the implicit spectral/hp DG compressible
+Navier-Stokes hot path: DG residual, Jacobian-free Newton-Krylov product,
+restarted GMRES, block relaxed Jacobi preconditioner, Newton and SDIRK
+(arXiv 2002.04222, Sec. 3-4).
+
+The compute path is the CUDA library libdgjfnk.so behind the C ABI of
+include/dg.h; this module only marshals torch CUDA tensors and host
+descriptors into it.  There is no CPU path.
+"""
+import ctypes
+
+import torch
+
+from . import _lib
+
+_LIB = None
+
+
+def lib():
+    global _LIB
+    if _LIB is None:
+        _LIB = _lib.load()
+    return _LIB
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise ValueError("expected a contiguous CUDA float64 tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _check(name, code, ok=(0,)):
+    if code not in ok:
+        raise _lib.DGError(name, code)
+    return code
+
+
+class Mesh:
+    """A mesh handle (dg_mesh_t) built from a workloads mesh, P, Q and
+    Physics record."""
+
+    def __init__(self, mesh, P, Q, phys, stream=None):
+        self._lib = lib()
+        self._desc = _lib.mesh_desc(mesh, P, Q)
+        self._phys = _lib.physics(phys)
+        h = ctypes.c_void_p()
+        _check("dg_mesh_create", self._lib.dg_mesh_create(ctypes.byref(self._desc),
+                                                          ctypes.byref(self._phys),
+                                                          _stream(stream), ctypes.byref(h)))
+        self.handle = h
+        info = _lib.MeshInfo()
+        _check("dg_mesh_info", self._lib.dg_mesh_info(h, ctypes.byref(info)))
+        self.info = {f: getattr(info, f) for f, _ in _lib.MeshInfo._fields_}
+        self.shape = (info.n_elem, info.n_var, info.n_mode)
+
+    @classmethod
+    def from_case(cls, case, stream=None):
+        return cls(case.mesh, case.P, case.Q, case.phys, stream)
+
+    def close(self):
+        if self.handle:
+            self._lib.dg_mesh_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def empty(self):
+        return torch.empty(self.shape, dtype=torch.float64, device="cuda")
+
+    def project(self, t=0.0, out=None, stream=None):
+        out = self.empty() if out is None else out
+        _check("dg_project", self._lib.dg_project(self.handle, t, _ptr(out), _stream(stream)))
+        return out
+
+    def residual(self, u, t=0.0, out=None, stream=None):
+        out = self.empty() if out is None else out
+        _check("dg_residual", self._lib.dg_residual(self.handle, _ptr(u), t, _ptr(out),
+                                                    _stream(stream)))
+        return out
+
+    def jvp(self, u, r_u, v, t=0.0, alpha=0.0, beta=1.0, out=None, stream=None):
+        out = self.empty() if out is None else out
+        _check("dg_jvp", self._lib.dg_jvp(self.handle, _ptr(u), _ptr(r_u), t, _ptr(v), alpha, beta,
+                                          _ptr(out), _stream(stream)))
+        return out
+
+    def gmres(self, u, r_u, b, t=0.0, dt_a=0.0, precond=None, restart=30, max_cycles=10,
+              rtol=5e-2, out=None, stream=None):
+        out = self.empty() if out is None else out
+        cfg = _lib.GmresCfg(restart, max_cycles, rtol)
+        st = _lib.GmresStats()
+        code = self._lib.dg_gmres(self.handle, precond.handle if precond else None, _ptr(u),
+                                  _ptr(r_u), t, dt_a, _ptr(b), _ptr(out), ctypes.byref(cfg),
+                                  ctypes.byref(st), _stream(stream))
+        _check("dg_gmres", code, ok=(0, _lib.DG_ERR_NOT_CONVERGED))
+        return out, {f: getattr(st, f) for f, _ in _lib.GmresStats._fields_}
+
+    def sdirk_step(self, u, t, dt, precond=None, tableau=2, alpha=1e-3, abs_tol=0.0,
+                   max_newton=20, rebuild=False, restart=30, max_cycles=10, rtol=5e-2,
+                   J=7, precision="fp64", omega=1.0, use_precond=True, stream=None):
+        """One SDIRK step in place on u; `precond` is a Precond holder whose
+        handle is built (or reused, frozen) by the library."""
+        cfg = _lib.SdirkCfg(tableau, alpha, abs_tol, max_newton, int(rebuild), int(use_precond),
+                            _lib.GmresCfg(restart, max_cycles, rtol),
+                            _lib.PrecCfg(J, _lib.PREC[precision], omega))
+        st = _lib.StepStats()
+        holder = precond if precond is not None else Precond(self)
+        code = self._lib.sdirk_step(self.handle, ctypes.byref(cfg), _ptr(u), t, dt,
+                                    ctypes.byref(holder.handle), ctypes.byref(st), _stream(stream))
+        _check("sdirk_step", code, ok=(0, _lib.DG_ERR_NOT_CONVERGED))
+        out = {f: getattr(st, f) for f, _ in _lib.StepStats._fields_}
+        for k in ("stage_newton", "stage_gmres", "stage_res0", "stage_res"):
+            out[k] = list(out[k])[: st.stages]
+        out["converged"] = code == 0
+        return out
+
+
+class Precond:
+    """Holder of a BRJ preconditioner handle (dg_precond_t)."""
+
+    def __init__(self, mesh):
+        self.mesh = mesh
+        self.handle = ctypes.c_void_p()
+        self._lib = lib()
+
+    def build(self, u, t=0.0, dt_a=0.0, J=7, precision="fp64", omega=1.0, stream=None):
+        cfg = _lib.PrecCfg(J, _lib.PREC[precision], omega)
+        _check("dg_precond_build", self._lib.dg_precond_build(
+            self.mesh.handle, _ptr(u), t, dt_a, ctypes.byref(cfg), ctypes.byref(self.handle),
+            _stream(stream)))
+        return self
+
+    def apply(self, q, out=None, stream=None):
+        out = self.mesh.empty() if out is None else out
+        _check("dg_precond_apply", self._lib.dg_precond_apply(self.handle, _ptr(q), _ptr(out),
+                                                              _stream(stream)))
+        return out
+
+    def close(self):
+        if self.handle:
+            self._lib.dg_precond_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

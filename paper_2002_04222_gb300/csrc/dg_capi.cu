@@ -1,0 +1,651 @@
+// C ABI entry points: mesh set-up (1-D tables, metrics, connectivity checks),
+// residual, Jacobian-free product, GMRES, Newton and SDIRK orchestration.
+// The host drives the Krylov/Newton/SDIRK loops; every vector operation,
+// reduction and residual evaluation runs in the library's CUDA kernels.
+#include <cmath>
+#include <cstring>
+#include <cstdio>
+#include <new>
+#include <vector>
+#include "dg_internal.h"
+#include "dg_precond.h"
+
+namespace dg {
+
+dg_status cuda_status(cudaError_t e) {
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return DG_ERR_OOM;
+  }
+  return DG_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------- 1-D tables
+static void gauss_legendre(int Q, double* x, double* w) {
+  for (int i = 0; i < Q; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (Q + 0.5));
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= Q; ++k) {
+        double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      double pq = Q == 0 ? 1.0 : p1, pm = p0;
+      if (Q == 1) {
+        pq = z;
+        pm = 1.0;
+      }
+      double dp = Q * (z * pq - pm) / (z * z - 1.0);
+      double dz = pq / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) {
+        it = 100;
+      }
+    }
+    double p0 = 1.0, p1 = z;
+    for (int k = 2; k <= Q; ++k) {
+      double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k;
+      p0 = p1;
+      p1 = p2;
+    }
+    double pq = Q == 1 ? z : p1, pm = Q == 1 ? 1.0 : p0;
+    double dp = Q * (z * pq - pm) / (z * z - 1.0);
+    x[Q - 1 - i] = z;
+    w[Q - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+// Jacobi P_n^(1,1)(x) and derivative
+static void jacobi11(int n, double x, double* p, double* dp) {
+  auto val = [](int n, double a, double b, double x) {
+    if (n == 0) return 1.0;
+    double p0 = 1.0, p1 = 0.5 * ((a - b) + (a + b + 2.0) * x);
+    for (int k = 1; k < n; ++k) {
+      double c = 2.0 * k + a + b;
+      double a1 = 2.0 * (k + 1) * (k + a + b + 1) * c;
+      double a2 = (c + 1) * (a * a - b * b);
+      double a3 = c * (c + 1) * (c + 2);
+      double a4 = 2.0 * (k + a) * (k + b) * (c + 2);
+      double p2 = ((a2 + a3 * x) * p1 - a4 * p0) / a1;
+      p0 = p1;
+      p1 = p2;
+    }
+    return p1;
+  };
+  *p = val(n, 1.0, 1.0, x);
+  *dp = n == 0 ? 0.0 : 0.5 * (n + 3) * val(n - 1, 2.0, 2.0, x);
+}
+
+// modified basis psi_k(x) and derivative, k = 0..P
+static void modified_basis(int P, double x, double* phi, double* dphi) {
+  phi[0] = 0.5 * (1 - x);
+  dphi[0] = -0.5;
+  phi[P] = 0.5 * (1 + x);
+  dphi[P] = 0.5;
+  for (int p = 1; p < P; ++p) {
+    double j, dj;
+    jacobi11(p - 1, x, &j, &dj);
+    double b = 0.25 * (1 - x) * (1 + x);
+    phi[p] = b * j;
+    dphi[p] = -0.5 * x * j + b * dj;
+  }
+}
+
+static bool invert_small(int n, const double* A, double* Ainv) {
+  std::vector<double> M(A, A + n * n), I(n * n, 0.0);
+  for (int i = 0; i < n; ++i) I[i * n + i] = 1.0;
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (std::fabs(M[r * n + c]) > std::fabs(M[piv * n + c])) piv = r;
+    if (M[piv * n + c] == 0.0) return false;
+    for (int k = 0; k < n; ++k) {
+      std::swap(M[c * n + k], M[piv * n + k]);
+      std::swap(I[c * n + k], I[piv * n + k]);
+    }
+    double d = 1.0 / M[c * n + c];
+    for (int k = 0; k < n; ++k) {
+      M[c * n + k] *= d;
+      I[c * n + k] *= d;
+    }
+    for (int r = 0; r < n; ++r) {
+      if (r == c) continue;
+      double f = M[r * n + c];
+      if (f == 0.0) continue;
+      for (int k = 0; k < n; ++k) {
+        M[r * n + k] -= f * M[c * n + k];
+        I[r * n + k] -= f * I[c * n + k];
+      }
+    }
+  }
+  std::memcpy(Ainv, I.data(), sizeof(double) * n * n);
+  return true;
+}
+
+static void build_tables(int P, int Q, Tables& t) {
+  std::memset(&t, 0, sizeof(t));
+  const int n = P + 1;
+  t.n = n;
+  t.q = Q;
+  gauss_legendre(Q, t.x, t.w);
+  double phi[NMAX], dphi[NMAX];
+  for (int q = 0; q < Q; ++q) {
+    modified_basis(P, t.x[q], phi, dphi);
+    for (int k = 0; k < n; ++k) t.B[q * n + k] = phi[k];
+  }
+  // barycentric weights of the Gauss points
+  double bw[QMAX];
+  for (int k = 0; k < Q; ++k) {
+    double p = 1.0;
+    for (int j = 0; j < Q; ++j)
+      if (j != k) p *= (t.x[k] - t.x[j]);
+    bw[k] = 1.0 / p;
+  }
+  for (int i = 0; i < Q; ++i) {
+    double diag = 0.0;
+    for (int k = 0; k < Q; ++k) {
+      if (k == i) continue;
+      double d = (bw[k] / bw[i]) / (t.x[i] - t.x[k]);
+      t.Dq[i * Q + k] = d;
+      diag -= d;
+    }
+    t.Dq[i * Q + i] = diag;
+  }
+  for (int k = 0; k < Q; ++k) {
+    double am = 1.0, ap = 1.0;
+    for (int j = 0; j < Q; ++j) {
+      if (j == k) continue;
+      am *= (-1.0 - t.x[j]) / (t.x[k] - t.x[j]);
+      ap *= (1.0 - t.x[j]) / (t.x[k] - t.x[j]);
+    }
+    t.lm[k] = am;
+    t.lp[k] = ap;
+  }
+  double M1[NMAX * NMAX];
+  for (int a = 0; a < n; ++a)
+    for (int b = 0; b < n; ++b) {
+      double s = 0.0;
+      for (int q = 0; q < Q; ++q) s += t.B[q * n + a] * t.w[q] * t.B[q * n + b];
+      M1[a * n + b] = s;
+    }
+  invert_small(n, M1, t.Minv);
+  modified_basis(P, -1.0, phi, dphi);
+  for (int k = 0; k < n; ++k) t.dpm[k] = dphi[k];
+  modified_basis(P, 1.0, phi, dphi);
+  for (int k = 0; k < n; ++k) t.dpp[k] = dphi[k];
+}
+
+}  // namespace dg
+
+using namespace dg;
+
+extern "C" {
+
+const char* dg_status_string(dg_status s) {
+  switch (s) {
+    case DG_OK: return "ok";
+    case DG_ERR_ARG: return "invalid argument";
+    case DG_ERR_CUDA: return "CUDA error";
+    case DG_ERR_OOM: return "out of device memory";
+    case DG_ERR_NONFINITE: return "non-finite norm";
+    case DG_ERR_NOT_CONVERGED: return "iteration cap reached without convergence";
+    case DG_ERR_UNSUPPORTED: return "unsupported configuration";
+    case DG_ERR_TIMEOUT: return "device wait timed out";
+  }
+  return "unknown status";
+}
+
+static void free_mesh(dg_mesh_s* m) {
+  if (!m) return;
+  cudaFree(m->geo);
+  cudaFree(m->faces);
+  cudaFree(m->hbuf);
+  cudaFree(m->tbuf);
+  cudaFree(m->fbuf);
+  cudaFree(m->force);
+  cudaFree(m->scratch);
+  cudaFree(m->red);
+  cudaFree(m->w1);
+  cudaFree(m->w2);
+  cudaFree(m->krylov);
+  cudaFree(m->hdev);
+  cudaFree(m->stage);
+  if (m->hhost) cudaFreeHost(m->hhost);
+  delete m;
+}
+
+dg_status dg_mesh_create(const dg_mesh_desc* md, const dg_physics* ph, void* stream,
+                         dg_mesh_t* out) {
+  if (!md || !ph || !out || !md->nodes || !md->faces) return DG_ERR_ARG;
+  *out = nullptr;
+  const int d = md->dim;
+  if (d != 2 && d != 3) return DG_ERR_ARG;
+  if (md->P < 1 || md->Q < 1 || md->n_elem < 1 || md->n_faces < 1) return DG_ERR_ARG;
+  if (md->P + 1 > NMAX || md->Q > QMAX) return DG_ERR_UNSUPPORTED;
+  if (md->geom_order != 1) return DG_ERR_UNSUPPORTED;
+  if (!supported(d, md->P, md->Q)) return DG_ERR_UNSUPPORTED;
+  if (ph->n_bc < 0 || ph->n_bc > 8) return DG_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int E = md->n_elem, F = md->n_faces;
+  // geometry: axis-aligned boxes only
+  std::vector<ElemGeo> geo(E);
+  const int nn = 1 << d;
+  for (int e = 0; e < E; ++e) {
+    const double* X = md->nodes + (size_t)e * nn * d;
+    ElemGeo g{};
+    for (int r = 0; r < d; ++r) {
+      g.x0[r] = X[r];
+      g.h[r] = X[(1 << r) * d + r] - X[r];
+      if (!(g.h[r] > 0.0)) return DG_ERR_UNSUPPORTED;
+    }
+    for (int a = 0; a < nn; ++a)
+      for (int r = 0; r < d; ++r) {
+        double expect = g.x0[r] + (((a >> r) & 1) ? g.h[r] : 0.0);
+        if (std::fabs(X[a * d + r] - expect) > 1e-12 * (1.0 + std::fabs(expect)))
+          return DG_ERR_UNSUPPORTED;
+      }
+    geo[e] = g;
+  }
+  // connectivity: every (element, local face) exactly once, aligned sides
+  std::vector<int> seen((size_t)E * 2 * d, 0);
+  for (int f = 0; f < F; ++f) {
+    const int32_t* fc = md->faces + (size_t)f * 6;
+    int eL = fc[0], fL = fc[1], eR = fc[2], fR = fc[3], orient = fc[4], bc = fc[5];
+    if (eL < 0 || eL >= E || fL < 0 || fL >= 2 * d) return DG_ERR_ARG;
+    if (orient != 0) return DG_ERR_UNSUPPORTED;
+    seen[(size_t)eL * 2 * d + fL]++;
+    if (eR >= 0) {
+      if (eR >= E || fR < 0 || fR >= 2 * d) return DG_ERR_ARG;
+      if ((fR >> 1) != (fL >> 1) || (fR & 1) == (fL & 1)) return DG_ERR_UNSUPPORTED;
+      seen[(size_t)eR * 2 * d + fR]++;
+    } else {
+      if (bc < 0 || bc >= ph->n_bc) return DG_ERR_ARG;
+      int t = ph->bc[bc];
+      if (t != DG_BC_DIRICHLET && t != DG_BC_ISO_WALL) return DG_ERR_UNSUPPORTED;
+    }
+  }
+  for (size_t i = 0; i < seen.size(); ++i)
+    if (seen[i] != 1) return DG_ERR_ARG;
+
+  dg_mesh_s* m = new (std::nothrow) dg_mesh_s();
+  if (!m) return DG_ERR_OOM;
+  m->dim = d;
+  m->P = md->P;
+  m->Q = md->Q;
+  m->E = E;
+  m->F = F;
+  m->nv = d + 2;
+  const int n = md->P + 1;
+  m->nm = d == 2 ? n * n : n * n * n;
+  m->nq = d == 2 ? md->Q * md->Q : md->Q * md->Q * md->Q;
+  m->nf = d == 2 ? md->Q : md->Q * md->Q;
+  m->ndof = (long long)E * m->nv * m->nm;
+  build_tables(md->P, md->Q, m->tab);
+  Phys& p = m->phys;
+  std::memset(&p, 0, sizeof(p));
+  p.gamma = ph->gamma;
+  p.gm1 = ph->gamma - 1.0;
+  p.Pr = ph->Pr;
+  p.Ma = ph->Ma;
+  p.Re = ph->Re;
+  p.mu = 1.0 / ph->Re;
+  p.kappa_fac = 1.0 / (ph->Ma * ph->Ma * ph->Pr * (ph->gamma - 1.0));
+  p.T_inf_K = ph->T_inf_K;
+  p.beta_s = ph->beta_s;
+  p.gMa2 = ph->gamma * ph->Ma * ph->Ma;
+  p.viscous = ph->viscous;
+  p.mu_law = ph->mu_law;
+  p.riemann = ph->riemann;
+  p.forcing = ph->forcing;
+  p.field = ph->field;
+  for (int i = 0; i < 8; ++i) {
+    p.fpar[i] = ph->fpar[i];
+    p.bc[i] = ph->bc[i];
+  }
+  const size_t nd = (size_t)m->ndof;
+  const size_t ntr = (size_t)E * 2 * d * (1 + d) * m->nv * m->nf;
+  cudaError_t err = cudaSuccess;
+  auto alloc = [&](void** ptr, size_t bytes) {
+    if (err == cudaSuccess) err = cudaMalloc(ptr, bytes);
+  };
+  alloc((void**)&m->geo, sizeof(ElemGeo) * E);
+  alloc((void**)&m->faces, sizeof(int32_t) * 6 * F);
+  alloc((void**)&m->hbuf, sizeof(double) * (size_t)E * d * m->nv * m->nq);
+  alloc((void**)&m->tbuf, sizeof(double) * ntr);
+  alloc((void**)&m->fbuf, sizeof(double) * ntr);
+  alloc((void**)&m->scratch, sizeof(double) * 64);
+  alloc((void**)&m->red, sizeof(double) * RED_BLOCKS * 64);
+  alloc((void**)&m->w1, sizeof(double) * nd);
+  alloc((void**)&m->w2, sizeof(double) * nd);
+  if (ph->forcing) alloc((void**)&m->force, sizeof(double) * nd);
+  if (err != cudaSuccess) {
+    free_mesh(m);
+    return cuda_status(err);
+  }
+  err = cudaMemcpyAsync(m->geo, geo.data(), sizeof(ElemGeo) * E, cudaMemcpyHostToDevice, s);
+  if (err == cudaSuccess)
+    err = cudaMemcpyAsync(m->faces, md->faces, sizeof(int32_t) * 6 * F, cudaMemcpyHostToDevice, s);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+  if (err != cudaSuccess) {
+    free_mesh(m);
+    return cuda_status(err);
+  }
+  if (ph->forcing) {
+    dg_status st = launch_project(m, 1, 0.0, m->force, s);
+    if (st != DG_OK) {
+      free_mesh(m);
+      return st;
+    }
+  }
+  *out = m;
+  return DG_OK;
+}
+
+dg_status dg_mesh_destroy(dg_mesh_t m) {
+  if (!m) return DG_ERR_ARG;
+  cudaError_t e = cudaDeviceSynchronize();
+  free_mesh(m);
+  return e == cudaSuccess ? DG_OK : cuda_status(e);
+}
+
+dg_status dg_mesh_info(dg_mesh_t m, dg_mesh_info_t* info) {
+  if (!m || !info) return DG_ERR_ARG;
+  info->dim = m->dim;
+  info->P = m->P;
+  info->Q = m->Q;
+  info->n_elem = m->E;
+  info->n_var = m->nv;
+  info->n_mode = m->nm;
+  info->n_quad = m->nq;
+  info->n_faces = m->F;
+  info->n_dof = m->ndof;
+  return DG_OK;
+}
+
+dg_status dg_project(dg_mesh_t m, double t, double* u, void* stream) {
+  if (!m || !u) return DG_ERR_ARG;
+  return launch_project(m, 0, t, u, (cudaStream_t)stream);
+}
+
+dg_status dg_residual(dg_mesh_t m, const double* u, double t, double* r, void* stream) {
+  if (!m || !u || !r || u == r) return DG_ERR_ARG;
+  EvalArgs a{};
+  a.u = u;
+  a.t = t;
+  a.out = r;
+  return launch_residual(m, a, (cudaStream_t)stream);
+}
+
+dg_status dg_jvp(dg_mesh_t m, const double* u, const double* r_u, double t, const double* v,
+                 double alpha, double beta, double* out, void* stream) {
+  if (!m || !u || !r_u || !v || !out) return DG_ERR_ARG;
+  if (out == u || out == r_u || out == v) return DG_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  DG_TRY(jvp_eps(u, v, m->ndof, m->red, m->scratch, s));
+  EvalArgs a{};
+  a.u = u;
+  a.v = v;
+  a.r_u = r_u;
+  a.eps = m->scratch;
+  a.alpha = alpha;
+  a.beta = beta;
+  a.t = t;
+  a.out = out;
+  return launch_residual(m, a, s);
+}
+
+// ---------------------------------------------------------------- GMRES
+static dg_status ensure_krylov(dg_mesh_s* m, int restart) {
+  if (m->krylov && m->krylov_m >= restart) return DG_OK;
+  cudaFree(m->krylov);
+  cudaFree(m->hdev);
+  if (m->hhost) cudaFreeHost(m->hhost);
+  m->krylov = nullptr;
+  m->hdev = nullptr;
+  m->hhost = nullptr;
+  const size_t nd = (size_t)m->ndof;
+  DG_CUDA(cudaMalloc(&m->krylov, sizeof(double) * nd * (2 * (size_t)restart + 1)));
+  DG_CUDA(cudaMalloc(&m->hdev, sizeof(double) * 4 * (restart + 2)));
+  DG_CUDA(cudaMallocHost(&m->hhost, sizeof(double) * 4 * (restart + 2)));
+  m->krylov_m = restart;
+  return DG_OK;
+}
+
+static dg_status host_norm(dg_mesh_s* m, const double* a, double* out, cudaStream_t s) {
+  DG_TRY(dot(a, a, m->ndof, m->red, m->hdev, s));
+  DG_CUDA(cudaMemcpyAsync(m->hhost, m->hdev, sizeof(double), cudaMemcpyDeviceToHost, s));
+  DG_CUDA(cudaStreamSynchronize(s));
+  *out = std::sqrt(m->hhost[0]);
+  if (!std::isfinite(*out)) return DG_ERR_NONFINITE;
+  return DG_OK;
+}
+
+// A z = z - dt_a (R(u + eps z) - r_u)/eps
+static dg_status apply_A(dg_mesh_s* m, const double* u, const double* r_u, double t, double dta,
+                         const double* z, double* out, cudaStream_t s) {
+  return dg_jvp(m, u, r_u, t, z, 1.0, -dta, out, s);
+}
+
+static dg_status gmres_impl(dg_mesh_s* m, dg_precond_s* p, const double* u, const double* r_u,
+                            double t, double dta, const double* b, double* x,
+                            const dg_gmres_cfg* cfg, dg_gmres_stats* st, cudaStream_t s) {
+  const int mr = cfg->restart;
+  const long long n = m->ndof;
+  DG_TRY(ensure_krylov(m, mr));
+  double* V = m->krylov;                       // (mr+1) vectors
+  double* Z = p ? V + (size_t)(mr + 1) * n : nullptr;  // mr vectors
+  dg_gmres_stats S{};
+  double bn;
+  DG_TRY(host_norm(m, b, &bn, s));
+  S.res0 = bn;
+  DG_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+  if (bn == 0.0) {
+    S.converged = 1;
+    if (st) *st = S;
+    return DG_OK;
+  }
+  const double tol = cfg->rtol * bn;
+  std::vector<double> H((size_t)(mr + 1) * mr), cs(mr), sn(mr), g(mr + 1), y(mr);
+  double* hd = m->hdev;
+  double* hh = m->hhost;
+  for (int cyc = 0; cyc < cfg->max_cycles; ++cyc) {
+    double beta;
+    if (cyc == 0) {
+      DG_CUDA(cudaMemcpyAsync(V, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+      beta = bn;
+    } else {
+      DG_TRY(apply_A(m, u, r_u, t, dta, x, m->w2, s));
+      DG_TRY(lincomb(V, b, 1.0, m->w2, -1.0, n, s));
+      DG_TRY(host_norm(m, V, &beta, s));
+    }
+    S.res = beta;
+    if (beta <= tol) {
+      S.converged = 1;
+      break;
+    }
+    S.cycles++;
+    DG_TRY(axpby(V, 1.0 / beta, V, 0.0, n, s));
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int kused = 0;
+    bool done = false;
+    for (int k = 0; k < mr; ++k) {
+      const double* vk = V + (size_t)k * n;
+      const double* zk = vk;
+      if (p) {
+        double* zz = Z + (size_t)k * n;
+        DG_TRY(precond_apply_impl(p, vk, zz, s));
+        zk = zz;
+      }
+      double* w = V + (size_t)(k + 1) * n;
+      DG_TRY(apply_A(m, u, r_u, t, dta, zk, w, s));
+      S.iters++;
+      // classical Gram-Schmidt, applied twice
+      DG_TRY(multi_dot(V, k + 1, w, n, m->red, hd, s));
+      DG_TRY(multi_axpy(w, V, k + 1, hd, n, s));
+      DG_TRY(multi_dot(V, k + 1, w, n, m->red, hd + (mr + 2), s));
+      DG_TRY(multi_axpy(w, V, k + 1, hd + (mr + 2), n, s));
+      DG_TRY(dot(w, w, n, m->red, hd + 2 * (mr + 2), s));
+      DG_CUDA(cudaMemcpyAsync(hh, hd, sizeof(double) * 3 * (mr + 2), cudaMemcpyDeviceToHost, s));
+      DG_CUDA(cudaStreamSynchronize(s));
+      const double hn = std::sqrt(hh[2 * (mr + 2)]);
+      if (!std::isfinite(hn)) return DG_ERR_NONFINITE;
+      for (int i = 0; i <= k; ++i) H[(size_t)i * mr + k] = hh[i] + hh[(mr + 2) + i];
+      H[(size_t)(k + 1) * mr + k] = hn;
+      if (hn > 0.0) DG_TRY(axpby(w, 1.0 / hn, w, 0.0, n, s));
+      for (int i = 0; i < k; ++i) {
+        double t0 = cs[i] * H[(size_t)i * mr + k] + sn[i] * H[(size_t)(i + 1) * mr + k];
+        H[(size_t)(i + 1) * mr + k] = -sn[i] * H[(size_t)i * mr + k] + cs[i] * H[(size_t)(i + 1) * mr + k];
+        H[(size_t)i * mr + k] = t0;
+      }
+      const double den = std::hypot(H[(size_t)k * mr + k], H[(size_t)(k + 1) * mr + k]);
+      cs[k] = H[(size_t)k * mr + k] / den;
+      sn[k] = H[(size_t)(k + 1) * mr + k] / den;
+      H[(size_t)k * mr + k] = den;
+      H[(size_t)(k + 1) * mr + k] = 0.0;
+      g[k + 1] = -sn[k] * g[k];
+      g[k] = cs[k] * g[k];
+      kused = k + 1;
+      S.res = std::fabs(g[k + 1]);
+      if (S.res <= tol || hn == 0.0) {
+        done = S.res <= tol;
+        break;
+      }
+    }
+    for (int i = kused - 1; i >= 0; --i) {
+      double acc = g[i];
+      for (int j = i + 1; j < kused; ++j) acc -= H[(size_t)i * mr + j] * y[j];
+      y[i] = acc / H[(size_t)i * mr + i];
+    }
+    // x += sum_i y_i z_i  (multi_axpy subtracts: pass -y)
+    for (int i = 0; i < kused; ++i) hh[i] = -y[i];
+    DG_CUDA(cudaMemcpyAsync(hd, hh, sizeof(double) * kused, cudaMemcpyHostToDevice, s));
+    DG_TRY(multi_axpy(x, p ? Z : V, kused, hd, n, s));
+    DG_CUDA(cudaStreamSynchronize(s));
+    if (done) {
+      S.converged = 1;
+      break;
+    }
+  }
+  if (st) *st = S;
+  return S.converged ? DG_OK : DG_ERR_NOT_CONVERGED;
+}
+
+dg_status dg_gmres(dg_mesh_t m, dg_precond_t p, const double* u, const double* r_u, double t,
+                   double dt_a, const double* b, double* x, const dg_gmres_cfg* cfg,
+                   dg_gmres_stats* stats, void* stream) {
+  if (!m || !u || !r_u || !b || !x || !cfg) return DG_ERR_ARG;
+  if (cfg->restart < 1 || cfg->max_cycles < 1 || !(cfg->rtol > 0.0)) return DG_ERR_ARG;
+  if (p && precond_mesh(p) != m) return DG_ERR_ARG;
+  return gmres_impl(m, p, u, r_u, t, dt_a, b, x, cfg, stats, (cudaStream_t)stream);
+}
+
+// ---------------------------------------------------------------- SDIRK
+static void tableau(int which, double A[3][3], double* b, double* c, int* M) {
+  std::memset(A, 0, sizeof(double) * 9);
+  if (which == DG_SDIRK3) {
+    const double l = 0.4358665215;
+    const double b1 = (-6 * l * l + 16 * l - 1) / 4, b2 = (6 * l * l - 20 * l + 5) / 4;
+    A[0][0] = l;
+    A[1][0] = (1 - l) / 2;
+    A[1][1] = l;
+    A[2][0] = b1;
+    A[2][1] = b2;
+    A[2][2] = l;
+    b[0] = b1;
+    b[1] = b2;
+    b[2] = l;
+    *M = 3;
+  } else {
+    const double l = 1.0 - std::sqrt(2.0) / 2.0;
+    A[0][0] = l;
+    A[1][0] = 1 - l;
+    A[1][1] = l;
+    b[0] = 1 - l;
+    b[1] = l;
+    *M = 2;
+  }
+  for (int i = 0; i < *M; ++i) {
+    c[i] = 0;
+    for (int j = 0; j <= i; ++j) c[i] += A[i][j];
+  }
+}
+
+dg_status sdirk_step(dg_mesh_t m, const dg_sdirk_cfg* cfg, double* u_n, double t, double dt,
+                     dg_precond_t* p_inout, dg_step_stats* stats, void* stream) {
+  if (!m || !cfg || !u_n || !(dt > 0.0)) return DG_ERR_ARG;
+  if (cfg->tableau != DG_SDIRK2 && cfg->tableau != DG_SDIRK3) return DG_ERR_ARG;
+  if (cfg->use_precond && !p_inout) return DG_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long n = m->ndof;
+  double A[3][3], b[3], c[3];
+  int M;
+  tableau(cfg->tableau, A, b, c, &M);
+  if (!m->stage) DG_CUDA(cudaMalloc(&m->stage, sizeof(double) * (size_t)n * 7));
+  double* Ev[3] = {m->stage, m->stage + n, m->stage + 2 * n};
+  double* Sv = m->stage + 3 * n;
+  double* U = m->stage + 4 * n;
+  double* R = m->stage + 5 * n;
+  double* Nn = m->stage + 6 * n;
+  double* dx = m->w1;
+  dg_step_stats st{};
+  st.stages = M;
+  dg_precond_s* P = nullptr;
+  if (cfg->use_precond) {
+    if (!*p_inout || cfg->rebuild) {
+      DG_TRY(dg_precond_build(m, u_n, t, dt * A[0][0], &cfg->prec, p_inout, s));
+      st.precond_built = 1;
+    }
+    P = *p_inout;
+  }
+  dg_status result = DG_OK;
+  for (int i = 0; i < M; ++i) {
+    // S_i = u^n + sum_{j<i} a_ij E^j
+    DG_CUDA(cudaMemcpyAsync(Sv, u_n, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    for (int j = 0; j < i; ++j) DG_TRY(axpby(Sv, A[i][j], Ev[j], 1.0, n, s));
+    DG_CUDA(cudaMemcpyAsync(U, Sv, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    const double ti = t + c[i] * dt, dta = dt * A[i][i];
+    DG_TRY(dg_residual(m, U, ti, R, s));
+    DG_TRY(newton_resid(Nn, U, Sv, R, dta, n, s));
+    double res;
+    DG_TRY(host_norm(m, Nn, &res, s));
+    const double res0 = res;
+    const double tol = cfg->abs_tol > 0.0 ? cfg->abs_tol : cfg->alpha * res0;
+    int it = 0, gits = 0;
+    bool conv = false;
+    while (true) {
+      if (res <= 0.0 || ((it > 0 || cfg->abs_tol > 0.0) && res < tol)) {
+        conv = true;
+        break;
+      }
+      if (it >= cfg->max_newton) break;
+      dg_gmres_stats gs{};
+      dg_status g = gmres_impl(m, P, U, R, ti, dta, Nn, dx, &cfg->gmres, &gs, s);
+      if (g != DG_OK && g != DG_ERR_NOT_CONVERGED) return g;
+      gits += gs.iters;
+      DG_TRY(axpby(U, 1.0, dx, 1.0, n, s));
+      ++it;
+      DG_TRY(dg_residual(m, U, ti, R, s));
+      DG_TRY(newton_resid(Nn, U, Sv, R, dta, n, s));
+      DG_TRY(host_norm(m, Nn, &res, s));
+    }
+    if (!conv) result = DG_ERR_NOT_CONVERGED;
+    st.newton_iters += it;
+    st.gmres_iters += gits;
+    if (i < 4) {
+      st.stage_newton[i] = it;
+      st.stage_gmres[i] = gits;
+      st.stage_res0[i] = res0;
+      st.stage_res[i] = res;
+    }
+    // E^i = dt R(u^i) from the residual of the converged iterate
+    DG_TRY(axpby(Ev[i], dt, R, 0.0, n, s));
+  }
+  for (int i = 0; i < M; ++i) DG_TRY(axpby(u_n, b[i], Ev[i], 1.0, n, s));
+  DG_CUDA(cudaStreamSynchronize(s));
+  if (stats) *stats = st;
+  return result;
+}
+
+}  // extern "C"

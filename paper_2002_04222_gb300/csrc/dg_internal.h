@@ -1,0 +1,120 @@
+// Internal definitions shared by the CUDA translation units of the DG library.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+#include <vector>
+#include "../../include/dg.h"
+
+namespace dg {
+
+constexpr int QMAX = 8;   // largest Gauss point count per direction
+constexpr int NMAX = 7;   // largest (P+1)
+
+// 1-D tables of one (P, Q) pair, passed by value to the kernels.
+struct Tables {
+  double B[QMAX * NMAX];      // B[q*n + k] = psi_k(x_q)
+  double Dq[QMAX * QMAX];     // Dq[q*Q + k] = l_k'(x_q): collocation derivative on the Gauss points
+  double w[QMAX];             // Gauss weights
+  double x[QMAX];             // Gauss points
+  double lm[QMAX], lp[QMAX];  // Lagrange extrapolation weights to xi = -1 and xi = +1
+  double Minv[NMAX * NMAX];   // inverse of the 1-D mass matrix B^T diag(w) B
+  double dpm[NMAX], dpp[NMAX];// psi_k'(-1), psi_k'(+1)
+  int n, q;
+};
+
+// Physical model on the device (copy of dg_physics with derived constants).
+struct Phys {
+  double gamma, gm1, Pr, Ma, Re, mu, kappa_fac, T_inf_K, beta_s, gMa2;
+  int viscous, mu_law, riemann, forcing, field;
+  double fpar[8];
+  int bc[8];
+};
+
+// Element geometry of an axis-aligned affine element: origin and edge lengths.
+struct ElemGeo {
+  double x0[3];
+  double h[3];
+};
+
+}  // namespace dg
+
+struct dg_precond_s;
+
+struct dg_mesh_s {
+  int dim, P, Q, E, nv, nm, nq, nf, F;
+  long long ndof;
+  dg::Tables tab;
+  dg::Phys phys;
+  // device buffers
+  dg::ElemGeo* geo = nullptr;   // [E]
+  int32_t* faces = nullptr;     // [F][6]
+  double* hbuf = nullptr;       // [E][dim][nv][nq]   weighted volume fluxes
+  double* tbuf = nullptr;       // [E][2dim][(1+dim)nv][nf] face traces
+  double* fbuf = nullptr;       // [E][2dim][(1+dim)nv][nf] face fluxes to lift
+  double* force = nullptr;      // [ndof] M^-1 B^T wJ f (nullptr when no forcing)
+  double* scratch = nullptr;    // [4] eps, 1/eps, ...
+  double* red = nullptr;        // reduction partials
+  double* w1 = nullptr;         // work vectors of ndof
+  double* w2 = nullptr;
+  // GMRES workspace (lazily sized)
+  double* krylov = nullptr;     // V[(m+1)][ndof] then Z[m][ndof]
+  int krylov_m = 0;
+  double* hdev = nullptr;       // [2*(mmax+2)] Hessenberg column on device
+  double* hhost = nullptr;      // pinned host mirror
+  // SDIRK workspace
+  double* stage = nullptr;      // [4 + 3][ndof]: E^0..E^3, S, R, N
+  std::vector<std::vector<int>> elem_faces;  // host: face id of (e, lf)
+  // cached norms of the JFNK base point
+  const double* jvp_u = nullptr;
+};
+
+namespace dg {
+
+// error plumbing
+dg_status cuda_status(cudaError_t e);
+#define DG_CUDA(call)                                   \
+  do {                                                  \
+    cudaError_t _e = (call);                            \
+    if (_e != cudaSuccess) return ::dg::cuda_status(_e); \
+  } while (0)
+#define DG_TRY(call)                 \
+  do {                               \
+    dg_status _s = (call);           \
+    if (_s != DG_OK) return _s;      \
+  } while (0)
+
+// residual pipeline (dg_residual.cu)
+enum EvalMode { EVAL_RESIDUAL = 0, EVAL_JVP = 1 };
+struct EvalArgs {
+  const double* u;     // base state
+  const double* v;     // JVP direction (nullptr for a plain residual)
+  const double* r_u;   // R(u) (JVP only)
+  const double* eps;   // device scalars {eps, 1/eps} (JVP only)
+  double alpha, beta;  // JVP combination
+  double t;
+  double* out;
+};
+dg_status launch_residual(dg_mesh_s* m, const EvalArgs& a, cudaStream_t s);
+dg_status launch_project(dg_mesh_s* m, int what, double t, double* out, cudaStream_t s);
+bool supported(int dim, int P, int Q);
+
+// dense vector kernels (dg_blas.cu)
+constexpr int RED_BLOCKS = 296;   // 2 per SM: fixed, so reductions repeat bitwise
+dg_status dot(const double* a, const double* b, long long n, double* partial, double* out,
+              cudaStream_t s);
+dg_status multi_dot(const double* V, int k, const double* w, long long n, double* partial,
+                    double* out, cudaStream_t s);
+dg_status multi_axpy(double* w, const double* V, int k, const double* h, long long n,
+                     cudaStream_t s);  // w -= sum_i h_i V_i
+dg_status axpby(double* y, double a, const double* x, double b, long long n, cudaStream_t s);
+dg_status lincomb(double* y, const double* x, double a, const double* z, double b, long long n,
+                  cudaStream_t s);  // y = a x + b z
+dg_status scale_dev(double* y, const double* x, const double* sdev, int inv, long long n,
+                    cudaStream_t s);
+dg_status jvp_eps(const double* u, const double* v, long long n, double* partial, double* eps,
+                  cudaStream_t s);
+dg_status newton_resid(double* N, const double* u, const double* S, const double* R, double dta,
+                       long long n, cudaStream_t s);
+
+}  // namespace dg

@@ -1,0 +1,370 @@
+// Device-side physics of the compressible Navier-Stokes equations (Sec. 2.1)
+// and the numerical fluxes of Sec. 3.1, templated on the scalar type so that
+// the volume flux can also be differentiated exactly with dual numbers.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+#include "dg_internal.h"
+
+namespace dg {
+
+// ------------------------------------------------------------ dual numbers
+// Forward-mode derivative carrier: v + d*e with e^2 = 0.
+struct Dual {
+  double v, d;
+  __host__ __device__ Dual() : v(0), d(0) {}
+  __host__ __device__ Dual(double a) : v(a), d(0) {}
+  __host__ __device__ Dual(double a, double b) : v(a), d(b) {}
+};
+__host__ __device__ inline Dual operator+(Dual a, Dual b) { return Dual(a.v + b.v, a.d + b.d); }
+__host__ __device__ inline Dual operator-(Dual a, Dual b) { return Dual(a.v - b.v, a.d - b.d); }
+__host__ __device__ inline Dual operator-(Dual a) { return Dual(-a.v, -a.d); }
+__host__ __device__ inline Dual operator*(Dual a, Dual b) { return Dual(a.v * b.v, a.d * b.v + a.v * b.d); }
+__host__ __device__ inline Dual operator/(Dual a, Dual b) {
+  double q = a.v / b.v;
+  return Dual(q, (a.d - q * b.d) / b.v);
+}
+__host__ __device__ inline Dual& operator+=(Dual& a, Dual b) { a = a + b; return a; }
+__host__ __device__ inline Dual& operator-=(Dual& a, Dual b) { a = a - b; return a; }
+__host__ __device__ inline Dual& operator*=(Dual& a, Dual b) { a = a * b; return a; }
+__device__ inline Dual dsqrt(Dual a) {
+  double s = sqrt(a.v);
+  return Dual(s, 0.5 * a.d / s);
+}
+__device__ inline double dsqrt(double a) { return sqrt(a); }
+__device__ inline double val(double a) { return a; }
+__device__ inline double val(Dual a) { return a.v; }
+
+// ------------------------------------------------------------ state helpers
+template <int D, typename T>
+__device__ inline void primitives(const T* U, const Phys& ph, T& irho, T* vel, T& p, T& temp) {
+  irho = T(1.0) / U[0];
+  T ke = T(0.0);
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    vel[k] = U[1 + k] * irho;
+    ke += U[1 + k] * vel[k];
+  }
+  p = T(ph.gm1) * (U[D + 1] - T(0.5) * ke);
+  temp = T(ph.gMa2) * p * irho;
+}
+
+template <typename T>
+__device__ inline T viscosity(const T& temp, const Phys& ph) {
+  if (ph.mu_law == 0) return T(ph.mu);
+  double s = 110.0 / ph.T_inf_K;
+  return temp * dsqrt(temp) * T(ph.mu * (1.0 + s)) / (temp + T(s));
+}
+
+// Advection flux F[i][v] of Eq. (conserved fluxes).
+template <int D, typename T>
+__device__ inline void euler_flux(const T* U, const Phys& ph, T F[D][D + 2]) {
+  T irho, vel[D], p, temp;
+  primitives<D>(U, ph, irho, vel, p, temp);
+  T Ep = U[D + 1] + p;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    F[i][0] = U[1 + i];
+#pragma unroll
+    for (int k = 0; k < D; ++k) F[i][1 + k] = U[1 + i] * vel[k];
+    F[i][1 + i] += p;
+    F[i][D + 1] = vel[i] * Ep;
+  }
+}
+
+// Diffusion flux G[i][v] of Eq. (conserved fluxes) from the physical gradient
+// dU[j][v] of the conservative variables (linear in dU at fixed U).
+template <int D, typename T, typename TG>
+__device__ inline void viscous_flux(const T* U, const TG dU[D][D + 2], const Phys& ph,
+                                    T G[D][D + 2]) {
+  T irho, vel[D], p, temp;
+  primitives<D>(U, ph, irho, vel, p, temp);
+  T mu = viscosity(temp, ph);
+  T e = U[D + 1] * irho;
+  T dvel[D][D], dT[D];
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    T de = (T(dU[j][D + 1]) - e * T(dU[j][0])) * irho;
+    T s = de;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      dvel[j][k] = (T(dU[j][1 + k]) - vel[k] * T(dU[j][0])) * irho;
+      s -= dvel[j][k] * vel[k];
+    }
+    dT[j] = T(ph.gMa2 * ph.gm1) * s;
+  }
+  T div = T(0.0);
+#pragma unroll
+  for (int k = 0; k < D; ++k) div += dvel[k][k];
+  T kap = mu * T(ph.kappa_fac);
+  T twothird = T(2.0 / 3.0) * mu * div;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    G[i][0] = T(0.0);
+    T en = kap * dT[i];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      T tau = mu * (dvel[k][i] + dvel[i][k]);
+      if (i == k) tau -= twothird;
+      G[i][1 + k] = tau;
+      en += vel[k] * tau;
+    }
+    G[i][D + 1] = en;
+  }
+}
+
+// Normal Euler flux F(U).n
+template <int D>
+__device__ inline void euler_flux_n(const double* U, const double* n, const Phys& ph,
+                                    double* Fn, double& p_out, double* vel_out) {
+  double irho, vel[D], p, temp;
+  primitives<D>(U, ph, irho, vel, p, temp);
+  double un = 0.0;
+#pragma unroll
+  for (int k = 0; k < D; ++k) un += vel[k] * n[k];
+  Fn[0] = U[0] * un;
+#pragma unroll
+  for (int k = 0; k < D; ++k) Fn[1 + k] = U[1 + k] * un + p * n[k];
+  Fn[D + 1] = (U[D + 1] + p) * un;
+  p_out = p;
+#pragma unroll
+  for (int k = 0; k < D; ++k) vel_out[k] = vel[k];
+}
+
+// Roe's approximate Riemann flux without entropy fix (Toro, Ch. 11).
+template <int D>
+__device__ inline void roe_flux(const double* UL, const double* UR, const double* n,
+                                const Phys& ph, double* Fh) {
+  double FL[D + 2], FR[D + 2], vL[D], vR[D], pL, pR;
+  euler_flux_n<D>(UL, n, ph, FL, pL, vL);
+  euler_flux_n<D>(UR, n, ph, FR, pR, vR);
+  double rL = UL[0], rR = UR[0];
+  double HL = (UL[D + 1] + pL) / rL, HR = (UR[D + 1] + pR) / rR;
+  double sL = sqrt(rL), sR = sqrt(rR);
+  double rt = sL * sR;
+  double isum = 1.0 / (sL + sR);
+  double ut[D], du[D], q2 = 0, unt = 0, dun = 0, udu = 0;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    ut[k] = (sL * vL[k] + sR * vR[k]) * isum;
+    du[k] = vR[k] - vL[k];
+    q2 += ut[k] * ut[k];
+    unt += ut[k] * n[k];
+    dun += du[k] * n[k];
+    udu += ut[k] * du[k];
+  }
+  double Ht = (sL * HL + sR * HR) * isum;
+  double c2 = ph.gm1 * (Ht - 0.5 * q2);
+  double c = sqrt(c2);
+  double ic2 = 1.0 / c2;
+  double dr = rR - rL, dp = pR - pL;
+  double a1 = (dp - rt * c * dun) * 0.5 * ic2;
+  double a5 = (dp + rt * c * dun) * 0.5 * ic2;
+  double a2 = dr - dp * ic2;
+  double l1 = fabs(unt - c), l2 = fabs(unt), l5 = fabs(unt + c);
+  double w1 = l1 * a1, w5 = l5 * a5, w2 = l2 * a2, ws = l2 * rt;
+  Fh[0] = 0.5 * (FL[0] + FR[0]) - 0.5 * (w1 + w2 + w5);
+#pragma unroll
+  for (int k = 0; k < D; ++k)
+    Fh[1 + k] = 0.5 * (FL[1 + k] + FR[1 + k]) -
+                0.5 * (w1 * (ut[k] - c * n[k]) + w5 * (ut[k] + c * n[k]) + w2 * ut[k] +
+                       ws * (du[k] - dun * n[k]));
+  Fh[D + 1] = 0.5 * (FL[D + 1] + FR[D + 1]) -
+              0.5 * (w1 * (Ht - unt * c) + w5 * (Ht + unt * c) + w2 * 0.5 * q2 +
+                     ws * (udu - unt * dun));
+}
+
+// HLLC flux (Toro, Ch. 10) with Einfeldt (Roe-averaged) wave speeds.
+template <int D>
+__device__ inline void hllc_flux(const double* UL, const double* UR, const double* n,
+                                 const Phys& ph, double* Fh) {
+  double FL[D + 2], FR[D + 2], vL[D], vR[D], pL, pR;
+  euler_flux_n<D>(UL, n, ph, FL, pL, vL);
+  euler_flux_n<D>(UR, n, ph, FR, pR, vR);
+  double rL = UL[0], rR = UR[0];
+  double cL = sqrt(ph.gamma * pL / rL), cR = sqrt(ph.gamma * pR / rR);
+  double HL = (UL[D + 1] + pL) / rL, HR = (UR[D + 1] + pR) / rR;
+  double sL = sqrt(rL), sR = sqrt(rR);
+  double isum = 1.0 / (sL + sR);
+  double q2 = 0, unt = 0, unL = 0, unR = 0;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    double u = (sL * vL[k] + sR * vR[k]) * isum;
+    q2 += u * u;
+    unt += u * n[k];
+    unL += vL[k] * n[k];
+    unR += vR[k] * n[k];
+  }
+  double Ht = (sL * HL + sR * HR) * isum;
+  double ct = sqrt(ph.gm1 * (Ht - 0.5 * q2));
+  double SL = fmin(unL - cL, unt - ct);
+  double SR = fmax(unR + cR, unt + ct);
+  double Ss = (pR - pL + rL * unL * (SL - unL) - rR * unR * (SR - unR)) /
+              (rL * (SL - unL) - rR * (SR - unR));
+  if (SL >= 0.0) {
+#pragma unroll
+    for (int v = 0; v < D + 2; ++v) Fh[v] = FL[v];
+  } else if (Ss < 0.0 && SR <= 0.0) {
+#pragma unroll
+    for (int v = 0; v < D + 2; ++v) Fh[v] = FR[v];
+  } else {
+    const bool left = Ss >= 0.0;
+    const double* U = left ? UL : UR;
+    const double* F = left ? FL : FR;
+    const double* vv = left ? vL : vR;
+    double r = left ? rL : rR, p = left ? pL : pR, un = left ? unL : unR, S = left ? SL : SR;
+    double f = r * (S - un) / (S - Ss);
+    double st[D + 2];
+    st[0] = f;
+#pragma unroll
+    for (int k = 0; k < D; ++k) st[1 + k] = f * (vv[k] + (Ss - un) * n[k]);
+    st[D + 1] = f * (U[D + 1] / r + (Ss - un) * (Ss + p / (r * (S - un))));
+#pragma unroll
+    for (int v = 0; v < D + 2; ++v) Fh[v] = F[v] + S * (st[v] - U[v]);
+  }
+}
+
+template <int D>
+__device__ inline void riemann_flux(const double* UL, const double* UR, const double* n,
+                                    const Phys& ph, double* Fh) {
+  if (ph.riemann == DG_RIEMANN_HLLC)
+    hllc_flux<D>(UL, UR, n, ph, Fh);
+  else
+    roe_flux<D>(UL, UR, n, ph, Fh);
+}
+
+// ------------------------------------------------------------ analytic fields
+__device__ inline void conservative_from(int D, double rho, const double* vel, double temp,
+                                         const Phys& ph, double* U) {
+  double p = rho * temp / ph.gMa2;
+  double ke = 0;
+  U[0] = rho;
+  for (int k = 0; k < D; ++k) {
+    U[1 + k] = rho * vel[k];
+    ke += vel[k] * vel[k];
+  }
+  U[D + 1] = p / ph.gm1 + 0.5 * rho * ke;
+}
+
+// State of the workload's analytic field at x (Sec. 6.1 vortex with the
+// sign of the u perturbation that makes it a vortex; manufactured
+// Poiseuille; Taylor-Green vortex; uniform stream).
+__device__ inline void exact_state(int D, const Phys& ph, const double* x, double t, double* U) {
+  double rho = 1.0, temp = 1.0, vel[3] = {0.0, 0.0, 0.0};
+  const double PI = 3.14159265358979323846;
+  if (ph.field == DG_FIELD_VORTEX) {
+    double u0 = ph.fpar[0], v0 = ph.fpar[1], phi = ph.fpar[2], xc = ph.fpar[3], yc = ph.fpar[4],
+           s = ph.fpar[5];
+    double dx = x[0] - (xc + u0 * t), dy = x[1] - (yc + v0 * t);
+    dx -= rint(dx);
+    dy -= rint(dy);
+    double X = s * dx, Y = s * dy;
+    double ex = exp(1.0 - X * X - Y * Y);
+    vel[0] = u0 - phi / (2 * PI) * Y * ex;
+    vel[1] = v0 + phi / (2 * PI) * X * ex;
+    temp = 1.0 - ph.gm1 * ph.Ma * ph.Ma * phi * phi / (16 * PI * PI) * ex * ex;
+    rho = pow(temp, 1.0 / ph.gm1);
+  } else if (ph.field == DG_FIELD_POISEUILLE) {
+    double theta = ph.fpar[0], L = ph.fpar[1], dpdx = ph.fpar[2];
+    double y = x[1];
+    vel[0] = -dpdx / (2 * ph.mu) * (y * (L - y) + theta * y * y * (L - y) * (L - y));
+    double p = 1.0 / ph.gMa2 + dpdx * x[0];
+    rho = 1.0;
+    temp = ph.gMa2 * p / rho;
+  } else if (ph.field == DG_FIELD_TGV) {
+    double X = x[0], Y = x[1], Z = x[2];
+    vel[0] = sin(X) * cos(Y) * cos(Z);
+    vel[1] = -cos(X) * sin(Y) * cos(Z);
+    double pinf = 1.0 / ph.gMa2;
+    double p = pinf + (cos(2 * X) + cos(2 * Y)) * (cos(2 * Z) + 2.0) / 16.0;
+    rho = p / pinf;
+    temp = 1.0;
+  } else {  // uniform / cylinder free stream
+    vel[0] = 1.0;
+  }
+  conservative_from(D, rho, vel, temp, ph, U);
+}
+
+// Manufactured source of the compressible Poiseuille case (App. B) with the
+// energy component built on h(y) = y(L-y) + theta y^2 (L-y)^2.
+__device__ inline void forcing(int D, const Phys& ph, const double* x, double* f) {
+  for (int v = 0; v < D + 2; ++v) f[v] = 0.0;
+  if (ph.forcing != DG_FORCING_POISEUILLE) return;
+  double theta = ph.fpar[0], L = ph.fpar[1], dpdx = ph.fpar[2], mu = ph.mu;
+  double y = x[1];
+  double c = L * L - 6 * y * L + 6 * y * y;
+  double h = y * (L - y) + theta * y * y * (L - y) * (L - y);
+  double q = 2 * theta * y * L - 2 * theta * y * y + 1;
+  f[1] = dpdx * theta * c;
+  f[D + 1] = dpdx * dpdx / (2 * mu) * h * (1 - theta * c - ph.gamma / ph.gm1) -
+             dpdx * dpdx / (4 * mu) * (L - 2 * y) * (L - 2 * y) * q * q;
+}
+
+__device__ inline double wall_temperature(const Phys& ph, const double* x) {
+  if (ph.field == DG_FIELD_POISEUILLE) return 1.0 + ph.gMa2 * ph.fpar[2] * x[0];
+  return 1.0;
+}
+
+// Weakly imposed boundary state (exterior state of the Riemann flux and the
+// state of the viscous boundary flux).
+template <int D>
+__device__ inline void boundary_state(int bctype, const Phys& ph, const double* x, double t,
+                                      const double* UL, double* UB) {
+  if (bctype == DG_BC_ISO_WALL) {
+    double Tw = wall_temperature(ph, x);
+    UB[0] = UL[0];
+#pragma unroll
+    for (int k = 0; k < D; ++k) UB[1 + k] = 0.0;
+    UB[D + 1] = UL[0] * Tw / (ph.gamma * ph.gm1 * ph.Ma * ph.Ma);
+  } else {  // DG_BC_DIRICHLET
+    exact_state(D, ph, x, t, UB);
+  }
+}
+
+// Numerical normal flux H^n = F^n - G^n on a face with owner-side normal
+// n = sgn e_r (Sec. 3.1, with the adjoint-consistent interior penalty):
+//   S_i  = G_i({Q}, n (x) [Q]),  [Q] = Q_L - Q_R,
+//   G^n  = n . (G({Q}, {grad Q}) - beta_p S),
+// where on a boundary face Q_R = {Q} = the boundary state built from Q_L and
+// {grad Q} is the interior gradient.  dQa is the face-average gradient.
+template <int D>
+__device__ inline void numerical_flux(const double* QL, const double* QRin, int bctype,
+                                      const double* x, double t, const double dQa[D][D + 2],
+                                      int r, double sgn, double beta, const Phys& ph,
+                                      double* Hn, double S[D][D + 2]) {
+  constexpr int NV = D + 2;
+  double QR[NV], Qa[NV], n[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) n[k] = k == r ? sgn : 0.0;
+  if (bctype > 0) {
+    boundary_state<D>(bctype, ph, x, t, QL, QR);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Qa[v] = QR[v];
+  } else {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      QR[v] = QRin[v];
+      Qa[v] = 0.5 * (QL[v] + QR[v]);
+    }
+  }
+  riemann_flux<D>(QL, QR, n, ph, Hn);
+  if (ph.viscous) {
+    double gS[D][NV];
+#pragma unroll
+    for (int j = 0; j < D; ++j)
+#pragma unroll
+      for (int v = 0; v < NV; ++v) gS[j][v] = j == r ? sgn * (QL[v] - QR[v]) : 0.0;
+    viscous_flux<D>(Qa, gS, ph, S);
+    double Gv[D][NV];
+    viscous_flux<D>(Qa, dQa, ph, Gv);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Hn[v] -= sgn * (Gv[r][v] - beta * S[r][v]);
+  } else {
+#pragma unroll
+    for (int j = 0; j < D; ++j)
+#pragma unroll
+      for (int v = 0; v < NV; ++v) S[j][v] = 0.0;
+  }
+}
+
+}  // namespace dg

@@ -1,0 +1,990 @@
+// Block relaxed Jacobi preconditioner BRJ(J) of Sec. 4.2.2.
+//
+// Build (Eq. Jacobian-matrix-form, -form2, numerical-Jac-on-traces):
+//   brj_weights_kernel  state and gradient at the Gauss points (sum
+//                       factorisation), exact flux Jacobians dH_j/dQ (dual
+//                       numbers) and dH_j/d(grad_i Q) (G is linear in grad Q),
+//                       times w|J| and the reference metric;
+//   brj_tracejac_kernel one thread per face point: one-sided differences of
+//                       the numerical flux in each trace variable (boundary
+//                       states re-evaluated), chi_k = sqrt(eps)||u_k||;
+//   brj_block_kernel    one block per (element, variable pair): the volume
+//                       terms sum_q (D_j B)^T W (B; D_i B) plus the own-side
+//                       trace term B_f^T J B_f, then D = I - dt_a M^-1 X;
+//   brj_invert_kernel   in-place Gauss-Jordan inversion with partial pivoting
+//                       of every diagonal block.
+// Apply (Eq. precond-Jacobi): q^1 = D^-1 q; q^j = D^-1 (q - (L+U) q^(j-1)), the
+// off-diagonal product formed on the fly from the neighbour traces and the
+// stored neighbour trace Jacobians (brj_trace_kernel + brj_offdiag_kernel),
+// the block product by brj_diag_kernel (HBM-bound batched GEMV).
+#include <cmath>
+#include <cstring>
+#include <cuda_bf16.h>
+#include <new>
+#include <vector>
+#include "dg_internal.h"
+#include "dg_physics.cuh"
+#include "dg_precond.h"
+#include "dg_sumfact.cuh"
+
+namespace dg {
+
+template <typename T>
+struct Prec;
+template <>
+struct Prec<double> {
+  static constexpr int code = DG_PREC_FP64;
+};
+template <>
+struct Prec<float> {
+  static constexpr int code = DG_PREC_FP32;
+};
+
+__host__ __device__ constexpr int round_up8(int x) { return (x + 7) & ~7; }
+
+// ------------------------------------------------------------ weights
+// W[e][q][j][a][k][l], a = 0: w|J| (2/h_j) dH_jk/dQ_l;
+//                       a = 1+i: w|J| (2/h_j)(2/h_i) dH_jk/d(d_i Q_l)
+template <int DIM, int P, int Q, typename TW>
+__global__ void __launch_bounds__(256) brj_weights_kernel(const __grid_constant__ Tables tab,
+                                                          const __grid_constant__ Phys ph,
+                                                          const ElemGeo* __restrict__ geo,
+                                                          int e_begin, int ne,
+                                                          const double* __restrict__ u,
+                                                          TW* __restrict__ W) {
+  using C = Cfg<DIM, P, Q>;
+  constexpr int N = C::N, NV = C::NV, NM = C::NM, NQ = C::NQ, Q2 = C::Q2, N2 = C::N2;
+  constexpr int NW = DIM * (DIM + 1) * NV * NV;
+  extern __shared__ double sm[];
+  double* sB = sm;
+  double* sD = sB + Q * N;
+  double* sw = sD + Q * Q + 2 * Q + N * N;
+  double* sU = sm + C::TAB;
+  double* sQ = sU + NV * NM;
+  double* sG = sQ + NV * NQ;  // DIM arrays
+  double* sT = sG + DIM * NV * NQ;
+  const int el = blockIdx.x;
+  const int e = e_begin + el;
+  stage_tables<DIM, P, Q>(tab, sm);
+  for (int i = threadIdx.x; i < NV * NM; i += blockDim.x) sU[i] = u[(long long)e * NV * NM + i];
+  __syncthreads();
+  if (DIM == 2) {
+    contract<N, N, 1, 0, Q, N, 1, false>(sU, sT, sB, NV);
+    __syncthreads();
+    contract<Q, N, 1, 1, Q, N, 1, false>(sT, sQ, sB, NV);
+  } else {
+    contract<N, N, N2, 0, Q, N, 1, false>(sU, sG + NV * NQ, sB, NV);
+    __syncthreads();
+    contract<Q, N, N2, 1, Q, N, 1, false>(sG + NV * NQ, sG + 2 * NV * NQ, sB, NV);
+    __syncthreads();
+    contract<Q, Q, N2, 2, Q, N, 1, false>(sG + 2 * NV * NQ, sQ, sB, NV);
+  }
+  __syncthreads();
+  contract<Q, Q, Q2, 0, Q, Q, 1, false>(sQ, sG, sD, NV);
+  contract<Q, Q, Q2, 1, Q, Q, 1, false>(sQ, sG + NV * NQ, sD, NV);
+  if (DIM == 3) contract<Q, Q, Q2, 2, Q, Q, 1, false>(sQ, sG + 2 * NV * NQ, sD, NV);
+  __syncthreads();
+  const ElemGeo g = geo[e];
+  double rh[DIM], detJ = 1.0;
+#pragma unroll
+  for (int r = 0; r < DIM; ++r) {
+    rh[r] = 2.0 / g.h[r];
+    detJ *= 0.5 * g.h[r];
+  }
+  for (int q = threadIdx.x; q < NQ; q += blockDim.x) {
+    int c[3];
+    grid_coords<DIM, Q>(q, c);
+    const double wJ = sw[c[0]] * sw[c[1]] * (DIM == 3 ? sw[c[2]] : 1.0) * detJ;
+    double U[NV], dU[DIM][NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      U[v] = sQ[v * NQ + q];
+#pragma unroll
+      for (int r = 0; r < DIM; ++r) dU[r][v] = sG[(r * NV + v) * NQ + q] * rh[r];
+    }
+    TW* Wq = W + ((long long)el * NQ + q) * NW;
+    for (int l = 0; l < NV; ++l) {
+      Dual Ud[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Ud[v] = Dual(U[v], v == l ? 1.0 : 0.0);
+      Dual F[DIM][NV];
+      euler_flux<DIM>(Ud, ph, F);
+      if (ph.viscous) {
+        Dual G[DIM][NV];
+        viscous_flux<DIM, Dual, double>(Ud, dU, ph, G);
+#pragma unroll
+        for (int j = 0; j < DIM; ++j)
+#pragma unroll
+          for (int k = 0; k < NV; ++k) F[j][k] = F[j][k] - G[j][k];
+      }
+#pragma unroll
+      for (int j = 0; j < DIM; ++j)
+#pragma unroll
+        for (int k = 0; k < NV; ++k)
+          Wq[((j * (DIM + 1) + 0) * NV + k) * NV + l] = (TW)(wJ * rh[j] * F[j][k].d);
+    }
+    for (int i = 0; i < DIM; ++i)
+      for (int l = 0; l < NV; ++l) {
+        double G[DIM][NV];
+        if (ph.viscous) {
+          double gu[DIM][NV];
+#pragma unroll
+          for (int a = 0; a < DIM; ++a)
+#pragma unroll
+            for (int v = 0; v < NV; ++v) gu[a][v] = (a == i && v == l) ? 1.0 : 0.0;
+          viscous_flux<DIM>(U, gu, ph, G);
+        } else {
+#pragma unroll
+          for (int a = 0; a < DIM; ++a)
+#pragma unroll
+            for (int v = 0; v < NV; ++v) G[a][v] = 0.0;
+        }
+#pragma unroll
+        for (int j = 0; j < DIM; ++j)
+#pragma unroll
+          for (int k = 0; k < NV; ++k)
+            Wq[((j * (DIM + 1) + 1 + i) * NV + k) * NV + l] = (TW)(-wJ * rh[j] * rh[i] * G[j][k]);
+      }
+  }
+}
+
+// ------------------------------------------------------------ trace Jacobians
+// Jd[e][lf][p][k][l] = s wJf dH_k/dQ_own,l ; Jo = s wJf dH_k/dQ_nbr,l with
+// s = -1 on the owner (left) side and +1 on the right side.
+template <int DIM, int P, int Q, typename TJ>
+__global__ void __launch_bounds__(128) brj_tracejac_kernel(
+    const __grid_constant__ Tables tab, const __grid_constant__ Phys ph,
+    const ElemGeo* __restrict__ geo, const int32_t* __restrict__ faces, int F, double t,
+    const double* __restrict__ tbuf, const double* __restrict__ chi, TJ* __restrict__ Jd,
+    TJ* __restrict__ Jo) {
+  using C = Cfg<DIM, P, Q>;
+  constexpr int NV = C::NV, NF = C::NF;
+  constexpr int NTR = 2 * DIM * (1 + DIM) * NV * NF;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= F * NF) return;
+  const int f = idx / NF, p = idx - f * NF;
+  const int eL = faces[f * 6 + 0], fL = faces[f * 6 + 1];
+  const int eR = faces[f * 6 + 2], fR = faces[f * 6 + 3], bc = faces[f * 6 + 5];
+  const int r = fL >> 1;
+  const double sgn = (fL & 1) ? 1.0 : -1.0;
+  const ElemGeo gL = geo[eL];
+  int pt[2] = {p % Q, DIM == 3 ? p / Q : 0};
+  double x[3] = {0, 0, 0};
+  double wJf = 1.0;
+  {
+    int a = 0;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+      if (k == r) {
+        x[k] = gL.x0[k] + ((fL & 1) ? gL.h[k] : 0.0);
+      } else {
+        x[k] = gL.x0[k] + 0.5 * (tab.x[pt[a]] + 1.0) * gL.h[k];
+        wJf *= tab.w[pt[a]] * 0.5 * gL.h[k];
+        ++a;
+      }
+    }
+  }
+  double QL[NV], QR[NV], dQa[DIM][NV];
+  const double* tl = tbuf + (long long)eL * NTR + (fL * (1 + DIM)) * NV * NF + p;
+  double hmin = gL.h[r];
+  int bctype = 0;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    QL[v] = tl[v * NF];
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) dQa[j][v] = tl[((1 + j) * NV + v) * NF];
+  }
+  if (eR >= 0) {
+    hmin = fmin(hmin, geo[eR].h[r]);
+    const double* tr = tbuf + (long long)eR * NTR + (fR * (1 + DIM)) * NV * NF + p;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      QR[v] = tr[v * NF];
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) dQa[j][v] = 0.5 * (dQa[j][v] + tr[((1 + j) * NV + v) * NF]);
+    }
+  } else {
+    bctype = ph.bc[bc];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) QR[v] = 0.0;
+  }
+  const double beta = (double)((P + 1) * (P + 1)) / hmin;
+  double H0[NV], H1[NV], S[DIM][NV];
+  numerical_flux<DIM>(QL, QR, bctype, x, t, dQa, r, sgn, beta, ph, H0, S);
+  TJ* jdl = Jd + (((long long)eL * 2 * DIM + fL) * NF + p) * NV * NV;
+  TJ* jol = Jo + (((long long)eL * 2 * DIM + fL) * NF + p) * NV * NV;
+  TJ* jdr = eR >= 0 ? Jd + (((long long)eR * 2 * DIM + fR) * NF + p) * NV * NV : nullptr;
+  TJ* jor = eR >= 0 ? Jo + (((long long)eR * 2 * DIM + fR) * NF + p) * NV * NV : nullptr;
+  for (int l = 0; l < NV; ++l) {
+    const double h = chi[l];
+    const double ih = 1.0 / h;
+    double Qp[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Qp[v] = QL[v] + (v == l ? h : 0.0);
+    numerical_flux<DIM>(Qp, QR, bctype, x, t, dQa, r, sgn, beta, ph, H1, S);
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      const double dHdL = (H1[k] - H0[k]) * ih;
+      jdl[k * NV + l] = (TJ)(-wJf * dHdL);
+      if (eR >= 0) jor[k * NV + l] = (TJ)(wJf * dHdL);
+    }
+    if (eR >= 0) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Qp[v] = QR[v] + (v == l ? h : 0.0);
+      numerical_flux<DIM>(QL, Qp, bctype, x, t, dQa, r, sgn, beta, ph, H1, S);
+#pragma unroll
+      for (int k = 0; k < NV; ++k) {
+        const double dHdR = (H1[k] - H0[k]) * ih;
+        jol[k * NV + l] = (TJ)(-wJf * dHdR);
+        jdr[k * NV + l] = (TJ)(wJf * dHdR);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < NV; ++k) jol[k * NV + l] = (TJ)0;
+    }
+  }
+}
+
+// ------------------------------------------------------------ block assembly
+// 1-D value/derivative factors of mode m at Gauss point q: B1[q][m_r] / D1[q][m_r]
+template <int DIM, int N>
+__device__ __forceinline__ void mode_coords(int m, int* mc) {
+  mc[0] = m % N;
+  mc[1] = (m / N) % N;
+  mc[2] = DIM == 3 ? m / (N * N) : 0;
+}
+
+template <int DIM, int P, int Q, typename T>
+__global__ void __launch_bounds__(256) brj_block_kernel(
+    const __grid_constant__ Tables tab, const ElemGeo* __restrict__ geo, int e_begin,
+    const T* __restrict__ W, const T* __restrict__ Jd, double dta, T* __restrict__ blocks,
+    int ld) {
+  using C = Cfg<DIM, P, Q>;
+  constexpr int N = C::N, NV = C::NV, NM = C::NM, NQ = C::NQ, NF = C::NF;
+  constexpr int NW = DIM * (DIM + 1) * NV * NV;
+  constexpr int TM = 4;                         // output tile TM x TM per thread
+  constexpr int NTILE = (NM + TM - 1) / TM;
+  __shared__ T sB1[Q * N], sD1[Q * N];
+  __shared__ double sMi[N * N];
+  extern __shared__ unsigned char smraw[];
+  T* X = reinterpret_cast<T*>(smraw);           // [NM (col)][NM (row)]
+  T* Y = X + NM * NM;
+  T* sW = Y + NM * NM;                          // [NQ][DIM][DIM+1]
+  const int el = blockIdx.x, e = e_begin + el;
+  const int k = blockIdx.y / NV, l = blockIdx.y % NV;
+  for (int i = threadIdx.x; i < Q * N; i += blockDim.x) {
+    sB1[i] = (T)tab.B[i];
+    const int q = i / N, m = i % N;
+    double d = 0.0;  // psi_m'(x_q) by collocation (exact)
+    for (int j = 0; j < Q; ++j) d += tab.Dq[q * Q + j] * tab.B[j * N + m];
+    sD1[i] = (T)d;
+  }
+  for (int i = threadIdx.x; i < N * N; i += blockDim.x) sMi[i] = tab.Minv[i];
+  const T* We = W + (long long)el * NQ * NW;
+  for (int i = threadIdx.x; i < NQ * DIM * (DIM + 1); i += blockDim.x) {
+    const int q = i / (DIM * (DIM + 1)), ja = i % (DIM * (DIM + 1));
+    sW[i] = We[(long long)q * NW + (ja * NV + k) * NV + l];
+  }
+  __syncthreads();
+  for (int tile = threadIdx.x; tile < NTILE * NTILE; tile += blockDim.x) {
+    const int tm = tile / NTILE, tn = tile % NTILE;
+    int mi[TM][3], ni[TM][3];
+    bool mv[TM], nvld[TM];
+#pragma unroll
+    for (int a = 0; a < TM; ++a) {
+      const int m = tm * TM + a, n = tn * TM + a;
+      mv[a] = m < NM;
+      nvld[a] = n < NM;
+      mode_coords<DIM, N>(mv[a] ? m : 0, mi[a]);
+      mode_coords<DIM, N>(nvld[a] ? n : 0, ni[a]);
+    }
+    T acc[TM][TM];
+#pragma unroll
+    for (int a = 0; a < TM; ++a)
+#pragma unroll
+      for (int b = 0; b < TM; ++b) acc[a][b] = (T)0;
+    for (int q = 0; q < NQ; ++q) {
+      int c[3];
+      grid_coords<DIM, Q>(q, c);
+      // trial functions (value and reference derivatives) of the tile columns
+      T tr[TM][DIM + 1];
+#pragma unroll
+      for (int b = 0; b < TM; ++b) {
+        T bv[3], dv[3];
+#pragma unroll
+        for (int r = 0; r < DIM; ++r) {
+          bv[r] = sB1[c[r] * N + ni[b][r]];
+          dv[r] = sD1[c[r] * N + ni[b][r]];
+        }
+        T prod = bv[0] * bv[1] * (DIM == 3 ? bv[2] : (T)1);
+        tr[b][0] = prod;
+        tr[b][1] = dv[0] * bv[1] * (DIM == 3 ? bv[2] : (T)1);
+        tr[b][2] = bv[0] * dv[1] * (DIM == 3 ? bv[2] : (T)1);
+        if (DIM == 3) tr[b][DIM] = bv[0] * bv[1] * dv[DIM - 1];
+      }
+      // inner sums S_j(n) = sum_a W_ja T_a(n)
+      const T* w = sW + q * DIM * (DIM + 1);
+      T sj[TM][DIM];
+#pragma unroll
+      for (int b = 0; b < TM; ++b)
+#pragma unroll
+        for (int j = 0; j < DIM; ++j) {
+          T s = (T)0;
+#pragma unroll
+          for (int a = 0; a < DIM + 1; ++a) s += w[j * (DIM + 1) + a] * tr[b][a];
+          sj[b][j] = s;
+        }
+      // test-function derivatives of the tile rows
+#pragma unroll
+      for (int a = 0; a < TM; ++a) {
+        T bv[3], dv[3];
+#pragma unroll
+        for (int r = 0; r < DIM; ++r) {
+          bv[r] = sB1[c[r] * N + mi[a][r]];
+          dv[r] = sD1[c[r] * N + mi[a][r]];
+        }
+        T te[DIM];
+        te[0] = dv[0] * bv[1] * (DIM == 3 ? bv[2] : (T)1);
+        te[1] = bv[0] * dv[1] * (DIM == 3 ? bv[2] : (T)1);
+        if (DIM == 3) te[2] = bv[0] * bv[1] * dv[2];
+#pragma unroll
+        for (int b = 0; b < TM; ++b)
+#pragma unroll
+          for (int j = 0; j < DIM; ++j) acc[a][b] += te[j] * sj[b][j];
+      }
+    }
+    // own-side trace term: sum_faces sum_p Bf(p,m) Jd(p) Bf(p,n)
+    for (int lf = 0; lf < 2 * DIM; ++lf) {
+      const int r = lf >> 1;
+      const int vert = (lf & 1) ? P : 0;
+      const T* jd = Jd + (((long long)e * 2 * DIM + lf) * NF) * NV * NV + k * NV + l;
+      for (int p = 0; p < NF; ++p) {
+        int pc[2] = {p % Q, DIM == 3 ? p / Q : 0};
+        const T jv = jd[(long long)p * NV * NV];
+        T fm[TM], fn[TM];
+#pragma unroll
+        for (int a = 0; a < TM; ++a) {
+          T vm = mi[a][r] == vert ? (T)1 : (T)0, vn = ni[a][r] == vert ? (T)1 : (T)0;
+          int t = 0;
+#pragma unroll
+          for (int s = 0; s < DIM; ++s) {
+            if (s == r) continue;
+            vm *= sB1[pc[t] * N + mi[a][s]];
+            vn *= sB1[pc[t] * N + ni[a][s]];
+            ++t;
+          }
+          fm[a] = vm;
+          fn[a] = vn * jv;
+        }
+#pragma unroll
+        for (int a = 0; a < TM; ++a)
+#pragma unroll
+          for (int b = 0; b < TM; ++b) acc[a][b] += fm[a] * fn[b];
+      }
+    }
+    // X stored column-major per trial mode n: X[n][m]
+#pragma unroll
+    for (int a = 0; a < TM; ++a)
+#pragma unroll
+      for (int b = 0; b < TM; ++b)
+        if (mv[a] && nvld[b]) X[(tn * TM + b) * NM + tm * TM + a] = acc[a][b];
+  }
+  __syncthreads();
+  // M^-1 on the row (test) index: |J|^-1 (M1^-1)^(x)DIM, axis by axis
+  const ElemGeo g = geo[e];
+  double idet = 1.0;
+#pragma unroll
+  for (int r = 0; r < DIM; ++r) idet *= 2.0 / g.h[r];
+  T* src = X;
+  T* dst = Y;
+  for (int ax = 0; ax < DIM; ++ax) {
+    for (int i = threadIdx.x; i < NM * NM; i += blockDim.x) {
+      const int col = i / NM, m = i % NM;
+      int mc[3];
+      mode_coords<DIM, N>(m, mc);
+      const int str = ax == 0 ? 1 : (ax == 1 ? N : N * N);
+      const int base = m - mc[ax] * str;
+      double s = 0.0;
+#pragma unroll
+      for (int kk = 0; kk < N; ++kk)
+        s += sMi[mc[ax] * N + kk] * (double)src[col * NM + base + kk * str];
+      dst[i] = (T)s;
+    }
+    __syncthreads();
+    T* tmp = src;
+    src = dst;
+    dst = tmp;
+  }
+  // D = I - dt_a M^-1 X into rows k*NM + m, columns l*NM + n
+  T* out = blocks + (long long)e * (NV * NM) * ld;
+  for (int i = threadIdx.x; i < NM * NM; i += blockDim.x) {
+    const int m = i / NM, n = i % NM;
+    double val = -dta * idet * (double)src[n * NM + m];
+    if (k == l && m == n) val += 1.0;
+    out[(long long)(k * NM + m) * ld + l * NM + n] = (T)val;
+  }
+}
+
+// ------------------------------------------------------------ inversion
+// In-place Gauss-Jordan inversion with partial pivoting of the nb x nb block
+// of each element (row stride ld); singular blocks set *fail.
+template <typename T>
+__global__ void __launch_bounds__(512) brj_invert_kernel(T* __restrict__ blocks, int nb, int ld,
+                                                         int* __restrict__ fail) {
+  extern __shared__ unsigned char smraw[];
+  T* col = reinterpret_cast<T*>(smraw);   // [nb] pivot column
+  T* row = col + nb;                      // [nb] pivot row
+  int* perm = reinterpret_cast<int*>(row + nb);
+  __shared__ T redv[512];
+  __shared__ int redi[512];
+  T* A = blocks + (long long)blockIdx.x * nb * ld;
+  for (int kk = 0; kk < nb; ++kk) {
+    // pivot search (largest magnitude, smallest index on ties)
+    T best = (T)-1;
+    int bi = kk;
+    for (int i = kk + threadIdx.x; i < nb; i += blockDim.x) {
+      T v = fabs(A[(long long)i * ld + kk]);
+      if (v > best) {
+        best = v;
+        bi = i;
+      }
+    }
+    redv[threadIdx.x] = best;
+    redi[threadIdx.x] = bi;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+      if (threadIdx.x < s) {
+        T o = redv[threadIdx.x + s];
+        int oi = redi[threadIdx.x + s];
+        if (o > redv[threadIdx.x] || (o == redv[threadIdx.x] && oi < redi[threadIdx.x])) {
+          redv[threadIdx.x] = o;
+          redi[threadIdx.x] = oi;
+        }
+      }
+      __syncthreads();
+    }
+    const int pr = redi[0];
+    const T pmag = redv[0];
+    __syncthreads();
+    if (threadIdx.x == 0) perm[kk] = pr;
+    if (!(pmag > (T)0)) {
+      if (threadIdx.x == 0) atomicExch(fail, 1);
+      return;
+    }
+    if (pr != kk)
+      for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+        T a = A[(long long)kk * ld + j];
+        A[(long long)kk * ld + j] = A[(long long)pr * ld + j];
+        A[(long long)pr * ld + j] = a;
+      }
+    __syncthreads();
+    const T piv = A[(long long)kk * ld + kk];
+    const T ipiv = (T)1 / piv;
+    for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+      T a = j == kk ? ipiv : A[(long long)kk * ld + j] * ipiv;
+      row[j] = a;
+      col[j] = A[(long long)j * ld + kk];
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < nb; j += blockDim.x) A[(long long)kk * ld + j] = row[j];
+    for (int i2 = threadIdx.x; i2 < (nb - 1) * nb; i2 += blockDim.x) {
+      int i = i2 / nb, j = i2 % nb;
+      if (i >= kk) ++i;  // skip the pivot row
+      const T f = col[i];
+      T a = j == kk ? (T)0 : A[(long long)i * ld + j];
+      A[(long long)i * ld + j] = a - f * row[j];
+    }
+    __syncthreads();
+  }
+  // undo the row interchanges by column swaps in reverse order
+  for (int kk = nb - 1; kk >= 0; --kk) {
+    const int pr = perm[kk];
+    if (pr != kk)
+      for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+        T a = A[(long long)i * ld + kk];
+        A[(long long)i * ld + kk] = A[(long long)i * ld + pr];
+        A[(long long)i * ld + pr] = a;
+      }
+    __syncthreads();
+  }
+}
+
+__global__ void to_bf16_kernel(const float* __restrict__ src, __nv_bfloat16* __restrict__ dst,
+                               long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    dst[i] = __float2bfloat16_rn(src[i]);
+}
+
+// chi_k = sqrt(2^-52) ||u_k||_2 (sqrt(2^-52) when the variable vanishes)
+__global__ void __launch_bounds__(256) var_norm_kernel(const double* __restrict__ u, int E,
+                                                       int nv, int nm, double* __restrict__ chi) {
+  __shared__ double sh[256];
+  const int k = blockIdx.x;
+  double s = 0.0;
+  for (long long i = threadIdx.x; i < (long long)E * nm; i += 256) {
+    const long long e = i / nm, m = i % nm;
+    const double v = u[(e * nv + k) * nm + m];
+    s = fma(v, v, s);
+  }
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if (threadIdx.x < st) sh[threadIdx.x] += sh[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double nk = sqrt(sh[0]);
+    chi[k] = 1.4901161193847656e-08 * (nk > 0.0 ? nk : 1.0);
+  }
+}
+
+// ------------------------------------------------------------ apply
+// out = omega * D^-1 y + (1 - omega) * qprev  (one warp per row group)
+template <typename TB, typename TA>
+__global__ void __launch_bounds__(256) brj_diag_kernel(const TB* __restrict__ blocks, int nb,
+                                                       int ld, const double* __restrict__ y,
+                                                       const double* __restrict__ qprev,
+                                                       double omega, double* __restrict__ out) {
+  extern __shared__ unsigned char smraw[];
+  TA* sy = reinterpret_cast<TA*>(smraw);
+  const int e = blockIdx.x;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) sy[i] = (TA)y[(long long)e * nb + i];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const TB* A = blocks + (long long)e * nb * ld;
+  for (int rrow = warp; rrow < nb; rrow += nw) {
+    const TB* ar = A + (long long)rrow * ld;
+    TA acc = (TA)0;
+    for (int c = lane; c < nb; c += 32) acc += (TA)ar[c] * sy[c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+      double v = (double)acc;
+      const long long gi = (long long)e * nb + rrow;
+      out[gi] = omega == 1.0 ? v : omega * v + (1.0 - omega) * qprev[gi];
+    }
+  }
+}
+
+// bf16 blocks, FP32 arithmetic, 8 elements per 16-byte load
+__global__ void __launch_bounds__(256) brj_diag_bf16_kernel(
+    const __nv_bfloat16* __restrict__ blocks, int nb, int ld, const double* __restrict__ y,
+    const double* __restrict__ qprev, double omega, double* __restrict__ out) {
+  extern __shared__ unsigned char smraw[];
+  float* sy = reinterpret_cast<float*>(smraw);
+  const int e = blockIdx.x;
+  for (int i = threadIdx.x; i < ld; i += blockDim.x)
+    sy[i] = i < nb ? (float)y[(long long)e * nb + i] : 0.0f;
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const __nv_bfloat16* A = blocks + (long long)e * nb * ld;
+  for (int rrow = warp; rrow < nb; rrow += nw) {
+    const uint4* ar = reinterpret_cast<const uint4*>(A + (long long)rrow * ld);
+    float acc = 0.0f;
+    for (int c8 = lane; c8 < ld / 8; c8 += 32) {
+      uint4 pk = ar[c8];
+      const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&pk);
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        float2 f = __bfloat1622float2(h2[t]);
+        acc = fmaf(f.x, sy[c8 * 8 + 2 * t], acc);
+        acc = fmaf(f.y, sy[c8 * 8 + 2 * t + 1], acc);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+      const long long gi = (long long)e * nb + rrow;
+      out[gi] = omega == 1.0 ? (double)acc : omega * (double)acc + (1.0 - omega) * qprev[gi];
+    }
+  }
+}
+
+// face values of an iterate: tr[e][lf][v][p] = sum over the face modes
+template <int DIM, int P, int Q, typename TA>
+__global__ void __launch_bounds__(128) brj_trace_kernel(const __grid_constant__ Tables tab,
+                                                        const double* __restrict__ q, int E,
+                                                        double* __restrict__ tr) {
+  using C = Cfg<DIM, P, Q>;
+  constexpr int N = C::N, NV = C::NV, NM = C::NM, NF = C::NF;
+  constexpr int NTOT = 2 * DIM * NV * NF;
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= (long long)E * NTOT) return;
+  const int e = (int)(idx / NTOT);
+  int rem = (int)(idx % NTOT);
+  const int p = rem % NF;
+  rem /= NF;
+  const int v = rem % NV;
+  const int lf = rem / NV;
+  const int r = lf >> 1, vert = (lf & 1) ? P : 0;
+  const int pc[2] = {p % Q, DIM == 3 ? p / Q : 0};
+  const double* qe = q + ((long long)e * NV + v) * NM;
+  TA acc = (TA)0;
+  if (DIM == 2) {
+    const int s = 1 - r;
+    for (int a = 0; a < N; ++a) {
+      int mc[2];
+      mc[r] = vert;
+      mc[s] = a;
+      acc += (TA)tab.B[pc[0] * N + a] * (TA)qe[mc[0] + N * mc[1]];
+    }
+  } else {
+    const int t0 = r == 0 ? 1 : 0, t1 = r == 2 ? 1 : 2;
+    for (int a = 0; a < N; ++a)
+      for (int b = 0; b < N; ++b) {
+        int mc[3];
+        mc[r] = vert;
+        mc[t0] = a;
+        mc[t1] = b;
+        acc += (TA)(tab.B[pc[0] * N + a] * tab.B[pc[1] * N + b]) *
+               (TA)qe[mc[0] + N * (mc[1] + N * mc[2])];
+      }
+  }
+  tr[idx] = (double)acc;
+}
+
+// y = q + dt_a M^-1 sum_faces B_f^T (Jo . trace of the neighbour)  (= q - (L+U) qh)
+template <int DIM, int P, int Q, typename TA, typename TJ>
+__global__ void __launch_bounds__(128) brj_offdiag_kernel(
+    const __grid_constant__ Tables tab, const ElemGeo* __restrict__ geo, int E,
+    const TJ* __restrict__ Jo, const int32_t* __restrict__ nbr, const double* __restrict__ tr,
+    const double* __restrict__ q, double dta, double* __restrict__ y) {
+  using C = Cfg<DIM, P, Q>;
+  constexpr int N = C::N, NV = C::NV, NM = C::NM, NF = C::NF;
+  __shared__ TA cf[2 * DIM * NV * NF];
+  __shared__ double L0[NV * NM], L1[NV * NM];
+  const int e = blockIdx.x;
+  for (int i = threadIdx.x; i < 2 * DIM * NV * NF; i += blockDim.x) {
+    const int p = i % NF, k = (i / NF) % NV, lf = i / (NF * NV);
+    const int nb = nbr[e * 2 * DIM + lf];
+    TA s = (TA)0;
+    if (nb >= 0) {
+      const TJ* j = Jo + (((long long)e * 2 * DIM + lf) * NF + p) * NV * NV + k * NV;
+      const double* t = tr + (long long)nb * NV * NF + p;  // nb = element*2d + face
+#pragma unroll
+      for (int l = 0; l < NV; ++l) s += (TA)j[l] * (TA)t[l * NF];
+    }
+    cf[i] = s;
+  }
+  __syncthreads();
+  // lift onto the face modes
+  for (int i = threadIdx.x; i < NV * NM; i += blockDim.x) {
+    const int v = i / NM, m = i % NM;
+    int mc[3];
+    mode_coords<DIM, N>(m, mc);
+    TA s = (TA)0;
+    for (int lf = 0; lf < 2 * DIM; ++lf) {
+      const int r = lf >> 1, vert = (lf & 1) ? P : 0;
+      if (mc[r] != vert) continue;
+      const TA* c = cf + (lf * NV + v) * NF;
+      if (DIM == 2) {
+        const int a = mc[1 - r];
+        for (int p = 0; p < Q; ++p) s += (TA)tab.B[p * N + a] * c[p];
+      } else {
+        const int t0 = r == 0 ? 1 : 0, t1 = r == 2 ? 1 : 2;
+        const int a = mc[t0], b = mc[t1];
+        for (int p1 = 0; p1 < Q; ++p1) {
+          TA s2 = (TA)0;
+          for (int p0 = 0; p0 < Q; ++p0) s2 += (TA)tab.B[p0 * N + a] * c[p0 + Q * p1];
+          s += (TA)tab.B[p1 * N + b] * s2;
+        }
+      }
+    }
+    L0[i] = (double)s;
+  }
+  __syncthreads();
+  // inverse mass matrix, axis by axis
+  double* src = L0;
+  double* dst = L1;
+  for (int ax = 0; ax < DIM; ++ax) {
+    for (int i = threadIdx.x; i < NV * NM; i += blockDim.x) {
+      const int m = i % NM;
+      int mc[3];
+      mode_coords<DIM, N>(m, mc);
+      const int str = ax == 0 ? 1 : (ax == 1 ? N : N * N);
+      const int base = i - mc[ax] * str;
+      TA s = (TA)0;
+#pragma unroll
+      for (int kk = 0; kk < N; ++kk) s += (TA)tab.Minv[mc[ax] * N + kk] * (TA)src[base + kk * str];
+      dst[i] = (double)s;
+    }
+    __syncthreads();
+    double* t = src;
+    src = dst;
+    dst = t;
+  }
+  const ElemGeo g = geo[e];
+  double idet = 1.0;
+#pragma unroll
+  for (int r = 0; r < DIM; ++r) idet *= 2.0 / g.h[r];
+  for (int i = threadIdx.x; i < NV * NM; i += blockDim.x) {
+    const long long gi = (long long)e * NV * NM + i;
+    y[gi] = q[gi] + dta * idet * src[i];
+  }
+}
+
+// ------------------------------------------------------------ drivers
+template <int DIM, int P, int Q>
+struct BRJImpl {
+  using C = Cfg<DIM, P, Q>;
+
+  template <typename T>
+  static dg_status build(dg_mesh_s* m, dg_precond_s* pc, const double* u, double t, double dta,
+                         cudaStream_t s) {
+    constexpr int NV = C::NV, NM = C::NM, NQ = C::NQ, NF = C::NF;
+    constexpr int NW = DIM * (DIM + 1) * NV * NV;
+    const int E = m->E, nb = pc->nb, ld = round_up8(nb);
+    // traces of Q and grad Q at u (residual pass fills the trace buffer)
+    EvalArgs a{};
+    a.u = u;
+    a.t = t;
+    a.out = m->w2;
+    DG_TRY(launch_residual(m, a, s));
+    double* chi = m->scratch + 8;
+    var_norm_kernel<<<NV, 256, 0, s>>>(u, E, NV, NM, chi);
+    DG_CUDA(cudaGetLastError());
+    T* Jd = (T*)pc->jd;
+    T* Jo = (T*)pc->jo;
+    brj_tracejac_kernel<DIM, P, Q, T><<<(m->F * NF + 127) / 128, 128, 0, s>>>(
+        m->tab, m->phys, m->geo, m->faces, m->F, t, m->tbuf, chi, Jd, Jo);
+    DG_CUDA(cudaGetLastError());
+    // blocks: FP64 mode stores double, FP32/BF16 modes assemble in float
+    T* blk = (T*)(pc->precision == DG_PREC_BF16 ? pc->work : pc->blocks);
+    T* Wbuf = (T*)((char*)pc->work +
+                   (pc->precision == DG_PREC_BF16 ? sizeof(float) * (size_t)E * nb * ld : 0));
+    const size_t wsm = sizeof(double) * (C::TAB + NV * NM + (1 + DIM) * NV * NQ + (DIM == 2 ? NV * NQ : 0));
+    DG_CUDA(cudaFuncSetAttribute(brj_weights_kernel<DIM, P, Q, T>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsm));
+    const size_t bsm = sizeof(T) * (2 * NM * NM + NQ * DIM * (DIM + 1));
+    DG_CUDA(cudaFuncSetAttribute(brj_block_kernel<DIM, P, Q, T>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm));
+    const int CH = pc->wchunk;
+    for (int e0 = 0; e0 < E; e0 += CH) {
+      const int ne = E - e0 < CH ? E - e0 : CH;
+      brj_weights_kernel<DIM, P, Q, T><<<ne, 256, wsm, s>>>(m->tab, m->phys, m->geo, e0, ne, u,
+                                                            Wbuf);
+      DG_CUDA(cudaGetLastError());
+      brj_block_kernel<DIM, P, Q, T><<<dim3(ne, NV * NV), 256, bsm, s>>>(m->tab, m->geo, e0, Wbuf,
+                                                                         Jd, dta, blk, ld);
+      DG_CUDA(cudaGetLastError());
+    }
+    int* fail = (int*)(m->scratch + 16);
+    DG_CUDA(cudaMemsetAsync(fail, 0, sizeof(int), s));
+    const size_t ism = sizeof(T) * 2 * nb + sizeof(int) * nb;
+    DG_CUDA(cudaFuncSetAttribute(brj_invert_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)ism));
+    brj_invert_kernel<T><<<E, 512, ism, s>>>(blk, nb, ld, fail);
+    DG_CUDA(cudaGetLastError());
+    if (pc->precision == DG_PREC_BF16) {
+      const long long n = (long long)E * nb * ld;
+      to_bf16_kernel<<<152 * 16, 256, 0, s>>>((const float*)blk, (__nv_bfloat16*)pc->blocks, n);
+      DG_CUDA(cudaGetLastError());
+    }
+    int hfail = 0;
+    DG_CUDA(cudaMemcpyAsync(&hfail, fail, sizeof(int), cudaMemcpyDeviceToHost, s));
+    DG_CUDA(cudaStreamSynchronize(s));
+    return hfail ? DG_ERR_NONFINITE : DG_OK;
+  }
+
+  template <typename TA, typename TJ>
+  static dg_status offdiag(dg_mesh_s* m, dg_precond_s* pc, const double* qh, const double* q,
+                           double* y, cudaStream_t s) {
+    constexpr int NV = C::NV, NF = C::NF;
+    const long long ntr = (long long)m->E * 2 * DIM * NV * NF;
+    brj_trace_kernel<DIM, P, Q, TA><<<(unsigned)((ntr + 127) / 128), 128, 0, s>>>(m->tab, qh, m->E,
+                                                                                   pc->tr);
+    DG_CUDA(cudaGetLastError());
+    brj_offdiag_kernel<DIM, P, Q, TA, TJ><<<m->E, 128, 0, s>>>(m->tab, m->geo, m->E,
+                                                               (const TJ*)pc->jo, pc->nbr, pc->tr,
+                                                               q, pc->dt_a, y);
+    DG_CUDA(cudaGetLastError());
+    return DG_OK;
+  }
+};
+
+static dg_status diag_apply(dg_precond_s* pc, const double* y, const double* qprev, double* out,
+                            cudaStream_t s) {
+  const int E = pc->mesh->E, nb = pc->nb, ld = round_up8(nb);
+  if (pc->precision == DG_PREC_FP64) {
+    brj_diag_kernel<double, double><<<E, 256, sizeof(double) * nb, s>>>(
+        (const double*)pc->blocks, nb, ld, y, qprev, pc->omega, out);
+  } else if (pc->precision == DG_PREC_FP32) {
+    brj_diag_kernel<float, float><<<E, 256, sizeof(float) * nb, s>>>(
+        (const float*)pc->blocks, nb, ld, y, qprev, pc->omega, out);
+  } else {
+    brj_diag_bf16_kernel<<<E, 256, sizeof(float) * ld, s>>>((const __nv_bfloat16*)pc->blocks, nb,
+                                                           ld, y, qprev, pc->omega, out);
+  }
+  DG_CUDA(cudaGetLastError());
+  return DG_OK;
+}
+
+#define DG_PREC_INSTANCES(X)                                                                  \
+  X(2, 1, 3) X(2, 2, 3) X(2, 2, 4) X(2, 3, 5) X(2, 4, 6) X(2, 5, 7) X(2, 6, 8) X(3, 1, 3) \
+  X(3, 2, 4) X(3, 2, 5) X(3, 3, 5) X(3, 3, 6) X(3, 4, 6) X(3, 4, 8)
+
+static dg_status dispatch_build(dg_mesh_s* m, dg_precond_s* pc, const double* u, double t,
+                                double dta, cudaStream_t s) {
+#define DG_B(D_, P_, Q_)                                                  \
+  if (m->dim == D_ && m->P == P_ && m->Q == Q_) {                         \
+    if (pc->precision == DG_PREC_FP64)                                    \
+      return BRJImpl<D_, P_, Q_>::build<double>(m, pc, u, t, dta, s);     \
+    return BRJImpl<D_, P_, Q_>::build<float>(m, pc, u, t, dta, s);        \
+  }
+  DG_PREC_INSTANCES(DG_B)
+#undef DG_B
+  return DG_ERR_UNSUPPORTED;
+}
+
+static dg_status dispatch_offdiag(dg_precond_s* pc, const double* qh, const double* q, double* y,
+                                  cudaStream_t s) {
+  dg_mesh_s* m = pc->mesh;
+#define DG_O(D_, P_, Q_)                                                                 \
+  if (m->dim == D_ && m->P == P_ && m->Q == Q_) {                                        \
+    if (pc->precision == DG_PREC_FP64)                                                   \
+      return BRJImpl<D_, P_, Q_>::offdiag<double, double>(m, pc, qh, q, y, s);           \
+    return BRJImpl<D_, P_, Q_>::offdiag<float, float>(m, pc, qh, q, y, s);               \
+  }
+  DG_PREC_INSTANCES(DG_O)
+#undef DG_O
+  return DG_ERR_UNSUPPORTED;
+}
+
+dg_status precond_apply_impl(dg_precond_s* pc, const double* q, double* out, cudaStream_t s) {
+  // sweep 1 from qh = 0: D^-1 q (the relaxation term vanishes)
+  double* cur = pc->J == 1 ? out : pc->qh;
+  {
+    const double om = pc->omega;
+    const int E = pc->mesh->E, nb = pc->nb, ld = round_up8(nb);
+    (void)E;
+    (void)ld;
+    (void)nb;
+    dg_precond_s tmp = *pc;
+    tmp.omega = 1.0;
+    DG_TRY(diag_apply(&tmp, q, nullptr, cur, s));
+    if (om != 1.0) DG_TRY(axpby(cur, 0.0, cur, om, pc->mesh->ndof, s));
+  }
+  for (int j = 1; j < pc->J; ++j) {
+    DG_TRY(dispatch_offdiag(pc, cur, q, pc->y, s));
+    double* nxt = j == pc->J - 1 ? out : pc->qh;
+    if (nxt != cur && pc->omega != 1.0)
+      DG_CUDA(cudaMemcpyAsync(nxt, cur, sizeof(double) * pc->mesh->ndof, cudaMemcpyDeviceToDevice, s));
+    DG_TRY(diag_apply(pc, pc->y, nxt, nxt, s));
+    cur = nxt;
+  }
+  return DG_OK;
+}
+
+}  // namespace dg
+
+using namespace dg;
+
+static void free_precond(dg_precond_s* p) {
+  if (!p) return;
+  cudaFree(p->blocks);
+  cudaFree(p->jd);
+  cudaFree(p->jo);
+  cudaFree(p->nbr);
+  cudaFree(p->tr);
+  cudaFree(p->qh);
+  cudaFree(p->y);
+  cudaFree(p->work);
+  delete p;
+}
+
+extern "C" {
+
+dg_status dg_precond_build(dg_mesh_t m, const double* u, double t, double dt_a,
+                           const dg_prec_cfg* cfg, dg_precond_t* inout, void* stream) {
+  if (!m || !u || !cfg || !inout) return DG_ERR_ARG;
+  if (cfg->J < 1 || !(cfg->omega > 0.0)) return DG_ERR_ARG;
+  if (cfg->precision < DG_PREC_FP64 || cfg->precision > DG_PREC_BF16) return DG_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int d = m->dim, E = m->E, NV = m->nv;
+  const int nb = NV * m->nm, ld = round_up8(nb);
+  if (cfg->precision == DG_PREC_FP64 && 2 * (size_t)m->nm * m->nm * 8 > 200 * 1024)
+    return DG_ERR_UNSUPPORTED;
+  dg_precond_s* p = *inout;
+  if (p && (p->mesh != m || p->precision != cfg->precision)) {
+    free_precond(p);
+    *inout = nullptr;
+    p = nullptr;
+  }
+  const size_t vb = cfg->precision == DG_PREC_FP64 ? 8 : 4;  // build / trace-Jacobian value size
+  const size_t nwq = (size_t)d * (d + 1) * NV * NV * m->nq;  // weights per element
+  if (!p) {
+    p = new (std::nothrow) dg_precond_s();
+    if (!p) return DG_ERR_OOM;
+    p->mesh = m;
+    p->precision = cfg->precision;
+    p->nb = nb;
+    const size_t bsz = cfg->precision == DG_PREC_FP64 ? 8 : (cfg->precision == DG_PREC_FP32 ? 4 : 2);
+    const size_t njac = (size_t)E * 2 * d * m->nf * NV * NV;
+    // weights workspace: bounded to ~1 GiB by processing elements in chunks
+    size_t per = nwq * vb;
+    int ch = (int)((size_t(1) << 30) / per);
+    if (ch < 1) ch = 1;
+    if (ch > E) ch = E;
+    p->wchunk = ch;
+    const size_t stage = cfg->precision == DG_PREC_BF16 ? sizeof(float) * (size_t)E * nb * ld : 0;
+    p->work_bytes = stage + per * ch;
+    cudaError_t err = cudaSuccess;
+    auto alloc = [&](void** ptr, size_t bytes) {
+      if (err == cudaSuccess) err = cudaMalloc(ptr, bytes);
+    };
+    alloc(&p->blocks, bsz * (size_t)E * nb * ld);
+    alloc(&p->jd, vb * njac);
+    alloc(&p->jo, vb * njac);
+    alloc((void**)&p->nbr, sizeof(int32_t) * E * 2 * d);
+    alloc((void**)&p->tr, sizeof(double) * (size_t)E * 2 * d * NV * m->nf);
+    alloc((void**)&p->qh, sizeof(double) * (size_t)m->ndof);
+    alloc((void**)&p->y, sizeof(double) * (size_t)m->ndof);
+    alloc(&p->work, p->work_bytes);
+    // zero padding columns once: the block kernels never write them
+    if (err == cudaSuccess) err = cudaMemset(p->blocks, 0, bsz * (size_t)E * nb * ld);
+    if (err == cudaSuccess) err = cudaMemset(p->work, 0, p->work_bytes);
+    if (err != cudaSuccess) {
+      free_precond(p);
+      return cuda_status(err);
+    }
+    // neighbour map (element * 2d + local face of the other side) per element face
+    std::vector<int32_t> faces((size_t)m->F * 6), nbr((size_t)E * 2 * d, -1);
+    if (cudaMemcpy(faces.data(), m->faces, sizeof(int32_t) * 6 * m->F, cudaMemcpyDeviceToHost) !=
+        cudaSuccess) {
+      free_precond(p);
+      return DG_ERR_CUDA;
+    }
+    for (int f = 0; f < m->F; ++f) {
+      const int eL = faces[f * 6], fL = faces[f * 6 + 1], eR = faces[f * 6 + 2], fR = faces[f * 6 + 3];
+      if (eR >= 0) {
+        nbr[(size_t)eL * 2 * d + fL] = eR * 2 * d + fR;
+        nbr[(size_t)eR * 2 * d + fR] = eL * 2 * d + fL;
+      }
+    }
+    if (cudaMemcpy(p->nbr, nbr.data(), sizeof(int32_t) * nbr.size(), cudaMemcpyHostToDevice) !=
+        cudaSuccess) {
+      free_precond(p);
+      return DG_ERR_CUDA;
+    }
+    *inout = p;
+  }
+  p->J = cfg->J;
+  p->omega = cfg->omega;
+  p->dt_a = dt_a;
+  return dispatch_build(m, p, u, t, dt_a, s);
+}
+
+dg_status dg_precond_apply(dg_precond_t p, const double* q, double* out, void* stream) {
+  if (!p || !q || !out || q == out) return DG_ERR_ARG;
+  return precond_apply_impl(p, q, out, (cudaStream_t)stream);
+}
+
+dg_status dg_precond_destroy(dg_precond_t p) {
+  if (!p) return DG_ERR_ARG;
+  cudaError_t e = cudaDeviceSynchronize();
+  free_precond(p);
+  return e == cudaSuccess ? DG_OK : cuda_status(e);
+}
+
+}  // extern "C"

@@ -1,0 +1,27 @@
+// Internal interface of the block relaxed Jacobi preconditioner.
+#pragma once
+#include "dg_internal.h"
+
+struct dg_precond_s {
+  dg_mesh_s* mesh = nullptr;
+  int J = 7;
+  int precision = DG_PREC_FP64;
+  double omega = 1.0;
+  double dt_a = 0.0;
+  int nb = 0;             // block size n_var * n_mode
+  void* blocks = nullptr; // [E][nb][nb] inverse diagonal blocks (double, float or bf16)
+  void* jd = nullptr;     // [E][2d][nf][nv][nv] own-side trace Jacobians (double or float)
+  void* jo = nullptr;     // [E][2d][nf][nv][nv] neighbour trace Jacobians
+  int32_t* nbr = nullptr; // [E][2d] neighbour (element * 2d + local face) or -1
+  double* tr = nullptr;   // [E][2d][nv][nf] face values of the current iterate
+  double* qh = nullptr;   // [ndof] iterate
+  double* y = nullptr;    // [ndof] right-hand side of a sweep
+  void* work = nullptr;   // build workspace
+  size_t work_bytes = 0;
+  int wchunk = 1;          // elements per pass of the weights workspace
+};
+
+namespace dg {
+dg_status precond_apply_impl(dg_precond_s* p, const double* q, double* out, cudaStream_t s);
+inline dg_mesh_s* precond_mesh(dg_precond_s* p) { return p->mesh; }
+}  // namespace dg

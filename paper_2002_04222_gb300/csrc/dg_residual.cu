@@ -1,0 +1,499 @@
+// DG residual R(u) = M^-1 L(u, t) of Sec. 3.1 (Eq. matrix-form-equations) on
+// axis-aligned affine quads/hexes, in three FP64 kernels:
+//   vol_kernel   sum-factorised BwdTrans (B), collocation derivatives on the
+//                Gauss grid (D_j), fused Euler + viscous volume flux H_j
+//                weighted by w|J| and the reference metric, and the face
+//                traces of Q and grad Q (interpolation J to the faces);
+//   face_kernel  one thread per face point: Riemann flux (Roe/HLLC), the
+//                interior-penalty viscous flux and the symmetric flux S_i;
+//   lift_kernel  spreads the face fluxes back onto the Gauss grid (J^T),
+//                applies sum_j D_j^T, B^T and the inverse mass matrix
+//                |J|^-1 (M1^-1)^(x)d, adds the forcing and (for the
+//                Jacobian-free product) the finite-difference combination.
+// FP64 throughout: on GB300 this path is bound by the FP64 pipe, so every
+// stage is written to issue as few FP64 instructions as possible.
+#include <cstdio>
+#include "dg_internal.h"
+#include "dg_physics.cuh"
+#include "dg_sumfact.cuh"
+
+namespace dg {
+
+// ---------------------------------------------------------------- kernel 1
+template <int DIM, int P, int Q>
+__global__ void __launch_bounds__(256) vol_kernel(const __grid_constant__ Tables tab,
+                                                  const __grid_constant__ Phys ph,
+                                                  const ElemGeo* __restrict__ geo, int E,
+                                                  const double* __restrict__ u,
+                                                  const double* __restrict__ v,
+                                                  const double* __restrict__ epsp,
+                                                  double* __restrict__ hbuf,
+                                                  double* __restrict__ tbuf) {
+  using C = Cfg<DIM, P, Q>;
+  constexpr int N = C::N, NV = C::NV, NM = C::NM, NQ = C::NQ, NF = C::NF, EPB = C::EPB;
+  constexpr int Q2 = C::Q2, N2 = C::N2;
+  extern __shared__ double sm[];
+  double* sB = sm;
+  double* sD = sB + Q * N;
+  double* sl = sD + Q * Q;  // lm, lp
+  double* sw = sl + 2 * Q + N * N;
+  double* sU = sm + C::TAB;            // [EPB][NV][NM]
+  double* sQ = sU + EPB * NV * NM;     // [EPB][NV][NQ]
+  double* sG = sQ + EPB * NV * NQ;     // DIM arrays [EPB][NV][NQ]
+  double* sT = sG + EPB * DIM * NV * NQ;  // 2-D only: scratch
+  const int e0 = blockIdx.x * EPB;
+  const int nrep = EPB * NV;
+
+  stage_tables<DIM, P, Q>(tab, sm);
+  const double eps = v ? epsp[0] : 0.0;
+  for (int i = threadIdx.x; i < EPB * NV * NM; i += blockDim.x) {
+    const int eb = i / (NV * NM);
+    const long long g = (long long)(e0 + eb) * NV * NM + (i - eb * NV * NM);
+    double val = 0.0;
+    if (e0 + eb < E) {
+      val = u[g];
+      if (v) val = fma(eps, v[g], val);
+    }
+    sU[i] = val;
+  }
+  __syncthreads();
+  // BwdTrans: contract direction 0, 1 (, 2) with B
+  if (DIM == 2) {
+    contract<N, N, 1, 0, Q, N, 1, false>(sU, sT, sB, nrep);
+    __syncthreads();
+    contract<Q, N, 1, 1, Q, N, 1, false>(sT, sQ, sB, nrep);
+  } else {
+    double* t1 = sG + EPB * NV * NQ;       // reuse gradient slots 1 and 2
+    double* t2 = sG + 2 * EPB * NV * NQ;
+    contract<N, N, N2, 0, Q, N, 1, false>(sU, t1, sB, nrep);
+    __syncthreads();
+    contract<Q, N, N2, 1, Q, N, 1, false>(t1, t2, sB, nrep);
+    __syncthreads();
+    contract<Q, Q, N2, 2, Q, N, 1, false>(t2, sQ, sB, nrep);
+  }
+  __syncthreads();
+  // reference derivatives on the Gauss grid (exact for the degree-P expansion)
+  contract<Q, Q, Q2, 0, Q, Q, 1, false>(sQ, sG, sD, nrep);
+  contract<Q, Q, Q2, 1, Q, Q, 1, false>(sQ, sG + EPB * NV * NQ, sD, nrep);
+  if (DIM == 3) contract<Q, Q, Q2, 2, Q, Q, 1, false>(sQ, sG + 2 * EPB * NV * NQ, sD, nrep);
+  __syncthreads();
+  // volume flux at the Gauss points
+  for (int idx = threadIdx.x; idx < EPB * NQ; idx += blockDim.x) {
+    const int eb = idx / NQ, q = idx - eb * NQ;
+    const int e = e0 + eb;
+    if (e >= E) continue;
+    const ElemGeo g = geo[e];
+    int c[3];
+    grid_coords<DIM, Q>(q, c);
+    double U[NV], dU[DIM][NV], H[DIM][NV];
+    double rh[DIM];
+#pragma unroll
+    for (int r = 0; r < DIM; ++r) rh[r] = 2.0 / g.h[r];
+#pragma unroll
+    for (int vv = 0; vv < NV; ++vv) {
+      U[vv] = sQ[(eb * NV + vv) * NQ + q];
+#pragma unroll
+      for (int r = 0; r < DIM; ++r) dU[r][vv] = sG[((r * EPB + eb) * NV + vv) * NQ + q] * rh[r];
+    }
+    euler_flux<DIM>(U, ph, H);
+    if (ph.viscous) {
+      double G[DIM][NV];
+      viscous_flux<DIM>(U, dU, ph, G);
+#pragma unroll
+      for (int r = 0; r < DIM; ++r)
+#pragma unroll
+        for (int vv = 0; vv < NV; ++vv) H[r][vv] -= G[r][vv];
+    }
+    double wJ = sw[c[0]] * sw[c[1]] * (DIM == 3 ? sw[c[2]] : 1.0);
+    double detJ = 1.0;
+#pragma unroll
+    for (int r = 0; r < DIM; ++r) detJ *= 0.5 * g.h[r];
+    wJ *= detJ;
+    double* hb = hbuf + (long long)e * DIM * NV * NQ + q;
+#pragma unroll
+    for (int r = 0; r < DIM; ++r) {
+      const double s = wJ * rh[r];
+#pragma unroll
+      for (int vv = 0; vv < NV; ++vv) hb[(r * NV + vv) * NQ] = s * H[r][vv];
+    }
+  }
+  // face traces of Q and grad Q by Lagrange extrapolation along the normal
+  constexpr int NTR = 2 * DIM * (1 + DIM) * NV * NF;
+  for (int idx = threadIdx.x; idx < EPB * NTR; idx += blockDim.x) {
+    const int eb = idx / NTR;
+    int rem = idx - eb * NTR;
+    const int e = e0 + eb;
+    if (e >= E) continue;
+    const int p = rem % NF;
+    rem /= NF;
+    const int vv = rem % NV;
+    rem /= NV;
+    const int fld = rem % (1 + DIM);
+    const int lf = rem / (1 + DIM);
+    const int r = lf >> 1;
+    const double* lw = sl + (lf & 1) * Q;
+    const double* src = fld == 0 ? sQ + (eb * NV + vv) * NQ
+                                 : sG + (((fld - 1) * EPB + eb) * NV + vv) * NQ;
+    // grid offset of the face point and stride along direction r
+    int c[3] = {0, 0, 0};
+    if (DIM == 2) {
+      c[1 - r] = p;
+    } else {
+      const int t0 = r == 0 ? 1 : 0, t1 = r == 2 ? 1 : 2;
+      c[t0] = p % Q;
+      c[t1] = p / Q;
+    }
+    const int base = c[0] + Q * c[1] + Q * Q * c[2];
+    const int str = r == 0 ? 1 : (r == 1 ? Q : Q * Q);
+    double acc = 0.0;
+#pragma unroll
+    for (int k = 0; k < Q; ++k) acc = fma(lw[k], src[base + k * str], acc);
+    if (fld > 0) acc *= 2.0 / geo[e].h[fld - 1];
+    tbuf[(long long)e * NTR + ((lf * (1 + DIM) + fld) * NV + vv) * NF + p] = acc;
+  }
+}
+
+// ---------------------------------------------------------------- kernel 2
+template <int DIM, int P, int Q>
+__global__ void __launch_bounds__(128) face_kernel(const __grid_constant__ Tables tab,
+                                                   const __grid_constant__ Phys ph,
+                                                   const ElemGeo* __restrict__ geo,
+                                                   const int32_t* __restrict__ faces, int F,
+                                                   double t, const double* __restrict__ tbuf,
+                                                   double* __restrict__ fbuf) {
+  using C = Cfg<DIM, P, Q>;
+  constexpr int NV = C::NV, NF = C::NF;
+  constexpr int NTR = 2 * DIM * (1 + DIM) * NV * NF;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= F * NF) return;
+  const int f = idx / NF, p = idx - f * NF;
+  const int eL = faces[f * 6 + 0], fL = faces[f * 6 + 1];
+  const int eR = faces[f * 6 + 2], fR = faces[f * 6 + 3], bc = faces[f * 6 + 5];
+  const int r = fL >> 1;
+  const double sgn = (fL & 1) ? 1.0 : -1.0;
+  const ElemGeo gL = geo[eL];
+  // tangential Gauss indices of the face point
+  int pt[2] = {p % Q, DIM == 3 ? p / Q : 0};
+  double x[3] = {0, 0, 0};
+  double wJf = 1.0;
+  {
+    int a = 0;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+      if (k == r) {
+        x[k] = gL.x0[k] + ((fL & 1) ? gL.h[k] : 0.0);
+      } else {
+        x[k] = gL.x0[k] + 0.5 * (tab.x[pt[a]] + 1.0) * gL.h[k];
+        wJf *= tab.w[pt[a]] * 0.5 * gL.h[k];
+        ++a;
+      }
+    }
+  }
+  double QL[NV], dQL[DIM][NV], QR[NV], dQa[DIM][NV];
+  const double* tl = tbuf + (long long)eL * NTR + (fL * (1 + DIM)) * NV * NF + p;
+#pragma unroll
+  for (int vv = 0; vv < NV; ++vv) {
+    QL[vv] = tl[vv * NF];
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) dQL[j][vv] = tl[((1 + j) * NV + vv) * NF];
+  }
+  double hmin = gL.h[r], cfac;
+  double hR[DIM];
+  int bctype = 0;
+  if (eR >= 0) {
+    const ElemGeo gR = geo[eR];
+    hmin = fmin(hmin, gR.h[r]);
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) hR[k] = gR.h[k];
+    const double* tr = tbuf + (long long)eR * NTR + (fR * (1 + DIM)) * NV * NF + p;
+#pragma unroll
+    for (int vv = 0; vv < NV; ++vv) {
+      QR[vv] = tr[vv * NF];
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) dQa[j][vv] = 0.5 * (dQL[j][vv] + tr[((1 + j) * NV + vv) * NF]);
+    }
+    cfac = 0.5;
+  } else {
+    bctype = ph.bc[bc];
+#pragma unroll
+    for (int vv = 0; vv < NV; ++vv) {
+      QR[vv] = 0.0;
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) dQa[j][vv] = dQL[j][vv];
+    }
+    cfac = 1.0;
+  }
+  double Hn[NV], S[DIM][NV];
+  const double beta = (double)((P + 1) * (P + 1)) / hmin;
+  numerical_flux<DIM>(QL, QR, bctype, x, t, dQa, r, sgn, beta, ph, Hn, S);
+  double* fl = fbuf + (long long)eL * NTR + (fL * (1 + DIM)) * NV * NF + p;
+  const double cs = cfac * ph.beta_s * wJf;
+#pragma unroll
+  for (int vv = 0; vv < NV; ++vv) {
+    fl[vv * NF] = -Hn[vv] * wJf;
+#pragma unroll
+    for (int j = 0; j < DIM; ++j)
+      fl[((1 + j) * NV + vv) * NF] = ph.viscous ? cs * (2.0 / gL.h[j]) * S[j][vv] : 0.0;
+  }
+  if (eR >= 0) {
+    double* fr = fbuf + (long long)eR * NTR + (fR * (1 + DIM)) * NV * NF + p;
+#pragma unroll
+    for (int vv = 0; vv < NV; ++vv) {
+      fr[vv * NF] = Hn[vv] * wJf;
+#pragma unroll
+      for (int j = 0; j < DIM; ++j)
+        fr[((1 + j) * NV + vv) * NF] = ph.viscous ? cs * (2.0 / hR[j]) * S[j][vv] : 0.0;
+    }
+  }
+}
+
+// B^T then |J|^-1 (M1^-1)^(x)d on G [EPB][NV][NQ] -> result in R [EPB][NV][NM]
+template <int DIM, int P, int Q>
+__device__ __forceinline__ void bt_minv(double* sG, double* t1, double* t2, double* sR,
+                                        const double* sB, const double* sMi, int nrep) {
+  using C = Cfg<DIM, P, Q>;
+  constexpr int N = C::N, Q2 = C::Q2, N2 = C::N2;
+  if (DIM == 2) {
+    contract<Q, Q, 1, 1, N, 1, N, false>(sG, t1, sB, nrep);
+    __syncthreads();
+    contract<Q, N, 1, 0, N, 1, N, false>(t1, t2, sB, nrep);
+    __syncthreads();
+    contract<N, N, 1, 0, N, N, 1, false>(t2, t1, sMi, nrep);
+    __syncthreads();
+    contract<N, N, 1, 1, N, N, 1, false>(t1, sR, sMi, nrep);
+  } else {
+    contract<Q, Q, Q2, 2, N, 1, N, false>(sG, t1, sB, nrep);
+    __syncthreads();
+    contract<Q, Q, N2, 1, N, 1, N, false>(t1, t2, sB, nrep);
+    __syncthreads();
+    contract<Q, N, N2, 0, N, 1, N, false>(t2, t1, sB, nrep);
+    __syncthreads();
+    contract<N, N, N2, 0, N, N, 1, false>(t1, t2, sMi, nrep);
+    __syncthreads();
+    contract<N, N, N2, 1, N, N, 1, false>(t2, t1, sMi, nrep);
+    __syncthreads();
+    contract<N, N, N2, 2, N, N, 1, false>(t1, sR, sMi, nrep);
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------- kernel 3
+template <int DIM, int P, int Q>
+__global__ void __launch_bounds__(256) lift_kernel(const __grid_constant__ Tables tab,
+                                                   const ElemGeo* __restrict__ geo, int E,
+                                                   const double* __restrict__ hbuf,
+                                                   const double* __restrict__ fbuf,
+                                                   const double* __restrict__ force,
+                                                   const double* __restrict__ v,
+                                                   const double* __restrict__ r_u,
+                                                   const double* __restrict__ epsp, double alpha,
+                                                   double beta, double* __restrict__ out) {
+  using C = Cfg<DIM, P, Q>;
+  constexpr int N = C::N, NV = C::NV, NM = C::NM, NQ = C::NQ, NF = C::NF, EPB = C::EPB;
+  constexpr int Q2 = C::Q2;
+  constexpr int NTR = 2 * DIM * (1 + DIM) * NV * NF;
+  extern __shared__ double sm[];
+  double* sB = sm;
+  double* sD = sB + Q * N;
+  double* sl = sD + Q * Q;
+  double* sMi = sl + 2 * Q;
+  double* sH = sm + C::TAB;             // DIM arrays [EPB][NV][NQ]
+  double* sG = sH + DIM * EPB * NV * NQ;  // [EPB][NV][NQ]
+  double* t1 = sG + EPB * NV * NQ;
+  double* t2 = t1 + EPB * NV * NQ;
+  const int e0 = blockIdx.x * EPB;
+  const int nrep = EPB * NV;
+  stage_tables<DIM, P, Q>(tab, sm);
+  for (int i = threadIdx.x; i < EPB * DIM * NV * NQ; i += blockDim.x) {
+    const int eb = i / (DIM * NV * NQ), rem = i - eb * DIM * NV * NQ;
+    const int r = rem / (NV * NQ), o = rem - r * NV * NQ;
+    sH[(r * EPB + eb) * NV * NQ + o] =
+        e0 + eb < E ? hbuf[(long long)(e0 + eb) * DIM * NV * NQ + rem] : 0.0;
+  }
+  __syncthreads();
+  // J^T: spread the face fluxes of the 2*DIM faces onto the Gauss grid
+  for (int idx = threadIdx.x; idx < EPB * NV * NQ; idx += blockDim.x) {
+    const int eb = idx / (NV * NQ), rem = idx - eb * NV * NQ;
+    const int vv = rem / NQ, q = rem - vv * NQ;
+    const int e = e0 + eb;
+    double gsum = 0.0;
+    double hs[DIM];
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) hs[j] = 0.0;
+    if (e < E) {
+      int c[3];
+      grid_coords<DIM, Q>(q, c);
+      const double* fb = fbuf + (long long)e * NTR;
+#pragma unroll
+      for (int r = 0; r < DIM; ++r) {
+        const int p = face_point<DIM, Q>(c, r);
+        const double am = sl[c[r]], ap = sl[Q + c[r]];
+        const double* fm = fb + ((2 * r) * (1 + DIM) * NV + vv) * NF + p;
+        const double* fp = fb + ((2 * r + 1) * (1 + DIM) * NV + vv) * NF + p;
+        gsum = fma(am, fm[0], fma(ap, fp[0], gsum));
+#pragma unroll
+        for (int j = 0; j < DIM; ++j)
+          hs[j] = fma(am, fm[(1 + j) * NV * NF], fma(ap, fp[(1 + j) * NV * NF], hs[j]));
+      }
+    }
+    sG[idx] = gsum;
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) sH[j * EPB * NV * NQ + idx] += hs[j];
+  }
+  __syncthreads();
+  // G += sum_j D_j^T H_j
+  contract<Q, Q, Q2, 0, Q, 1, Q, true>(sH, sG, sD, nrep);
+  __syncthreads();
+  contract<Q, Q, Q2, 1, Q, 1, Q, true>(sH + EPB * NV * NQ, sG, sD, nrep);
+  __syncthreads();
+  if (DIM == 3) {
+    contract<Q, Q, Q2, 2, Q, 1, Q, true>(sH + 2 * EPB * NV * NQ, sG, sD, nrep);
+    __syncthreads();
+  }
+  double* sR = sH;  // reuse
+  bt_minv<DIM, P, Q>(sG, t1, t2, sR, sB, sMi, nrep);
+  for (int i = threadIdx.x; i < EPB * NV * NM; i += blockDim.x) {
+    const int eb = i / (NV * NM);
+    const int e = e0 + eb;
+    if (e >= E) continue;
+    const ElemGeo g = geo[e];
+    double idet = 1.0;
+#pragma unroll
+    for (int r = 0; r < DIM; ++r) idet *= 2.0 / g.h[r];
+    const long long gi = (long long)e * NV * NM + (i - eb * NV * NM);
+    double R = sR[i] * idet;
+    if (force) R += force[gi];
+    if (r_u) {
+      const double ie = epsp[1];
+      R = (R - r_u[gi]) * ie * beta;
+      if (alpha != 0.0) R = fma(alpha, v[gi], R);
+    }
+    out[gi] = R;
+  }
+}
+
+// L2 projection of the analytic field (what = 0) or of the forcing (what = 1)
+template <int DIM, int P, int Q>
+__global__ void __launch_bounds__(256) project_kernel(const __grid_constant__ Tables tab,
+                                                      const __grid_constant__ Phys ph,
+                                                      const ElemGeo* __restrict__ geo, int E,
+                                                      int what, double t,
+                                                      double* __restrict__ out) {
+  using C = Cfg<DIM, P, Q>;
+  constexpr int N = C::N, NV = C::NV, NM = C::NM, NQ = C::NQ, EPB = C::EPB;
+  extern __shared__ double sm[];
+  double* sB = sm;
+  double* sl = sB + Q * N + Q * Q;
+  double* sMi = sl + 2 * Q;
+  double* sw = sMi + N * N;
+  double* sH = sm + C::TAB;
+  double* sG = sH + DIM * EPB * NV * NQ;
+  double* t1 = sG + EPB * NV * NQ;
+  double* t2 = t1 + EPB * NV * NQ;
+  const int e0 = blockIdx.x * EPB;
+  stage_tables<DIM, P, Q>(tab, sm);
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < EPB * NQ; idx += blockDim.x) {
+    const int eb = idx / NQ, q = idx - eb * NQ;
+    const int e = e0 + eb;
+    double U[NV];
+#pragma unroll
+    for (int vv = 0; vv < NV; ++vv) U[vv] = 0.0;
+    if (e < E) {
+      const ElemGeo g = geo[e];
+      int c[3];
+      grid_coords<DIM, Q>(q, c);
+      double x[3] = {0, 0, 0};
+      double wJ = 1.0;
+      for (int r = 0; r < DIM; ++r) {
+        x[r] = g.x0[r] + 0.5 * (tab.x[c[r]] + 1.0) * g.h[r];
+        wJ *= sw[c[r]] * 0.5 * g.h[r];
+      }
+      if (what == 0)
+        exact_state(DIM, ph, x, t, U);
+      else
+        forcing(DIM, ph, x, U);
+#pragma unroll
+      for (int vv = 0; vv < NV; ++vv) U[vv] *= wJ;
+    }
+#pragma unroll
+    for (int vv = 0; vv < NV; ++vv) sG[(eb * NV + vv) * NQ + q] = U[vv];
+  }
+  __syncthreads();
+  bt_minv<DIM, P, Q>(sG, t1, t2, sH, sB, sMi, EPB * NV);
+  for (int i = threadIdx.x; i < EPB * NV * NM; i += blockDim.x) {
+    const int eb = i / (NV * NM);
+    const int e = e0 + eb;
+    if (e >= E) continue;
+    const ElemGeo g = geo[e];
+    double idet = 1.0;
+    for (int r = 0; r < DIM; ++r) idet *= 2.0 / g.h[r];
+    out[(long long)e * NV * NM + (i - eb * NV * NM)] = sH[i] * idet;
+  }
+}
+
+// ---------------------------------------------------------------- launchers
+template <int DIM, int P, int Q>
+static dg_status run_residual(dg_mesh_s* m, const EvalArgs& a, cudaStream_t s) {
+  using C = Cfg<DIM, P, Q>;
+  const int nb = (m->E + C::EPB - 1) / C::EPB;
+  const size_t vsm = sizeof(double) * C::VOL_SM, lsm = sizeof(double) * C::LIFT_SM;
+  DG_CUDA(cudaFuncSetAttribute(vol_kernel<DIM, P, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)vsm));
+  DG_CUDA(cudaFuncSetAttribute(lift_kernel<DIM, P, Q>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm));
+  vol_kernel<DIM, P, Q><<<nb, C::NT, vsm, s>>>(m->tab, m->phys, m->geo, m->E, a.u, a.v, a.eps,
+                                               m->hbuf, m->tbuf);
+  DG_CUDA(cudaGetLastError());
+  const int nfp = m->F * C::NF;
+  face_kernel<DIM, P, Q><<<(nfp + 127) / 128, 128, 0, s>>>(m->tab, m->phys, m->geo, m->faces,
+                                                           m->F, a.t, m->tbuf, m->fbuf);
+  DG_CUDA(cudaGetLastError());
+  lift_kernel<DIM, P, Q><<<nb, C::NT, lsm, s>>>(m->tab, m->geo, m->E, m->hbuf, m->fbuf, m->force,
+                                                a.v, a.r_u, a.eps, a.alpha, a.beta, a.out);
+  DG_CUDA(cudaGetLastError());
+  return DG_OK;
+}
+
+template <int DIM, int P, int Q>
+static dg_status run_project(dg_mesh_s* m, int what, double t, double* out, cudaStream_t s) {
+  using C = Cfg<DIM, P, Q>;
+  const int nb = (m->E + C::EPB - 1) / C::EPB;
+  const size_t lsm = sizeof(double) * C::LIFT_SM;
+  DG_CUDA(cudaFuncSetAttribute(project_kernel<DIM, P, Q>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm));
+  project_kernel<DIM, P, Q><<<nb, C::NT, lsm, s>>>(m->tab, m->phys, m->geo, m->E, what, t, out);
+  DG_CUDA(cudaGetLastError());
+  return DG_OK;
+}
+
+// (dim, P, Q) instances built into the library
+#define DG_INSTANCES(X)                                                                       \
+  X(2, 1, 3) X(2, 2, 3) X(2, 2, 4) X(2, 3, 5) X(2, 4, 6) X(2, 5, 7) X(2, 6, 8) X(3, 1, 3) \
+  X(3, 2, 4) X(3, 2, 5) X(3, 3, 5) X(3, 3, 6) X(3, 4, 6) X(3, 4, 8)
+
+bool supported(int dim, int P, int Q) {
+#define DG_SUP(D_, P_, Q_) \
+  if (dim == D_ && P == P_ && Q == Q_) return true;
+  DG_INSTANCES(DG_SUP)
+#undef DG_SUP
+  return false;
+}
+
+dg_status launch_residual(dg_mesh_s* m, const EvalArgs& a, cudaStream_t s) {
+#define DG_RUN(D_, P_, Q_) \
+  if (m->dim == D_ && m->P == P_ && m->Q == Q_) return run_residual<D_, P_, Q_>(m, a, s);
+  DG_INSTANCES(DG_RUN)
+#undef DG_RUN
+  return DG_ERR_UNSUPPORTED;
+}
+
+dg_status launch_project(dg_mesh_s* m, int what, double t, double* out, cudaStream_t s) {
+#define DG_RUN(D_, P_, Q_) \
+  if (m->dim == D_ && m->P == P_ && m->Q == Q_) return run_project<D_, P_, Q_>(m, what, t, out, s);
+  DG_INSTANCES(DG_RUN)
+#undef DG_RUN
+  return DG_ERR_UNSUPPORTED;
+}
+
+}  // namespace dg

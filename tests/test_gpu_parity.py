@@ -1,0 +1,179 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle on
+the same seeded inputs: residual (1e-12 relative), projection, JFNK product
+(1e-6 relative: the difference quotient amplifies rounding of R by 1/eps),
+BRJ apply, GMRES and SDIRK (equal Newton and GMRES iteration counts)."""
+import numpy as np
+import pytest
+import torch
+
+import workloads as w
+from oracle.dg import DG
+from oracle import implicit as im
+from oracle import physics as phy
+
+pytestmark = pytest.mark.gpu
+
+R_TOL = 1e-12
+JVP_TOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def dgl():
+    import paper_2002_04222_gb300 as dgl
+    return dgl
+
+
+def to_dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def perturbed(dg, seed=0, amp=0.01):
+    u = dg.project_exact()
+    return u + amp * w.random_direction(u, seed)
+
+
+CASES = {
+    "vortex8_P2": lambda: w.vortex_case(n=8, P=2),
+    "vortex_hllc_P3": lambda: w.vortex_case(n=5, P=3, Q=5, riemann=phy.RIEMANN_HLLC),
+    "vortex_euler_P2": lambda: w.vortex_case(n=4, P=2, viscous=False),
+    "poiseuille_P1": lambda: w.poiseuille_case(1),
+    "poiseuille_P3": lambda: w.poiseuille_case(3, nx=6, ny=4),
+    "poiseuille_P6": lambda: w.poiseuille_case(6, nx=4, ny=2),
+    "box_P1": lambda: w.small_tgv_case((3, 2, 2), P=1),
+    "box_P2_Q4": lambda: w.small_tgv_case((3, 3, 2), P=2, Q=4, stretch=True),
+    "box_P3_Q6": lambda: w.small_tgv_case((3, 2, 3), P=3),
+    "box_P4_Q8": lambda: w.small_tgv_case((2, 2, 2), P=4, riemann=phy.RIEMANN_HLLC),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_residual_parity(dgl, name):
+    c = CASES[name]()
+    dg = DG(c.mesh, c.P, c.Q, c.phys)
+    m = dgl.Mesh.from_case(c)
+    u = perturbed(dg)
+    R_ref = dg.residual(u, 0.0)
+    R = m.residual(to_dev(u)).cpu().numpy()
+    assert rel(R, R_ref) < R_TOL
+    assert np.abs(R - R_ref).max() < R_TOL * np.abs(R_ref).max() * 10
+
+
+@pytest.mark.parametrize("name", ["vortex8_P2", "poiseuille_P3", "box_P3_Q6"])
+def test_projection_parity(dgl, name):
+    c = CASES[name]()
+    dg = DG(c.mesh, c.P, c.Q, c.phys)
+    m = dgl.Mesh.from_case(c)
+    ref = dg.project_exact(0.0)
+    got = m.project(0.0).cpu().numpy()
+    assert rel(got, ref) < 1e-13
+
+
+def test_residual_repeats_bitwise(dgl):
+    c = CASES["box_P3_Q6"]()
+    m = dgl.Mesh.from_case(c)
+    u = to_dev(perturbed(DG(c.mesh, c.P, c.Q, c.phys)))
+    a = m.residual(u)
+    b = m.residual(u)
+    assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("name", ["vortex8_P2", "poiseuille_P3", "box_P2_Q4", "box_P3_Q6"])
+def test_jvp_parity(dgl, name):
+    c = CASES[name]()
+    dg = DG(c.mesh, c.P, c.Q, c.phys)
+    m = dgl.Mesh.from_case(c)
+    u = perturbed(dg)
+    v = w.random_direction(u, 7)
+    R = dg.residual(u)
+    ud, Rd, vd = to_dev(u), to_dev(R), to_dev(v)
+    for alpha, beta in ((0.0, 1.0), (1.0, -0.013)):
+        ref = im.jvp(dg, u, R, 0.0, v, alpha, beta)
+        got = m.jvp(ud, Rd, vd, 0.0, alpha, beta).cpu().numpy()
+        assert rel(got, ref) < JVP_TOL
+    zero = m.jvp(ud, Rd, torch.zeros_like(vd), 0.0, 1.0, -0.1).cpu().numpy()
+    assert np.all(zero == 0.0)
+
+
+def test_free_stream_and_conservation_on_gpu(dgl):
+    c = w.small_tgv_case((3, 2, 2), P=3)
+    dg = DG(c.mesh, c.P, c.Q, c.phys)
+    m = dgl.Mesh.from_case(c)
+    one = np.round(dg.one_coeffs(), 10)
+    U0 = phy.exact_state(c.phys, np.zeros((1, 3)), 0.0)[0]
+    u = U0[None, :, None] * one[None, None, :] * np.ones((dg.E, 1, 1))
+    R = m.residual(to_dev(u)).cpu().numpy()
+    Mx = np.linalg.inv(dg.Minv)
+    L = np.einsum("emn,evn->evm", Mx, R)
+    scale = np.abs(np.einsum("emn,evn->evm", Mx, dg.apply_minv(dg.rhs(u, faces=False)))).sum(axis=2).max()
+    assert np.abs(L).max() < 1e-12 * scale
+    ur = perturbed(dg, amp=0.05)
+    R = m.residual(to_dev(ur)).cpu().numpy()
+    L = np.einsum("emn,evn->evm", Mx, R)
+    tot = np.einsum("evm,m->v", L, dg.one_coeffs())
+    assert np.all(np.abs(tot) < 1e-12 * np.abs(L).sum(axis=(0, 2)))
+
+
+@pytest.mark.parametrize("name,precision,tol", [("vortex8_P2", "fp64", 1e-6),
+                                                ("poiseuille_P3", "fp64", 1e-6),
+                                                ("box_P2_Q4", "fp64", 1e-6),
+                                                ("box_P2_Q4", "fp32", 1e-4),
+                                                ("box_P3_Q6", "bf16", 3e-2)])
+def test_precond_apply_parity(dgl, name, precision, tol):
+    c = CASES[name]()
+    dg = DG(c.mesh, c.P, c.Q, c.phys)
+    m = dgl.Mesh.from_case(c)
+    u = perturbed(dg)
+    dt_a = 0.02
+    ref_pc = im.BRJ(dg, u, 0.0, dt_a, J=7)
+    q = w.random_direction(u, 3)
+    ref = ref_pc.apply(q)
+    pc = dgl.Precond(m).build(to_dev(u), 0.0, dt_a, J=7, precision=precision)
+    got = pc.apply(to_dev(q)).cpu().numpy()
+    assert rel(got, ref) < tol
+    # J = 1 is plain block Jacobi
+    ref_pc.J = 1
+    pc1 = dgl.Precond(m).build(to_dev(u), 0.0, dt_a, J=1, precision=precision)
+    assert rel(pc1.apply(to_dev(q)).cpu().numpy(), ref_pc.apply(q)) < tol
+
+
+@pytest.mark.parametrize("name", ["vortex8_P2", "box_P2_Q4"])
+def test_gmres_parity(dgl, name):
+    c = CASES[name]()
+    dg = DG(c.mesh, c.P, c.Q, c.phys)
+    m = dgl.Mesh.from_case(c)
+    u = perturbed(dg)
+    R = dg.residual(u)
+    dt_a = 0.05
+    b = w.random_direction(u, 11)
+    pc_ref = im.BRJ(dg, u, 0.0, dt_a, J=7)
+    A = lambda v: im.jvp(dg, u, R, 0.0, v, 1.0, -dt_a)
+    cfg = im.GmresConfig(restart=20, rtol=1e-3, max_cycles=5)
+    x_ref, st_ref = im.gmres(A, b, pc_ref.apply, cfg)
+    pc = dgl.Precond(m).build(to_dev(u), 0.0, dt_a, J=7)
+    x, st = m.gmres(to_dev(u), to_dev(R), to_dev(b), 0.0, dt_a, pc, restart=20, max_cycles=5, rtol=1e-3)
+    assert st["iters"] == st_ref.iters
+    assert rel(x.cpu().numpy(), x_ref) < 1e-5
+
+
+def test_sdirk_step_parity_vortex_cfg(dgl):
+    """One SDIRK2 step of the 8x8 P=2 vortex at dt = 0.01 (BRJ(7), restart 20):
+    equal Newton and GMRES counts per stage and the same u^{n+1}."""
+    c = w.vortex_case(n=8, P=2)
+    dg = DG(c.mesh, c.P, c.Q, c.phys)
+    m = dgl.Mesh.from_case(c)
+    u0 = dg.project_exact()
+    dt = 0.01
+    lam = 1 - np.sqrt(2) / 2
+    pc_ref = im.BRJ(dg, u0, 0.0, dt * lam, J=7)
+    cfg = im.NewtonConfig(alpha=1e-3, gmres=im.GmresConfig(restart=20))
+    u1_ref, st_ref = im.sdirk_step(dg, u0, 0.0, dt, "sdirk2", pc_ref.apply, cfg)
+    ud = to_dev(u0)
+    st = m.sdirk_step(ud, 0.0, dt, restart=20, J=7)
+    assert st["converged"]
+    assert st["stage_newton"] == [s.iters for s in st_ref.stages]
+    assert st["stage_gmres"] == [s.gmres_iters for s in st_ref.stages]
+    assert rel(ud.cpu().numpy(), u1_ref) < 1e-9
