@@ -1,0 +1,394 @@
+#!/usr/bin/env python
+"""Benchmark of the implicit DG hot path on one GB300 (or N replicas).
+
+A step is one SDIRK2 step (Sec. 3.2, App. A) of the 3-D Taylor-Green vortex on
+16^3 periodic hexahedra, P = 3, Q = 6 Gauss points per direction (the
+over-integration rule ceil(3(P+1)/2)), Re = 1600, Ma = 0.1, at 10x the explicit
+time step (CFL 0.10): each stage runs Newton (alpha = 1e-3 relative
+tolerance) with right-preconditioned restarted GMRES(30, rtol 5e-2), the
+Jacobian-free product and BRJ(7), the preconditioner rebuilt every 10 steps
+(frozen in between).  All arithmetic of the residual, the JFNK difference, the
+Krylov vectors and Newton is FP64; the BRJ blocks are stored in the chosen
+precision (default FP32, as in the paper).
+
+Output: one JSON line (rank 0).  `value` = DOF-steps per second over all
+ranks (n_dof x steps / time); `e2e` repeats the measurement through host
+buffers (host->device copy of u before and device->host copy after every
+step); `roofline` describes the kernel with the largest device time in the
+step; `cpu_baseline` times the CPU oracle on a bounded sample.
+
+--impl reference runs the CPU oracle as the reference arm (rank 0 only).
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = {"n": 16, "P": 3, "Q": 6, "Re": 1600.0, "Ma": 0.1, "cfl": 0.10, "dt_factor": 10.0}
+SAMPLE_N = 3          # CPU sample: the same case on 3^3 elements (same P, Q, CFL)
+FREEZE = 10
+
+
+def tgv_dt(n, P, Ma, cfl=0.10, factor=10.0):
+    """dt = factor x the explicit step of Eq. CFL (c_lambda = 0.2, d_RK = 2) with
+    c + |u| = 1/Ma + 1 (T = 1, |u| <= 1 for the Taylor-Green field)."""
+    dx = 2 * math.pi / n
+    return factor * cfl * 2.0 * dx / (0.2 * (1.0 / Ma + 1.0) * P * P)
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(path)), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9 and f[1].isdigit():
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        mhz = sorted(int(r[1]) for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": mhz[len(mhz) // 2], "sm_max_mhz": int(rows[0][2]), "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ work model
+def residual_flops_per_elem(P, Q, d=3):
+    """Algorithmic FP64 flops (FMA = 2) of one residual per element, as the
+    three kernels implement it; c_F / c_T = flops of the volume flux per Gauss
+    point and of the face flux per face point (counted from the flux code)."""
+    n, nv = P + 1, d + 2
+    c_F, c_T = 190, 420
+    bwd = 2 * nv * (n ** 3 * Q + n * n * Q * Q + n * Q ** 3)
+    grad = 2 * d * nv * Q ** 4
+    trace = 2 * (2 * d) * (1 + d) * nv * Q ** 2 * Q
+    vol = bwd + grad + c_F * Q ** 3 + trace
+    face = d * Q ** 2 * c_T                   # d faces per element
+    spread = 2 * 2 * d * (1 + d) * nv * Q ** 3
+    lift = spread + grad + bwd + 2 * d * nv * n ** 4
+    return {"dg_vol": vol, "dg_face": face, "dg_lift": lift}
+
+
+def kernel_work(name, launches, E, nb, prec_bytes, P, Q):
+    """(bound, algorithmic units per launch, unit) of a kernel family."""
+    f = residual_flops_per_elem(P, Q)
+    if name in f:
+        return "alu", f[name] * E, "flop"
+    if name == "brj_diag":
+        return "hbm", E * (nb * nb * prec_bytes + 2 * nb * 8), "byte"
+    if name in ("multi_dot", "multi_axpy", "dot", "vector"):
+        return "hbm", None, "byte"
+    return None, None, None
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args, rank, world):
+    import torch
+    import torch.distributed as dist
+    import workloads as w
+    import paper_2002_04222_gb300 as dgl
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    wl = WORKLOAD
+    case = w.tgv_case(n=wl["n"], P=wl["P"], Q=wl["Q"], Re=wl["Re"], Ma=wl["Ma"])
+    dt = tgv_dt(wl["n"], wl["P"], wl["Ma"], wl["cfl"], wl["dt_factor"])
+    m = dgl.Mesh.from_case(case)
+    ndof = m.info["n_dof"]
+    E = m.info["n_elem"]
+    nb = m.info["n_var"] * m.info["n_mode"]
+    u = m.project(0.0)
+    pc = dgl.Precond(m)
+    kw = dict(restart=30, rtol=5e-2, alpha=1e-3, J=7, precision=args.precision)
+    state = {"k": 0, "t": 0.0}
+    stats = []
+
+    def step(uu):
+        st = m.sdirk_step(uu, state["t"], dt, precond=pc, rebuild=(state["k"] % FREEZE == 0), **kw)
+        state["k"] += 1
+        state["t"] += dt
+        stats.append(st)
+        return st
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step(u)
+    torch.cuda.synchronize()
+    clocks = Clocks(dev)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = dgl.kernel_launches()
+    stats.clear()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(u)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = dgl.kernel_launches() - l0
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    timed_stats = list(stats)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * ndof * args.steps / (ms / 1e3)
+
+    # per-kernel device time over the same number of further steps (CUDA events
+    # on the launch stream, recorded by the library)
+    dgl.profile_enable(True)
+    dgl.profile_read()
+    for _ in range(args.steps):
+        step(u)
+    prof = dgl.profile_read()
+    dgl.profile_enable(False)
+    total_k = sum(v[1] for v in prof.values())
+    dom = max(prof, key=lambda k: prof[k][1])
+    pk, how = peaks()
+    prec_bytes = {"fp64": 8, "fp32": 4, "bf16": 2}[args.precision]
+    bound, work, unit = kernel_work(dom, prof[dom][0], E, nb, prec_bytes, wl["P"], wl["Q"])
+    avg_ms = prof[dom][1] / prof[dom][0]
+    roof = {"kernel": dom, "launches": prof[dom][0], "avg_ms": avg_ms,
+            "share": prof[dom][1] / total_k, "traffic": None}
+    clock_mhz = clk.get("sm_max_mhz") or pk.get("sm_max_mhz", 2070.0)
+    if bound == "hbm":
+        roof.update(bound="hbm", achieved=work / (avg_ms / 1e3) / 1e9, peak=pk["hbm_gbs"], unit="GB/s",
+                    peak_source=how)
+    elif bound == "alu":
+        peak = 4.0 * 152 * clock_mhz * 1e6 / 1e12   # FP64: 2 DFMA/clk/SM
+        roof.update(bound="alu", achieved=work / (avg_ms / 1e3) / 1e12, peak=peak, unit="TFLOP/s",
+                    peak_source="FP64 units x SM clock (152 SMs x 4 flop/clk x sm_max_mhz)")
+    else:
+        roof.update(bound=None, achieved=None, peak=None, unit=None)
+    if roof.get("achieved") is not None:
+        roof["frac"] = roof["achieved"] / roof["peak"]
+    kernels = {k: {"launches": v[0], "ms": round(v[1], 3), "share": round(v[1] / total_k, 4)}
+               for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
+
+    # residual throughput (GDOF/s) on the same mesh and state
+    r = m.residual(u)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    nres = 20
+    for _ in range(nres):
+        m.residual(u, out=r)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    res_ms = e0.elapsed_time(e1) / nres
+
+    # end to end through host buffers
+    e2e = None
+    if not args.no_e2e:
+        host = torch.empty(u.shape, dtype=torch.float64, pin_memory=True)
+        host.copy_(u)
+        dev_u = torch.empty_like(u)
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            dev_u.copy_(host, non_blocking=True)
+            step(dev_u)
+            host.copy_(dev_u, non_blocking=True)
+            torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([el], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        nbytes = ndof * 8
+        e2e = {"value": world * ndof * args.steps / el, "unit": "DOF*step/s",
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+
+    newton = [s["newton_iters"] for s in timed_stats]
+    gm = [s["gmres_iters"] for s in timed_stats]
+    out = {
+        "metric": "SDIRK2 step throughput at fixed Newton tolerance (DOF-steps/s); "
+                  "TGV 16^3 hexes P=3, 10x explicit dt",
+        "value": value,
+        "unit": "DOF*step/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic (analytic Taylor-Green initial field)",
+        "config": {"workload": f"tgv{wl['n']}^3_P{wl['P']}_Q{wl['Q']}_sdirk2_dt{wl['dt_factor']:g}xexplicit",
+                   "n_dof": ndof, "dt": dt, "newton_alpha": 1e-3, "gmres": "restart 30, rtol 5e-2",
+                   "precond": f"BRJ(7) {args.precision} blocks, rebuilt every {FREEZE} steps",
+                   "l2": "working set > L2 (BRJ blocks %.2f GB read per sweep)" % (E * nb * nb * prec_bytes / 1e9),
+                   "parallelism": f"replicas x{world}"},
+        "newton_per_step": sum(newton) / len(newton),
+        "gmres_per_step": sum(gm) / len(gm),
+        "residual_gdofs": ndof / (res_ms / 1e3) / 1e9,
+        "residual_ms": res_ms,
+        "gpu_launches": launches,
+        "clocks": clk,
+        "roofline": roof,
+        "kernels": kernels,
+        "e2e": e2e,
+    }
+    return out
+
+
+# ------------------------------------------------------------------ CPU oracle
+def oracle_sample(steps, warmup):
+    """The CPU oracle (as it stands) on the bounded sample: same P, Q and CFL on
+    SAMPLE_N^3 elements; BRJ built every FREEZE steps."""
+    import numpy as np
+    import workloads as w
+    from oracle.dg import DG
+    from oracle import implicit as im
+    wl = WORKLOAD
+    c = w.tgv_case(n=SAMPLE_N, P=wl["P"], Q=wl["Q"], Re=wl["Re"], Ma=wl["Ma"])
+    dg = DG(c.mesh, c.P, c.Q, c.phys)
+    u = dg.project_exact()
+    dt = tgv_dt(SAMPLE_N, wl["P"], wl["Ma"], wl["cfl"], wl["dt_factor"])
+    lam = 1 - math.sqrt(2) / 2
+    cfg = im.NewtonConfig(alpha=1e-3, gmres=im.GmresConfig(restart=30, rtol=5e-2))
+    pc = None
+    t = 0.0
+    times = []
+    for k in range(warmup + steps):
+        t0 = time.perf_counter()
+        if k % FREEZE == 0:
+            pc = im.BRJ(dg, u, t, dt * lam, J=7)
+        u, _ = im.sdirk_step(dg, u, t, dt, "sdirk2", pc.apply, cfg)
+        t += dt
+        times.append(time.perf_counter() - t0)
+    timed = times[warmup:]
+    return u.size, sum(timed), len(timed)
+
+
+def cpu_baseline_sample():
+    """One build + one step of the oracle on the sample, amortised like the
+    GPU run (build every FREEZE steps)."""
+    import workloads as w
+    from oracle.dg import DG
+    from oracle import implicit as im
+    wl = WORKLOAD
+    c = w.tgv_case(n=SAMPLE_N, P=wl["P"], Q=wl["Q"], Re=wl["Re"], Ma=wl["Ma"])
+    dg = DG(c.mesh, c.P, c.Q, c.phys)
+    u = dg.project_exact()
+    dt = tgv_dt(SAMPLE_N, wl["P"], wl["Ma"], wl["cfl"], wl["dt_factor"])
+    lam = 1 - math.sqrt(2) / 2
+    cfg = im.NewtonConfig(alpha=1e-3, gmres=im.GmresConfig(restart=30, rtol=5e-2))
+    t0 = time.perf_counter()
+    pc = im.BRJ(dg, u, 0.0, dt * lam, J=7)
+    tb = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    im.sdirk_step(dg, u, 0.0, dt, "sdirk2", pc.apply, cfg)
+    ts = time.perf_counter() - t0
+    per_step = ts + tb / FREEZE
+    return {"value": u.size / per_step, "unit": "DOF*step/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"TGV {SAMPLE_N}^3 hexes P={wl['P']} Q={wl['Q']} ({u.size} DOF), same CFL: one BRJ "
+                      f"build ({tb:.1f} s, amortised over {FREEZE} steps) + one SDIRK2 step ({ts:.1f} s), "
+                      f"numpy FP64"}
+
+
+def run_reference(args):
+    ndof, secs, k = oracle_sample(args.steps, args.warmup)
+    value = ndof * k / secs
+    return {
+        "impl": "reference",
+        "metric": "SDIRK2 step throughput at fixed Newton tolerance (DOF-steps/s); "
+                  "TGV 16^3 hexes P=3, 10x explicit dt",
+        "value": value, "unit": "DOF*step/s", "n_gpus": 1, "steps": k, "warmup": args.warmup,
+        "ms_per_step": secs / k * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (analytic Taylor-Green initial field)",
+        "config": {"workload": f"tgv{WORKLOAD['n']}^3_P{WORKLOAD['P']}_Q{WORKLOAD['Q']}_sdirk2_dt10xexplicit",
+                   "sample": f"{SAMPLE_N}^3 elements, same P, Q, CFL"},
+        "cpu_baseline": {"value": value, "unit": "DOF*step/s", "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": f"TGV {SAMPLE_N}^3 hexes, {ndof} DOF, {k} steps after {args.warmup} "
+                                   f"warm-up, BRJ rebuilt every {FREEZE} steps"},
+        "e2e": {"value": value, "unit": "DOF*step/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "bf16"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)), flush=True)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    out = run_ours(args, rank, world)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline_sample()
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -145,8 +145,8 @@ dg_status dg_precond_destroy(dg_precond_t p);
  * (I - dt_a dR/du(u)) x = b with the Jacobian-free product at (u, r_u):
  * x0 = 0, Arnoldi by classical Gram-Schmidt applied twice with fixed-order
  * FP64 reductions, Givens rotations, stop when the residual estimate is
- * <= rtol*||b||, at most max_cycles restarts of length restart.  p may be
- * NULL (no preconditioner). */
+ * <= rtol*||b||, at most max_cycles restarts of length restart
+ * (1 <= restart <= 64).  p may be NULL (no preconditioner). */
 typedef struct {
   int restart;
   int max_cycles;
@@ -185,6 +185,23 @@ typedef struct {
 } dg_step_stats;
 dg_status sdirk_step(dg_mesh_t m, const dg_sdirk_cfg* cfg, double* u_inout, double t, double dt,
                      dg_precond_t* p_inout, dg_step_stats* stats, void* stream);
+
+/* Number of CUDA kernels this library has launched since it was loaded
+ * (all handles, all streams); a diagnostic counter for benchmarks. */
+long long dg_kernel_launches(void);
+
+/* Per-kernel timing (diagnostics, not part of the method): while enabled,
+ * the library brackets each of its kernel launches with CUDA events on the
+ * launch stream.  dg_profile_read synchronises the device and returns, per
+ * kernel family, the launch count and summed device time since the previous
+ * read (at most cap entries in out, *n set to the number written). */
+typedef struct {
+  char name[24];
+  long long launches;
+  double ms;
+} dg_kernel_time;
+dg_status dg_profile_enable(int on);
+dg_status dg_profile_read(dg_kernel_time* out, int cap, int* n);
 
 /* Static description of a status code. */
 const char* dg_status_string(dg_status s);

@@ -163,11 +163,11 @@ class BRJ:
             JL, JR = self._trace_jacobians(g, u, t, chi)           # [f][p][k][l]
             wJ = g["wJ"]
             BL = dg.Bf[g["fL"]]
-            blk = -np.einsum("pm,fp,fpkl,pn->fkmln", BL, wJ, JL, BL)
+            blk = -np.einsum("pm,fp,fpkl,pn->fkmln", BL, wJ, JL, BL, optimize=True)
             np.add.at(dLdu, g["eL"], blk.reshape(-1, self.nb, self.nb))
             if g["bctype"] is None:
                 BR = dg.Bf[g["fR"]]
-                blk = np.einsum("pm,fp,fpkl,pn->fkmln", BR, wJ, JR, BR)
+                blk = np.einsum("pm,fp,fpkl,pn->fkmln", BR, wJ, JR, BR, optimize=True)
                 np.add.at(dLdu, g["eR"], blk.reshape(-1, self.nb, self.nb))
                 self.off.append((g, JL, JR))
         # D = I - dt_a M^-1 dL/du (diagonal blocks), then invert
@@ -204,8 +204,8 @@ class BRJ:
         DB = np.einsum("eqrj,rqm->ejqm", dg.ginv, dg.D)
         wJ = dg.wJ
         # volume terms 1 and 2 of Eq. Jacobian-matrix-form2
-        T = np.einsum("eq,ejqm,eqjkl,qn->ekmln", wJ, DB, A0, dg.B)
-        T += np.einsum("eq,ejqm,eqjikl,eiqn->ekmln", wJ, DB, A1, DB)
+        T = np.einsum("eq,ejqm,eqjkl,qn->ekmln", wJ, DB, A0, dg.B, optimize=True)
+        T += np.einsum("eq,ejqm,eqjikl,eiqn->ekmln", wJ, DB, A1, DB, optimize=True)
         return T.reshape(E, nv * nm, nv * nm)
 
     def _flux_only(self, g, QL, QR, dQa, t):

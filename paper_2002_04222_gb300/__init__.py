@@ -157,3 +157,20 @@ class Precond:
             self.close()
         except Exception:
             pass
+
+
+def kernel_launches():
+    """Number of CUDA kernels the library has launched since it was loaded."""
+    return int(lib().dg_kernel_launches())
+
+
+def profile_enable(on=True):
+    _check("dg_profile_enable", lib().dg_profile_enable(int(on)))
+
+
+def profile_read(cap=32):
+    """{kernel family: (launches, total ms)} since the previous read."""
+    arr = (_lib.KernelTime * cap)()
+    n = ctypes.c_int()
+    _check("dg_profile_read", lib().dg_profile_read(arr, cap, ctypes.byref(n)))
+    return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].ms)) for i in range(n.value)}

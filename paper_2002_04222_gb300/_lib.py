@@ -73,6 +73,10 @@ class StepStats(ctypes.Structure):
                 ("stage_res", ctypes.c_double * 4)]
 
 
+class KernelTime(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_longlong), ("ms", ctypes.c_double)]
+
+
 # exported symbols and their argument types (mirrors include/dg.h)
 VP, D, I = ctypes.c_void_p, ctypes.c_double, ctypes.c_int
 SIGNATURES = {
@@ -88,6 +92,9 @@ SIGNATURES = {
     "dg_gmres": [VP, VP, VP, VP, D, D, VP, VP, ctypes.POINTER(GmresCfg), ctypes.POINTER(GmresStats), VP],
     "sdirk_step": [VP, ctypes.POINTER(SdirkCfg), VP, D, D, ctypes.POINTER(VP), ctypes.POINTER(StepStats), VP],
     "dg_status_string": [I],
+    "dg_kernel_launches": [],
+    "dg_profile_enable": [I],
+    "dg_profile_read": [ctypes.POINTER(KernelTime), I, ctypes.POINTER(I)],
 }
 
 
@@ -98,7 +105,8 @@ def load(path=LIB_PATH):
     for name, args in SIGNATURES.items():
         fn = getattr(lib, name)
         fn.argtypes = args
-        fn.restype = ctypes.c_char_p if name == "dg_status_string" else ctypes.c_int
+        fn.restype = {"dg_status_string": ctypes.c_char_p,
+                      "dg_kernel_launches": ctypes.c_longlong}.get(name, ctypes.c_int)
     return lib
 
 

@@ -47,9 +47,9 @@ __global__ void __launch_bounds__(RT) finish_kernel(const double* __restrict__ p
 
 dg_status dot(const double* a, const double* b, long long n, double* partial, double* out,
               cudaStream_t s) {
-  dot_partial_kernel<<<RED_BLOCKS, RT, 0, s>>>(a, b, n, partial);
-  finish_kernel<<<1, RT, 0, s>>>(partial, RED_BLOCKS, 1, out);
-  DG_CUDA(cudaGetLastError());
+  DG_PROF(K_DOT, s, dot_partial_kernel<<<RED_BLOCKS, RT, 0, s>>>(a, b, n, partial));
+  DG_PROF(K_DOT, s, finish_kernel<<<1, RT, 0, s>>>(partial, RED_BLOCKS, 1, out));
+  DG_LAUNCHED(2);
   return DG_OK;
 }
 
@@ -81,9 +81,9 @@ __global__ void __launch_bounds__(RT) multi_dot_kernel(const double* __restrict_
 dg_status multi_dot(const double* V, int k, const double* w, long long n, double* partial,
                     double* out, cudaStream_t s) {
   dim3 grid(RED_BLOCKS, (k + 7) / 8);
-  multi_dot_kernel<<<grid, RT, 0, s>>>(V, k, w, n, partial);
-  finish_kernel<<<k, RT, 0, s>>>(partial, RED_BLOCKS, k, out);
-  DG_CUDA(cudaGetLastError());
+  DG_PROF(K_MULTIDOT, s, multi_dot_kernel<<<grid, RT, 0, s>>>(V, k, w, n, partial));
+  DG_PROF(K_MULTIDOT, s, finish_kernel<<<k, RT, 0, s>>>(partial, RED_BLOCKS, k, out));
+  DG_LAUNCHED(2);
   return DG_OK;
 }
 
@@ -105,8 +105,8 @@ static int grid_for(long long n) {
 
 dg_status multi_axpy(double* w, const double* V, int k, const double* h, long long n,
                      cudaStream_t s) {
-  multi_axpy_kernel<<<grid_for(n), 256, 0, s>>>(w, V, k, h, n);
-  DG_CUDA(cudaGetLastError());
+  DG_PROF(K_MULTIAXPY, s, multi_axpy_kernel<<<grid_for(n), 256, 0, s>>>(w, V, k, h, n));
+  DG_LAUNCHED(1);
   return DG_OK;
 }
 
@@ -117,8 +117,8 @@ __global__ void axpby_kernel(double* __restrict__ y, double a, const double* __r
     y[i] = fma(a, x[i], b * y[i]);
 }
 dg_status axpby(double* y, double a, const double* x, double b, long long n, cudaStream_t s) {
-  axpby_kernel<<<grid_for(n), 256, 0, s>>>(y, a, x, b, n);
-  DG_CUDA(cudaGetLastError());
+  DG_PROF(K_VEC, s, axpby_kernel<<<grid_for(n), 256, 0, s>>>(y, a, x, b, n));
+  DG_LAUNCHED(1);
   return DG_OK;
 }
 
@@ -130,8 +130,8 @@ __global__ void lincomb_kernel(double* __restrict__ y, const double* __restrict_
 }
 dg_status lincomb(double* y, const double* x, double a, const double* z, double b, long long n,
                   cudaStream_t s) {
-  lincomb_kernel<<<grid_for(n), 256, 0, s>>>(y, x, a, z, b, n);
-  DG_CUDA(cudaGetLastError());
+  DG_PROF(K_VEC, s, lincomb_kernel<<<grid_for(n), 256, 0, s>>>(y, x, a, z, b, n));
+  DG_LAUNCHED(1);
   return DG_OK;
 }
 
@@ -146,7 +146,7 @@ __global__ void scale_dev_kernel(double* __restrict__ y, const double* __restric
 dg_status scale_dev(double* y, const double* x, const double* sdev, int inv, long long n,
                     cudaStream_t s) {
   scale_dev_kernel<<<grid_for(n), 256, 0, s>>>(y, x, sdev, inv, n);
-  DG_CUDA(cudaGetLastError());
+  DG_LAUNCHED(1);
   return DG_OK;
 }
 
@@ -172,10 +172,10 @@ __global__ void eps_finish_kernel(const double* __restrict__ partial, double* __
 
 dg_status jvp_eps(const double* u, const double* v, long long n, double* partial, double* eps,
                   cudaStream_t s) {
-  dot_partial_kernel<<<RED_BLOCKS, RT, 0, s>>>(u, u, n, partial);
-  dot_partial_kernel<<<RED_BLOCKS, RT, 0, s>>>(v, v, n, partial + RED_BLOCKS);
-  eps_finish_kernel<<<1, RT, 0, s>>>(partial, eps);
-  DG_CUDA(cudaGetLastError());
+  DG_PROF(K_DOT, s, dot_partial_kernel<<<RED_BLOCKS, RT, 0, s>>>(u, u, n, partial));
+  DG_PROF(K_DOT, s, dot_partial_kernel<<<RED_BLOCKS, RT, 0, s>>>(v, v, n, partial + RED_BLOCKS));
+  DG_PROF(K_DOT, s, eps_finish_kernel<<<1, RT, 0, s>>>(partial, eps));
+  DG_LAUNCHED(3);
   return DG_OK;
 }
 
@@ -189,8 +189,8 @@ __global__ void newton_resid_kernel(double* __restrict__ Nn, const double* __res
 }
 dg_status newton_resid(double* N, const double* u, const double* S, const double* R, double dta,
                        long long n, cudaStream_t s) {
-  newton_resid_kernel<<<grid_for(n), 256, 0, s>>>(N, u, S, R, dta, n);
-  DG_CUDA(cudaGetLastError());
+  DG_PROF(K_VEC, s, newton_resid_kernel<<<grid_for(n), 256, 0, s>>>(N, u, S, R, dta, n));
+  DG_LAUNCHED(1);
   return DG_OK;
 }
 

@@ -12,6 +12,45 @@
 
 namespace dg {
 
+long long g_launches = 0;
+
+// ---------------------------------------------------------------- profiling
+static const char* kernel_names[K_COUNT] = {
+    "dg_vol", "dg_face", "dg_lift", "dg_project", "dot", "multi_dot", "multi_axpy", "vector",
+    "brj_weights", "brj_tracejac", "brj_block", "brj_invert", "brj_diag", "brj_trace",
+    "brj_offdiag"};
+struct ProfRec {
+  int id;
+  cudaEvent_t a, b;
+};
+static bool g_prof = false;
+static std::vector<ProfRec> g_recs;
+static std::vector<cudaEvent_t> g_event_pool;
+
+static cudaEvent_t take_event() {
+  if (!g_event_pool.empty()) {
+    cudaEvent_t e = g_event_pool.back();
+    g_event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+int prof_begin(int id, cudaStream_t s) {
+  if (!g_prof) return -1;
+  ProfRec r{id, take_event(), take_event()};
+  cudaEventRecord(r.a, s);
+  g_recs.push_back(r);
+  return (int)g_recs.size() - 1;
+}
+
+void prof_end(int h, cudaStream_t s) {
+  if (h < 0) return;
+  cudaEventRecord(g_recs[h].b, s);
+}
+
 dg_status cuda_status(cudaError_t e) {
   if (e == cudaErrorMemoryAllocation) {
     cudaGetLastError();
@@ -182,6 +221,41 @@ using namespace dg;
 
 extern "C" {
 
+long long dg_kernel_launches(void) { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
+
+dg_status dg_profile_enable(int on) {
+  g_prof = on != 0;
+  return DG_OK;
+}
+
+dg_status dg_profile_read(dg_kernel_time* out, int cap, int* n) {
+  if (!out || !n || cap < 0) return DG_ERR_ARG;
+  DG_CUDA(cudaDeviceSynchronize());
+  double ms[K_COUNT] = {0};
+  long long cnt[K_COUNT] = {0};
+  for (const ProfRec& r : g_recs) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) ms[r.id] += t;
+    cnt[r.id]++;
+    g_event_pool.push_back(r.a);
+    g_event_pool.push_back(r.b);
+  }
+  g_recs.clear();
+  int k = 0;
+  for (int i = 0; i < K_COUNT; ++i) {
+    if (cnt[i] == 0) continue;
+    if (k < cap) {
+      std::memset(out[k].name, 0, sizeof(out[k].name));
+      std::strncpy(out[k].name, kernel_names[i], sizeof(out[k].name) - 1);
+      out[k].launches = cnt[i];
+      out[k].ms = ms[i];
+    }
+    ++k;
+  }
+  *n = k < cap ? k : cap;
+  return DG_OK;
+}
+
 const char* dg_status_string(dg_status s) {
   switch (s) {
     case DG_OK: return "ok";
@@ -315,7 +389,9 @@ dg_status dg_mesh_create(const dg_mesh_desc* md, const dg_physics* ph, void* str
   alloc((void**)&m->tbuf, sizeof(double) * ntr);
   alloc((void**)&m->fbuf, sizeof(double) * ntr);
   alloc((void**)&m->scratch, sizeof(double) * 64);
-  alloc((void**)&m->red, sizeof(double) * RED_BLOCKS * 64);
+  alloc((void**)&m->red, sizeof(double) * RED_BLOCKS * (MAX_RESTART + 8));
+  alloc((void**)&m->hdev, sizeof(double) * 4 * (MAX_RESTART + 2));
+  if (err == cudaSuccess) err = cudaMallocHost((void**)&m->hhost, sizeof(double) * 4 * (MAX_RESTART + 2));
   alloc((void**)&m->w1, sizeof(double) * nd);
   alloc((void**)&m->w2, sizeof(double) * nd);
   if (ph->forcing) alloc((void**)&m->force, sizeof(double) * nd);
@@ -398,16 +474,10 @@ dg_status dg_jvp(dg_mesh_t m, const double* u, const double* r_u, double t, cons
 // ---------------------------------------------------------------- GMRES
 static dg_status ensure_krylov(dg_mesh_s* m, int restart) {
   if (m->krylov && m->krylov_m >= restart) return DG_OK;
-  cudaFree(m->krylov);
-  cudaFree(m->hdev);
-  if (m->hhost) cudaFreeHost(m->hhost);
+  cudaFree(m->krylov);  // implicitly synchronises the device
   m->krylov = nullptr;
-  m->hdev = nullptr;
-  m->hhost = nullptr;
   const size_t nd = (size_t)m->ndof;
   DG_CUDA(cudaMalloc(&m->krylov, sizeof(double) * nd * (2 * (size_t)restart + 1)));
-  DG_CUDA(cudaMalloc(&m->hdev, sizeof(double) * 4 * (restart + 2)));
-  DG_CUDA(cudaMallocHost(&m->hhost, sizeof(double) * 4 * (restart + 2)));
   m->krylov_m = restart;
   return DG_OK;
 }
@@ -536,7 +606,8 @@ dg_status dg_gmres(dg_mesh_t m, dg_precond_t p, const double* u, const double* r
                    double dt_a, const double* b, double* x, const dg_gmres_cfg* cfg,
                    dg_gmres_stats* stats, void* stream) {
   if (!m || !u || !r_u || !b || !x || !cfg) return DG_ERR_ARG;
-  if (cfg->restart < 1 || cfg->max_cycles < 1 || !(cfg->rtol > 0.0)) return DG_ERR_ARG;
+  if (cfg->restart < 1 || cfg->restart > MAX_RESTART || cfg->max_cycles < 1 || !(cfg->rtol > 0.0))
+    return DG_ERR_ARG;
   if (p && precond_mesh(p) != m) return DG_ERR_ARG;
   return gmres_impl(m, p, u, r_u, t, dt_a, b, x, cfg, stats, (cudaStream_t)stream);
 }
@@ -577,6 +648,9 @@ dg_status sdirk_step(dg_mesh_t m, const dg_sdirk_cfg* cfg, double* u_n, double t
   if (!m || !cfg || !u_n || !(dt > 0.0)) return DG_ERR_ARG;
   if (cfg->tableau != DG_SDIRK2 && cfg->tableau != DG_SDIRK3) return DG_ERR_ARG;
   if (cfg->use_precond && !p_inout) return DG_ERR_ARG;
+  if (cfg->gmres.restart < 1 || cfg->gmres.restart > MAX_RESTART || cfg->gmres.max_cycles < 1 ||
+      !(cfg->gmres.rtol > 0.0) || cfg->max_newton < 0)
+    return DG_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   const long long n = m->ndof;
   double A[3][3], b[3], c[3];

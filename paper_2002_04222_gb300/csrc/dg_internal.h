@@ -10,6 +10,7 @@ namespace dg {
 
 constexpr int QMAX = 8;   // largest Gauss point count per direction
 constexpr int NMAX = 7;   // largest (P+1)
+constexpr int MAX_RESTART = 64;  // largest GMRES restart length
 
 // 1-D tables of one (P, Q) pair, passed by value to the kernels.
 struct Tables {
@@ -77,6 +78,28 @@ dg_status cuda_status(cudaError_t e);
   do {                                                  \
     cudaError_t _e = (call);                            \
     if (_e != cudaSuccess) return ::dg::cuda_status(_e); \
+  } while (0)
+// count of kernels launched by the library (diagnostics: dg_kernel_launches)
+extern long long g_launches;
+#define DG_LAUNCHED(n)                                     \
+  do {                                                     \
+    __atomic_fetch_add(&::dg::g_launches, (long long)(n), __ATOMIC_RELAXED); \
+    cudaError_t _e = cudaGetLastError();                   \
+    if (_e != cudaSuccess) return ::dg::cuda_status(_e);   \
+  } while (0)
+// optional per-kernel timing with CUDA events on the launch stream
+enum KernelId {
+  K_VOL, K_FACE, K_LIFT, K_PROJECT, K_DOT, K_MULTIDOT, K_MULTIAXPY, K_VEC,
+  K_BRJ_WEIGHTS, K_BRJ_TRACEJAC, K_BRJ_BLOCK, K_BRJ_INVERT, K_BRJ_DIAG, K_BRJ_TRACE,
+  K_BRJ_OFFDIAG, K_COUNT
+};
+int prof_begin(int id, cudaStream_t s);
+void prof_end(int handle, cudaStream_t s);
+#define DG_PROF(id, stream, ...)                    \
+  do {                                              \
+    const int _ph = ::dg::prof_begin(id, stream);   \
+    __VA_ARGS__;                                    \
+    ::dg::prof_end(_ph, stream);                    \
   } while (0)
 #define DG_TRY(call)                 \
   do {                               \

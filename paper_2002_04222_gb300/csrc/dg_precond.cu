@@ -743,12 +743,12 @@ struct BRJImpl {
     DG_TRY(launch_residual(m, a, s));
     double* chi = m->scratch + 8;
     var_norm_kernel<<<NV, 256, 0, s>>>(u, E, NV, NM, chi);
-    DG_CUDA(cudaGetLastError());
+    DG_LAUNCHED(1);
     T* Jd = (T*)pc->jd;
     T* Jo = (T*)pc->jo;
-    brj_tracejac_kernel<DIM, P, Q, T><<<(m->F * NF + 127) / 128, 128, 0, s>>>(
-        m->tab, m->phys, m->geo, m->faces, m->F, t, m->tbuf, chi, Jd, Jo);
-    DG_CUDA(cudaGetLastError());
+    DG_PROF(K_BRJ_TRACEJAC, s, brj_tracejac_kernel<DIM, P, Q, T><<<(m->F * NF + 127) / 128, 128, 0, s>>>(
+        m->tab, m->phys, m->geo, m->faces, m->F, t, m->tbuf, chi, Jd, Jo));
+    DG_LAUNCHED(1);
     // blocks: FP64 mode stores double, FP32/BF16 modes assemble in float
     T* blk = (T*)(pc->precision == DG_PREC_BF16 ? pc->work : pc->blocks);
     T* Wbuf = (T*)((char*)pc->work +
@@ -762,24 +762,24 @@ struct BRJImpl {
     const int CH = pc->wchunk;
     for (int e0 = 0; e0 < E; e0 += CH) {
       const int ne = E - e0 < CH ? E - e0 : CH;
-      brj_weights_kernel<DIM, P, Q, T><<<ne, 256, wsm, s>>>(m->tab, m->phys, m->geo, e0, ne, u,
-                                                            Wbuf);
-      DG_CUDA(cudaGetLastError());
-      brj_block_kernel<DIM, P, Q, T><<<dim3(ne, NV * NV), 256, bsm, s>>>(m->tab, m->geo, e0, Wbuf,
-                                                                         Jd, dta, blk, ld);
-      DG_CUDA(cudaGetLastError());
+      DG_PROF(K_BRJ_WEIGHTS, s, brj_weights_kernel<DIM, P, Q, T><<<ne, 256, wsm, s>>>(m->tab, m->phys, m->geo, e0, ne, u,
+                                                            Wbuf));
+      DG_LAUNCHED(1);
+      DG_PROF(K_BRJ_BLOCK, s, brj_block_kernel<DIM, P, Q, T><<<dim3(ne, NV * NV), 256, bsm, s>>>(m->tab, m->geo, e0, Wbuf,
+                                                                         Jd, dta, blk, ld));
+      DG_LAUNCHED(1);
     }
     int* fail = (int*)(m->scratch + 16);
     DG_CUDA(cudaMemsetAsync(fail, 0, sizeof(int), s));
     const size_t ism = sizeof(T) * 2 * nb + sizeof(int) * nb;
     DG_CUDA(cudaFuncSetAttribute(brj_invert_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)ism));
-    brj_invert_kernel<T><<<E, 512, ism, s>>>(blk, nb, ld, fail);
-    DG_CUDA(cudaGetLastError());
+    DG_PROF(K_BRJ_INVERT, s, brj_invert_kernel<T><<<E, 512, ism, s>>>(blk, nb, ld, fail));
+    DG_LAUNCHED(1);
     if (pc->precision == DG_PREC_BF16) {
       const long long n = (long long)E * nb * ld;
       to_bf16_kernel<<<152 * 16, 256, 0, s>>>((const float*)blk, (__nv_bfloat16*)pc->blocks, n);
-      DG_CUDA(cudaGetLastError());
+      DG_LAUNCHED(1);
     }
     int hfail = 0;
     DG_CUDA(cudaMemcpyAsync(&hfail, fail, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -792,13 +792,13 @@ struct BRJImpl {
                            double* y, cudaStream_t s) {
     constexpr int NV = C::NV, NF = C::NF;
     const long long ntr = (long long)m->E * 2 * DIM * NV * NF;
-    brj_trace_kernel<DIM, P, Q, TA><<<(unsigned)((ntr + 127) / 128), 128, 0, s>>>(m->tab, qh, m->E,
-                                                                                   pc->tr);
-    DG_CUDA(cudaGetLastError());
-    brj_offdiag_kernel<DIM, P, Q, TA, TJ><<<m->E, 128, 0, s>>>(m->tab, m->geo, m->E,
+    DG_PROF(K_BRJ_TRACE, s, brj_trace_kernel<DIM, P, Q, TA><<<(unsigned)((ntr + 127) / 128), 128, 0, s>>>(m->tab, qh, m->E,
+                                                                                   pc->tr));
+    DG_LAUNCHED(1);
+    DG_PROF(K_BRJ_OFFDIAG, s, brj_offdiag_kernel<DIM, P, Q, TA, TJ><<<m->E, 128, 0, s>>>(m->tab, m->geo, m->E,
                                                                (const TJ*)pc->jo, pc->nbr, pc->tr,
-                                                               q, pc->dt_a, y);
-    DG_CUDA(cudaGetLastError());
+                                                               q, pc->dt_a, y));
+    DG_LAUNCHED(1);
     return DG_OK;
   }
 };
@@ -807,16 +807,16 @@ static dg_status diag_apply(dg_precond_s* pc, const double* y, const double* qpr
                             cudaStream_t s) {
   const int E = pc->mesh->E, nb = pc->nb, ld = round_up8(nb);
   if (pc->precision == DG_PREC_FP64) {
-    brj_diag_kernel<double, double><<<E, 256, sizeof(double) * nb, s>>>(
-        (const double*)pc->blocks, nb, ld, y, qprev, pc->omega, out);
+    DG_PROF(K_BRJ_DIAG, s, brj_diag_kernel<double, double><<<E, 256, sizeof(double) * nb, s>>>(
+        (const double*)pc->blocks, nb, ld, y, qprev, pc->omega, out));
   } else if (pc->precision == DG_PREC_FP32) {
-    brj_diag_kernel<float, float><<<E, 256, sizeof(float) * nb, s>>>(
-        (const float*)pc->blocks, nb, ld, y, qprev, pc->omega, out);
+    DG_PROF(K_BRJ_DIAG, s, brj_diag_kernel<float, float><<<E, 256, sizeof(float) * nb, s>>>(
+        (const float*)pc->blocks, nb, ld, y, qprev, pc->omega, out));
   } else {
-    brj_diag_bf16_kernel<<<E, 256, sizeof(float) * ld, s>>>((const __nv_bfloat16*)pc->blocks, nb,
-                                                           ld, y, qprev, pc->omega, out);
+    DG_PROF(K_BRJ_DIAG, s, brj_diag_bf16_kernel<<<E, 256, sizeof(float) * ld, s>>>((const __nv_bfloat16*)pc->blocks, nb,
+                                                           ld, y, qprev, pc->omega, out));
   }
-  DG_CUDA(cudaGetLastError());
+  DG_LAUNCHED(1);
   return DG_OK;
 }
 

@@ -442,16 +442,16 @@ static dg_status run_residual(dg_mesh_s* m, const EvalArgs& a, cudaStream_t s) {
                                (int)vsm));
   DG_CUDA(cudaFuncSetAttribute(lift_kernel<DIM, P, Q>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm));
-  vol_kernel<DIM, P, Q><<<nb, C::NT, vsm, s>>>(m->tab, m->phys, m->geo, m->E, a.u, a.v, a.eps,
-                                               m->hbuf, m->tbuf);
-  DG_CUDA(cudaGetLastError());
+  DG_PROF(K_VOL, s, vol_kernel<DIM, P, Q><<<nb, C::NT, vsm, s>>>(m->tab, m->phys, m->geo, m->E, a.u, a.v, a.eps,
+                                               m->hbuf, m->tbuf));
+  DG_LAUNCHED(1);
   const int nfp = m->F * C::NF;
-  face_kernel<DIM, P, Q><<<(nfp + 127) / 128, 128, 0, s>>>(m->tab, m->phys, m->geo, m->faces,
-                                                           m->F, a.t, m->tbuf, m->fbuf);
-  DG_CUDA(cudaGetLastError());
-  lift_kernel<DIM, P, Q><<<nb, C::NT, lsm, s>>>(m->tab, m->geo, m->E, m->hbuf, m->fbuf, m->force,
-                                                a.v, a.r_u, a.eps, a.alpha, a.beta, a.out);
-  DG_CUDA(cudaGetLastError());
+  DG_PROF(K_FACE, s, face_kernel<DIM, P, Q><<<(nfp + 127) / 128, 128, 0, s>>>(m->tab, m->phys, m->geo, m->faces,
+                                                           m->F, a.t, m->tbuf, m->fbuf));
+  DG_LAUNCHED(1);
+  DG_PROF(K_LIFT, s, lift_kernel<DIM, P, Q><<<nb, C::NT, lsm, s>>>(m->tab, m->geo, m->E, m->hbuf, m->fbuf, m->force,
+                                                a.v, a.r_u, a.eps, a.alpha, a.beta, a.out));
+  DG_LAUNCHED(1);
   return DG_OK;
 }
 
@@ -462,8 +462,8 @@ static dg_status run_project(dg_mesh_s* m, int what, double t, double* out, cuda
   const size_t lsm = sizeof(double) * C::LIFT_SM;
   DG_CUDA(cudaFuncSetAttribute(project_kernel<DIM, P, Q>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm));
-  project_kernel<DIM, P, Q><<<nb, C::NT, lsm, s>>>(m->tab, m->phys, m->geo, m->E, what, t, out);
-  DG_CUDA(cudaGetLastError());
+  DG_PROF(K_PROJECT, s, project_kernel<DIM, P, Q><<<nb, C::NT, lsm, s>>>(m->tab, m->phys, m->geo, m->E, what, t, out));
+  DG_LAUNCHED(1);
   return DG_OK;
 }
 

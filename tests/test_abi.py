@@ -15,7 +15,7 @@ HEADER = os.path.join(ROOT, "include", "dg.h")
 
 def declared_functions():
     text = open(HEADER).read()
-    return sorted(set(re.findall(r"^\s*(?:dg_status|const char\*)\s+(\w+)\s*\(", text, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:dg_status|const char\*|long long)\s+(\w+)\s*\(", text, re.M)))
 
 
 @pytest.fixture(scope="module")
@@ -48,7 +48,8 @@ def test_struct_layouts_match_header():
     structs = {"dg_mesh_desc": _lib.MeshDesc, "dg_physics": _lib.Physics,
                "dg_mesh_info_t": _lib.MeshInfo, "dg_prec_cfg": _lib.PrecCfg,
                "dg_gmres_cfg": _lib.GmresCfg, "dg_gmres_stats": _lib.GmresStats,
-               "dg_sdirk_cfg": _lib.SdirkCfg, "dg_step_stats": _lib.StepStats}
+               "dg_sdirk_cfg": _lib.SdirkCfg, "dg_step_stats": _lib.StepStats,
+               "dg_kernel_time": _lib.KernelTime}
     lines = ["#include <stdio.h>", "#include <stddef.h>", f'#include "{HEADER}"', "int main(void){"]
     for cname, cls in structs.items():
         lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
