@@ -368,7 +368,10 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "bf16"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--elems", type=int, default=WORKLOAD["n"],
+                    help="elements per direction (16 = the benchmark; smaller only for profiler captures)")
     args = ap.parse_args()
+    WORKLOAD["n"] = args.elems
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":

@@ -15,7 +15,8 @@
 //                       of every diagonal block.
 // Apply (Eq. precond-Jacobi): q^1 = D^-1 q; q^j = D^-1 (q - (L+U) q^(j-1)), the
 // off-diagonal product formed on the fly from the neighbour traces and the
-// stored neighbour trace Jacobians (brj_trace_kernel + brj_offdiag_kernel),
+// stored neighbour trace Jacobians (brj_offdiag_kernel, which also evaluates the
+// neighbour traces),
 // the block product by brj_diag_kernel (HBM-bound batched GEMV).
 #include <cmath>
 #include <cstring>
@@ -567,6 +568,40 @@ __global__ void __launch_bounds__(256) brj_diag_kernel(const TB* __restrict__ bl
   }
 }
 
+// FP32 blocks and arithmetic, 4 elements per 16-byte load (rows padded to ld)
+__global__ void __launch_bounds__(256) brj_diag_f32_kernel(const float* __restrict__ blocks, int nb,
+                                                           int ld, const double* __restrict__ y,
+                                                           const double* __restrict__ qprev,
+                                                           double omega, double* __restrict__ out) {
+  extern __shared__ unsigned char smraw[];
+  float* sy = reinterpret_cast<float*>(smraw);
+  const int e = blockIdx.x;
+  for (int i = threadIdx.x; i < ld; i += blockDim.x)
+    sy[i] = i < nb ? (float)y[(long long)e * nb + i] : 0.0f;
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const float* A = blocks + (long long)e * nb * ld;
+  const float4* sy4 = reinterpret_cast<const float4*>(sy);
+  for (int rrow = warp; rrow < nb; rrow += nw) {
+    const float4* ar = reinterpret_cast<const float4*>(A + (long long)rrow * ld);
+    float acc = 0.0f;
+    for (int c4 = lane; c4 < ld / 4; c4 += 32) {
+      const float4 a = __ldcs(ar + c4);
+      const float4 b = sy4[c4];
+      acc = fmaf(a.x, b.x, acc);
+      acc = fmaf(a.y, b.y, acc);
+      acc = fmaf(a.z, b.z, acc);
+      acc = fmaf(a.w, b.w, acc);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+      const long long gi = (long long)e * nb + rrow;
+      out[gi] = omega == 1.0 ? (double)acc : omega * (double)acc + (1.0 - omega) * qprev[gi];
+    }
+  }
+}
+
 // bf16 blocks, FP32 arithmetic, 8 elements per 16-byte load
 __global__ void __launch_bounds__(256) brj_diag_bf16_kernel(
     const __nv_bfloat16* __restrict__ blocks, int nb, int ld, const double* __restrict__ y,
@@ -583,7 +618,7 @@ __global__ void __launch_bounds__(256) brj_diag_bf16_kernel(
     const uint4* ar = reinterpret_cast<const uint4*>(A + (long long)rrow * ld);
     float acc = 0.0f;
     for (int c8 = lane; c8 < ld / 8; c8 += 32) {
-      uint4 pk = ar[c8];
+      uint4 pk = __ldcs(ar + c8);
       const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&pk);
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
@@ -601,102 +636,136 @@ __global__ void __launch_bounds__(256) brj_diag_bf16_kernel(
   }
 }
 
-// face values of an iterate: tr[e][lf][v][p] = sum over the face modes
-template <int DIM, int P, int Q, typename TA>
-__global__ void __launch_bounds__(128) brj_trace_kernel(const __grid_constant__ Tables tab,
-                                                        const double* __restrict__ q, int E,
-                                                        double* __restrict__ tr) {
-  using C = Cfg<DIM, P, Q>;
-  constexpr int N = C::N, NV = C::NV, NM = C::NM, NF = C::NF;
-  constexpr int NTOT = 2 * DIM * NV * NF;
-  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (idx >= (long long)E * NTOT) return;
-  const int e = (int)(idx / NTOT);
-  int rem = (int)(idx % NTOT);
-  const int p = rem % NF;
-  rem /= NF;
-  const int v = rem % NV;
-  const int lf = rem / NV;
-  const int r = lf >> 1, vert = (lf & 1) ? P : 0;
-  const int pc[2] = {p % Q, DIM == 3 ? p / Q : 0};
-  const double* qe = q + ((long long)e * NV + v) * NM;
-  TA acc = (TA)0;
-  if (DIM == 2) {
-    const int s = 1 - r;
-    for (int a = 0; a < N; ++a) {
-      int mc[2];
-      mc[r] = vert;
-      mc[s] = a;
-      acc += (TA)tab.B[pc[0] * N + a] * (TA)qe[mc[0] + N * mc[1]];
-    }
-  } else {
-    const int t0 = r == 0 ? 1 : 0, t1 = r == 2 ? 1 : 2;
-    for (int a = 0; a < N; ++a)
-      for (int b = 0; b < N; ++b) {
-        int mc[3];
-        mc[r] = vert;
-        mc[t0] = a;
-        mc[t1] = b;
-        acc += (TA)(tab.B[pc[0] * N + a] * tab.B[pc[1] * N + b]) *
-               (TA)qe[mc[0] + N * (mc[1] + N * mc[2])];
-      }
-  }
-  tr[idx] = (double)acc;
-}
-
-// y = q + dt_a M^-1 sum_faces B_f^T (Jo . trace of the neighbour)  (= q - (L+U) qh)
+// y = q - (L+U) qh = q + dt_a M^-1 sum_faces B_f^T (Jo . trace of the neighbour's qh)
+// One block per element: the neighbour face values are evaluated from the
+// neighbour's face-mode coefficients (2-D sum factorisation), multiplied by
+// the stored neighbour trace Jacobians, lifted onto the face modes and
+// multiplied by the inverse mass matrix, all in the apply precision TA.
 template <int DIM, int P, int Q, typename TA, typename TJ>
 __global__ void __launch_bounds__(128) brj_offdiag_kernel(
     const __grid_constant__ Tables tab, const ElemGeo* __restrict__ geo, int E,
-    const TJ* __restrict__ Jo, const int32_t* __restrict__ nbr, const double* __restrict__ tr,
+    const TJ* __restrict__ Jo, const int32_t* __restrict__ nbr, const double* __restrict__ qh,
     const double* __restrict__ q, double dta, double* __restrict__ y) {
   using C = Cfg<DIM, P, Q>;
   constexpr int N = C::N, NV = C::NV, NM = C::NM, NF = C::NF;
-  __shared__ TA cf[2 * DIM * NV * NF];
-  __shared__ double L0[NV * NM], L1[NV * NM];
+  constexpr int NS = DIM == 2 ? N : N * N;        // face-slice modes
+  constexpr int NT = DIM == 2 ? 1 : Q * N;        // half-transformed slice per variable
+  __shared__ TA sB[Q * N], sMi[N * N];
+  __shared__ TA cs[2 * DIM * NV * NS];            // neighbour face-slice coefficients
+  __shared__ TA ct[2 * DIM * NV * NT];
+  __shared__ TA tr[2 * DIM * NV * NF];            // neighbour face values, then Jo . values
+  __shared__ TA L0[NV * NM], L1[NV * NM];
   const int e = blockIdx.x;
-  for (int i = threadIdx.x; i < 2 * DIM * NV * NF; i += blockDim.x) {
-    const int p = i % NF, k = (i / NF) % NV, lf = i / (NF * NV);
+  for (int i = threadIdx.x; i < Q * N; i += blockDim.x) sB[i] = (TA)tab.B[i];
+  for (int i = threadIdx.x; i < N * N; i += blockDim.x) sMi[i] = (TA)tab.Minv[i];
+  // gather the neighbour's face slice (modes with m_r = vertex of its face)
+  for (int i = threadIdx.x; i < 2 * DIM * NV * NS; i += blockDim.x) {
+    const int a = i % NS, v = (i / NS) % NV, lf = i / (NS * NV);
     const int nb = nbr[e * 2 * DIM + lf];
-    TA s = (TA)0;
+    TA val = (TA)0;
     if (nb >= 0) {
-      const TJ* j = Jo + (((long long)e * 2 * DIM + lf) * NF + p) * NV * NV + k * NV;
-      const double* t = tr + (long long)nb * NV * NF + p;  // nb = element*2d + face
-#pragma unroll
-      for (int l = 0; l < NV; ++l) s += (TA)j[l] * (TA)t[l * NF];
+      const int en = nb / (2 * DIM), fn = nb % (2 * DIM);
+      const int r = fn >> 1, vert = (fn & 1) ? P : 0;
+      int mc[3] = {0, 0, 0};
+      mc[r] = vert;
+      if (DIM == 2) {
+        mc[1 - r] = a;
+      } else {
+        const int t0 = r == 0 ? 1 : 0, t1 = r == 2 ? 1 : 2;
+        mc[t0] = a % N;
+        mc[t1] = a / N;
+      }
+      val = (TA)qh[((long long)en * NV + v) * NM + mc[0] + N * (mc[1] + N * mc[2])];
     }
-    cf[i] = s;
+    cs[i] = val;
   }
   __syncthreads();
-  // lift onto the face modes
+  // face values: contract the first tangential mode index, then the second
+  if (DIM == 2) {
+    for (int i = threadIdx.x; i < 2 * DIM * NV * NF; i += blockDim.x) {
+      const int p = i % NF, fv = i / NF;
+      TA acc = (TA)0;
+#pragma unroll
+      for (int a = 0; a < N; ++a) acc += sB[p * N + a] * cs[fv * NS + a];
+      tr[i] = acc;
+    }
+  } else {
+    for (int i = threadIdx.x; i < 2 * DIM * NV * NT; i += blockDim.x) {
+      const int p0 = i % Q, b = (i / Q) % N, fv = i / NT;
+      TA acc = (TA)0;
+#pragma unroll
+      for (int a = 0; a < N; ++a) acc += sB[p0 * N + a] * cs[fv * NS + a + N * b];
+      ct[i] = acc;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 2 * DIM * NV * NF; i += blockDim.x) {
+      const int p = i % NF, fv = i / NF;
+      const int p0 = p % Q, p1 = p / Q;
+      TA acc = (TA)0;
+#pragma unroll
+      for (int b = 0; b < N; ++b) acc += sB[p1 * N + b] * ct[fv * NT + p0 + Q * b];
+      tr[i] = acc;
+    }
+  }
+  __syncthreads();
+  // Jo . values (in registers, then back to tr)
+  TA prod[(2 * DIM * NV * NF + 127) / 128];
+#pragma unroll
+  for (int t = 0; t < (2 * DIM * NV * NF + 127) / 128; ++t) {
+    const int i = threadIdx.x + 128 * t;
+    TA s2 = (TA)0;
+    if (i < 2 * DIM * NV * NF) {
+      const int p = i % NF, k = (i / NF) % NV, lf = i / (NF * NV);
+      if (nbr[e * 2 * DIM + lf] >= 0) {
+        const TJ* j = Jo + (((long long)e * 2 * DIM + lf) * NF + p) * NV * NV + k * NV;
+        const TA* t0 = tr + lf * NV * NF + p;
+#pragma unroll
+        for (int l = 0; l < NV; ++l) s2 += (TA)j[l] * t0[l * NF];
+      }
+    }
+    prod[t] = s2;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int t = 0; t < (2 * DIM * NV * NF + 127) / 128; ++t) {
+    const int i = threadIdx.x + 128 * t;
+    if (i < 2 * DIM * NV * NF) tr[i] = prod[t];
+  }
+  __syncthreads();
+  // lift onto the face modes of this element
   for (int i = threadIdx.x; i < NV * NM; i += blockDim.x) {
     const int v = i / NM, m = i % NM;
     int mc[3];
     mode_coords<DIM, N>(m, mc);
-    TA s = (TA)0;
+    TA s2 = (TA)0;
+#pragma unroll
     for (int lf = 0; lf < 2 * DIM; ++lf) {
       const int r = lf >> 1, vert = (lf & 1) ? P : 0;
       if (mc[r] != vert) continue;
-      const TA* c = cf + (lf * NV + v) * NF;
+      const TA* c = tr + (lf * NV + v) * NF;
       if (DIM == 2) {
         const int a = mc[1 - r];
-        for (int p = 0; p < Q; ++p) s += (TA)tab.B[p * N + a] * c[p];
+#pragma unroll
+        for (int p = 0; p < Q; ++p) s2 += sB[p * N + a] * c[p];
       } else {
         const int t0 = r == 0 ? 1 : 0, t1 = r == 2 ? 1 : 2;
         const int a = mc[t0], b = mc[t1];
+#pragma unroll
         for (int p1 = 0; p1 < Q; ++p1) {
-          TA s2 = (TA)0;
-          for (int p0 = 0; p0 < Q; ++p0) s2 += (TA)tab.B[p0 * N + a] * c[p0 + Q * p1];
-          s += (TA)tab.B[p1 * N + b] * s2;
+          TA s3 = (TA)0;
+#pragma unroll
+          for (int p0 = 0; p0 < Q; ++p0) s3 += sB[p0 * N + a] * c[p0 + Q * p1];
+          s2 += sB[p1 * N + b] * s3;
         }
       }
     }
-    L0[i] = (double)s;
+    L0[i] = s2;
   }
   __syncthreads();
   // inverse mass matrix, axis by axis
-  double* src = L0;
-  double* dst = L1;
+  TA* src = L0;
+  TA* dst = L1;
+#pragma unroll
   for (int ax = 0; ax < DIM; ++ax) {
     for (int i = threadIdx.x; i < NV * NM; i += blockDim.x) {
       const int m = i % NM;
@@ -704,13 +773,13 @@ __global__ void __launch_bounds__(128) brj_offdiag_kernel(
       mode_coords<DIM, N>(m, mc);
       const int str = ax == 0 ? 1 : (ax == 1 ? N : N * N);
       const int base = i - mc[ax] * str;
-      TA s = (TA)0;
+      TA s2 = (TA)0;
 #pragma unroll
-      for (int kk = 0; kk < N; ++kk) s += (TA)tab.Minv[mc[ax] * N + kk] * (TA)src[base + kk * str];
-      dst[i] = (double)s;
+      for (int kk = 0; kk < N; ++kk) s2 += sMi[mc[ax] * N + kk] * src[base + kk * str];
+      dst[i] = s2;
     }
     __syncthreads();
-    double* t = src;
+    TA* t = src;
     src = dst;
     dst = t;
   }
@@ -718,9 +787,10 @@ __global__ void __launch_bounds__(128) brj_offdiag_kernel(
   double idet = 1.0;
 #pragma unroll
   for (int r = 0; r < DIM; ++r) idet *= 2.0 / g.h[r];
+  const double sc = dta * idet;
   for (int i = threadIdx.x; i < NV * NM; i += blockDim.x) {
     const long long gi = (long long)e * NV * NM + i;
-    y[gi] = q[gi] + dta * idet * src[i];
+    y[gi] = q[gi] + sc * (double)src[i];
   }
 }
 
@@ -790,14 +860,8 @@ struct BRJImpl {
   template <typename TA, typename TJ>
   static dg_status offdiag(dg_mesh_s* m, dg_precond_s* pc, const double* qh, const double* q,
                            double* y, cudaStream_t s) {
-    constexpr int NV = C::NV, NF = C::NF;
-    const long long ntr = (long long)m->E * 2 * DIM * NV * NF;
-    DG_PROF(K_BRJ_TRACE, s, brj_trace_kernel<DIM, P, Q, TA><<<(unsigned)((ntr + 127) / 128), 128, 0, s>>>(m->tab, qh, m->E,
-                                                                                   pc->tr));
-    DG_LAUNCHED(1);
-    DG_PROF(K_BRJ_OFFDIAG, s, brj_offdiag_kernel<DIM, P, Q, TA, TJ><<<m->E, 128, 0, s>>>(m->tab, m->geo, m->E,
-                                                               (const TJ*)pc->jo, pc->nbr, pc->tr,
-                                                               q, pc->dt_a, y));
+    DG_PROF(K_BRJ_OFFDIAG, s, brj_offdiag_kernel<DIM, P, Q, TA, TJ><<<m->E, 128, 0, s>>>(
+        m->tab, m->geo, m->E, (const TJ*)pc->jo, pc->nbr, qh, q, pc->dt_a, y));
     DG_LAUNCHED(1);
     return DG_OK;
   }
@@ -810,7 +874,7 @@ static dg_status diag_apply(dg_precond_s* pc, const double* y, const double* qpr
     DG_PROF(K_BRJ_DIAG, s, brj_diag_kernel<double, double><<<E, 256, sizeof(double) * nb, s>>>(
         (const double*)pc->blocks, nb, ld, y, qprev, pc->omega, out));
   } else if (pc->precision == DG_PREC_FP32) {
-    DG_PROF(K_BRJ_DIAG, s, brj_diag_kernel<float, float><<<E, 256, sizeof(float) * nb, s>>>(
+    DG_PROF(K_BRJ_DIAG, s, brj_diag_f32_kernel<<<E, 256, sizeof(float) * ld, s>>>(
         (const float*)pc->blocks, nb, ld, y, qprev, pc->omega, out));
   } else {
     DG_PROF(K_BRJ_DIAG, s, brj_diag_bf16_kernel<<<E, 256, sizeof(float) * ld, s>>>((const __nv_bfloat16*)pc->blocks, nb,
@@ -937,7 +1001,6 @@ dg_status dg_precond_build(dg_mesh_t m, const double* u, double t, double dt_a,
     alloc(&p->jd, vb * njac);
     alloc(&p->jo, vb * njac);
     alloc((void**)&p->nbr, sizeof(int32_t) * E * 2 * d);
-    alloc((void**)&p->tr, sizeof(double) * (size_t)E * 2 * d * NV * m->nf);
     alloc((void**)&p->qh, sizeof(double) * (size_t)m->ndof);
     alloc((void**)&p->y, sizeof(double) * (size_t)m->ndof);
     alloc(&p->work, p->work_bytes);
