@@ -83,9 +83,11 @@ def test_residual_parity(dgl, name):
     tol = max(R_TOL, 16.0 * rounding_floor(dg, u, R_ref))
     assert rel(R, R_ref) < tol, (rel(R, R_ref), tol)
     assert np.abs(R - R_ref).max() < 10 * tol * np.abs(R_ref).max()
-    # the well-conditioned weak form L = M R (no mass-matrix amplification)
+    # the weak form L = M R (no mass-matrix amplification); the kernels
+    # differentiate by collocation on the Q-point Gauss grid, whose matrix norm
+    # (~Q^2/2) multiplies their rounding, hence the wider factor
     L, L_ref = mass(dg, R), mass(dg, R_ref)
-    assert rel(L, L_ref) < max(R_TOL, 16.0 * rounding_floor(dg, u, R_ref, weak=True)), rel(L, L_ref)
+    assert rel(L, L_ref) < max(R_TOL, 64.0 * rounding_floor(dg, u, R_ref, weak=True)), rel(L, L_ref)
 
 
 @pytest.mark.parametrize("name", ["vortex8_P2", "poiseuille_P3", "box_P3_Q6"])
