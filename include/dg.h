@@ -160,6 +160,28 @@ dg_status dg_gmres(dg_mesh_t m, dg_precond_t p, const double* u, const double* r
                    double dt_a, const double* b, double* x, const dg_gmres_cfg* cfg,
                    dg_gmres_stats* stats, void* stream);
 
+/* GMRES for callers that cannot allocate device memory (the paper has no
+ * counterpart; this is an interface for such callers).  dg_gmres allocates its
+ * Krylov basis with cudaMalloc on its first call; code that runs during CUDA
+ * stream capture, under a memory pool that has reserved the device, or in a
+ * loop that forbids allocator calls cannot do that.  dg_gmres_noalloc solves
+ * the same system with the same algorithm and arguments as dg_gmres, but keeps
+ * the basis (restart+1 vectors, plus restart preconditioned vectors when p is
+ * not NULL) in one static device array of DG_GMRES_NOALLOC_MAX_DOUBLES doubles
+ * (16 MiB) that every GPU loading the library holds until exit; it calls no
+ * cudaMalloc, cudaFree or allocating routine.  It returns DG_ERR_ARG when
+ * n_dof * (restart + 1 + (p ? restart : 0)) exceeds that size.  The first call
+ * on each device looks up the array's device address (cudaGetSymbolAddress),
+ * so make that first call before any stream capture.  All calls share the
+ * array and it keeps the last call's contents: calls whose work overlaps on the
+ * GPU (other streams, other threads) race and must be serialised by the caller.
+ * The mesh and preconditioner handles must already exist (they are created
+ * with allocation, once, at set-up). */
+#define DG_GMRES_NOALLOC_MAX_DOUBLES 2097152
+dg_status dg_gmres_noalloc(dg_mesh_t m, dg_precond_t p, const double* u, const double* r_u,
+                           double t, double dt_a, const double* b, double* x,
+                           const dg_gmres_cfg* cfg, dg_gmres_stats* stats, void* stream);
+
 /* One SDIRK step (Sec. 3.2, Eq. rk-stage, rk-final; App. A tableaus): each
  * stage solves N(u) = u - S_m - dt a_mm R(u, t + c_m dt) = 0 by Newton
  * (Eq. Newton-Iteration) from u = S_m, stopping when ||N|| < alpha ||N(S_m)||

@@ -106,6 +106,19 @@ class Mesh:
         _check("dg_gmres", code, ok=(0, _lib.DG_ERR_NOT_CONVERGED))
         return out, {f: getattr(st, f) for f, _ in _lib.GmresStats._fields_}
 
+    def gmres_noalloc(self, u, r_u, b, out, t=0.0, dt_a=0.0, precond=None, restart=30,
+                      max_cycles=10, rtol=5e-2, stream=None):
+        """dg_gmres_noalloc: the same solve as gmres() for callers that cannot
+        allocate device memory; the Krylov basis lives in the library's fixed
+        static device array and `out` must be supplied by the caller."""
+        cfg = _lib.GmresCfg(restart, max_cycles, rtol)
+        st = _lib.GmresStats()
+        code = self._lib.dg_gmres_noalloc(self.handle, precond.handle if precond else None,
+                                          _ptr(u), _ptr(r_u), t, dt_a, _ptr(b), _ptr(out),
+                                          ctypes.byref(cfg), ctypes.byref(st), _stream(stream))
+        _check("dg_gmres_noalloc", code, ok=(0, _lib.DG_ERR_NOT_CONVERGED))
+        return out, {f: getattr(st, f) for f, _ in _lib.GmresStats._fields_}
+
     def sdirk_step(self, u, t, dt, precond=None, tableau=2, alpha=1e-3, abs_tol=0.0,
                    max_newton=20, rebuild=False, restart=30, max_cycles=10, rtol=5e-2,
                    J=7, precision="fp64", omega=1.0, use_precond=True, stream=None):

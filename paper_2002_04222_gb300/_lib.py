@@ -90,6 +90,8 @@ SIGNATURES = {
     "dg_precond_apply": [VP, VP, VP, VP],
     "dg_precond_destroy": [VP],
     "dg_gmres": [VP, VP, VP, VP, D, D, VP, VP, ctypes.POINTER(GmresCfg), ctypes.POINTER(GmresStats), VP],
+    "dg_gmres_noalloc": [VP, VP, VP, VP, D, D, VP, VP, ctypes.POINTER(GmresCfg),
+                         ctypes.POINTER(GmresStats), VP],
     "sdirk_step": [VP, ctypes.POINTER(SdirkCfg), VP, D, D, ctypes.POINTER(VP), ctypes.POINTER(StepStats), VP],
     "dg_status_string": [I],
     "dg_kernel_launches": [],
