@@ -319,6 +319,12 @@ dg_status dg_mesh_create(const dg_mesh_desc* md, const dg_physics* ph, void* str
         if (std::fabs(X[a * d + r] - expect) > 1e-12 * (1.0 + std::fabs(expect)))
           return DG_ERR_UNSUPPORTED;
       }
+    g.detJ = 1.0;
+    for (int r = 0; r < 3; ++r) {
+      g.rh[r] = r < d ? 2.0 / g.h[r] : 0.0;
+      if (r < d) g.detJ *= 0.5 * g.h[r];
+    }
+    g.idet = 1.0 / g.detJ;
     geo[e] = g;
   }
   // connectivity: every (element, local face) exactly once, aligned sides

@@ -36,6 +36,8 @@ struct Phys {
 struct ElemGeo {
   double x0[3];
   double h[3];
+  double rh[3];       // 2/h: reference-to-physical derivative factors
+  double detJ, idet;  // |J| = prod h/2 and its inverse
 };
 
 }  // namespace dg

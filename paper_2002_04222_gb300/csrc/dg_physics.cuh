@@ -367,4 +367,257 @@ __device__ inline void numerical_flux(const double* QL, const double* QRin, int 
   }
 }
 
+// ------------------------------------------------------------ fused / axis-specialised forms
+// The same fluxes with the work that is identically zero removed: one
+// evaluation of the primitive variables shared by F and G, and, on a face with
+// normal n = sgn e_R (R known at compile time), only row R of G for the
+// average gradient and the rank-1 gradient n (x) [Q] for S.  Equal to the
+// generic forms above up to rounding order.
+
+// H = F - G at a volume point with shared primitive variables
+template <int D>
+__device__ inline void ns_volume_flux(const double* U, const double dU[D][D + 2], const Phys& ph,
+                                      double H[D][D + 2]) {
+  constexpr int NV = D + 2;
+  const double irho = 1.0 / U[0];
+  double vel[D], ke = 0.0;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    vel[k] = U[1 + k] * irho;
+    ke = fma(U[1 + k], vel[k], ke);
+  }
+  const double p = ph.gm1 * (U[D + 1] - 0.5 * ke);
+  const double Ep = U[D + 1] + p;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    H[i][0] = U[1 + i];
+#pragma unroll
+    for (int k = 0; k < D; ++k) H[i][1 + k] = U[1 + i] * vel[k];
+    H[i][1 + i] += p;
+    H[i][D + 1] = vel[i] * Ep;
+  }
+  if (!ph.viscous) return;
+  const double temp = ph.gMa2 * p * irho;
+  const double mu = viscosity(temp, ph);
+  const double kap = mu * ph.kappa_fac;
+  const double e = U[D + 1] * irho;
+  double dvel[D][D], dT[D];
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    double s = (dU[j][D + 1] - e * dU[j][0]) * irho;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      dvel[j][k] = (dU[j][1 + k] - vel[k] * dU[j][0]) * irho;
+      s = fma(-dvel[j][k], vel[k], s);
+    }
+    dT[j] = ph.gMa2 * ph.gm1 * s;
+  }
+  double div = 0.0;
+#pragma unroll
+  for (int k = 0; k < D; ++k) div += dvel[k][k];
+  const double tt = (2.0 / 3.0) * mu * div;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    double en = kap * dT[i];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      double tau = mu * (dvel[k][i] + dvel[i][k]);
+      if (i == k) tau -= tt;
+      H[i][1 + k] -= tau;
+      en = fma(vel[k], tau, en);
+    }
+    H[i][D + 1] -= en;
+  }
+}
+
+// Roe flux for n = sgn e_R
+template <int D, int R>
+__device__ inline void roe_flux_axis(const double* UL, const double* UR, double sgn,
+                                     const Phys& ph, double* Fh) {
+  constexpr int NV = D + 2;
+  const double iL = 1.0 / UL[0], iR = 1.0 / UR[0];
+  double vL[D], vR[D], keL = 0.0, keR = 0.0;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    vL[k] = UL[1 + k] * iL;
+    vR[k] = UR[1 + k] * iR;
+    keL = fma(UL[1 + k], vL[k], keL);
+    keR = fma(UR[1 + k], vR[k], keR);
+  }
+  const double pL = ph.gm1 * (UL[D + 1] - 0.5 * keL), pR = ph.gm1 * (UR[D + 1] - 0.5 * keR);
+  const double unL = sgn * vL[R], unR = sgn * vR[R];
+  double FL[NV], FR[NV];
+  FL[0] = UL[0] * unL;
+  FR[0] = UR[0] * unR;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    FL[1 + k] = UL[1 + k] * unL;
+    FR[1 + k] = UR[1 + k] * unR;
+  }
+  FL[1 + R] += sgn * pL;
+  FR[1 + R] += sgn * pR;
+  FL[D + 1] = (UL[D + 1] + pL) * unL;
+  FR[D + 1] = (UR[D + 1] + pR) * unR;
+  const double HL = (UL[D + 1] + pL) * iL, HR = (UR[D + 1] + pR) * iR;
+  const double sL = sqrt(UL[0]), sR = sqrt(UR[0]);
+  const double rt = sL * sR;
+  const double isum = 1.0 / (sL + sR);
+  double ut[D], du[D], q2 = 0.0, udu = 0.0;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    ut[k] = (sL * vL[k] + sR * vR[k]) * isum;
+    du[k] = vR[k] - vL[k];
+    q2 = fma(ut[k], ut[k], q2);
+    if (k != R) udu = fma(ut[k], du[k], udu);
+  }
+  const double unt = sgn * ut[R], dun = sgn * du[R];
+  const double Ht = (sL * HL + sR * HR) * isum;
+  const double c2 = ph.gm1 * (Ht - 0.5 * q2);
+  const double c = sqrt(c2);
+  const double ic2 = 1.0 / c2;
+  const double dp = pR - pL;
+  const double a1 = (dp - rt * c * dun) * 0.5 * ic2;
+  const double a5 = (dp + rt * c * dun) * 0.5 * ic2;
+  const double a2 = (UR[0] - UL[0]) - dp * ic2;
+  const double l2 = fabs(unt);
+  const double w1 = fabs(unt - c) * a1, w5 = fabs(unt + c) * a5, w2 = l2 * a2, ws = l2 * rt;
+  Fh[0] = 0.5 * (FL[0] + FR[0] - (w1 + w2 + w5));
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    double d = (w1 + w5 + w2) * ut[k];
+    if (k == R)
+      d += (w5 - w1) * c * sgn;
+    else
+      d += ws * du[k];
+    Fh[1 + k] = 0.5 * (FL[1 + k] + FR[1 + k] - d);
+  }
+  Fh[D + 1] = 0.5 * (FL[D + 1] + FR[D + 1] -
+                     ((w1 + w5) * Ht + (w5 - w1) * unt * c + w2 * 0.5 * q2 + ws * udu));
+}
+
+// primitive data shared by the viscous fluxes of one state
+template <int D>
+struct ViscPrim {
+  double irho, vel[D], e, mu, kap;
+};
+template <int D>
+__device__ inline void visc_prim(const double* U, const Phys& ph, ViscPrim<D>& s) {
+  s.irho = 1.0 / U[0];
+  double ke = 0.0;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    s.vel[k] = U[1 + k] * s.irho;
+    ke = fma(U[1 + k], s.vel[k], ke);
+  }
+  const double p = ph.gm1 * (U[D + 1] - 0.5 * ke);
+  s.e = U[D + 1] * s.irho;
+  s.mu = viscosity(ph.gMa2 * p * s.irho, ph);
+  s.kap = s.mu * ph.kappa_fac;
+}
+
+// row R of G(U, dU)
+template <int D, int R>
+__device__ inline void viscous_row(const ViscPrim<D>& s, const double dU[D][D + 2],
+                                   const Phys& ph, double* G) {
+  double dv[D][D];  // dv[j][k] = d u_k / d x_j, only the entries row R needs
+#pragma unroll
+  for (int j = 0; j < D; ++j)
+#pragma unroll
+    for (int k = 0; k < D; ++k)
+      if (j == R || k == R || j == k) dv[j][k] = (dU[j][1 + k] - s.vel[k] * dU[j][0]) * s.irho;
+  double div = 0.0;
+#pragma unroll
+  for (int k = 0; k < D; ++k) div += dv[k][k];
+  double st = (dU[R][D + 1] - s.e * dU[R][0]) * s.irho;
+#pragma unroll
+  for (int k = 0; k < D; ++k) st = fma(-dv[R][k], s.vel[k], st);
+  double en = s.kap * (ph.gMa2 * ph.gm1 * st);
+  G[0] = 0.0;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    double tau = s.mu * (dv[k][R] + dv[R][k]);
+    if (k == R) tau -= (2.0 / 3.0) * s.mu * div;
+    G[1 + k] = tau;
+    en = fma(s.vel[k], tau, en);
+  }
+  G[D + 1] = en;
+}
+
+// G(U, g) for a gradient whose only non-zero row is R (= g)
+template <int D, int R>
+__device__ inline void viscous_rank1(const ViscPrim<D>& s, const double* g, const Phys& ph,
+                                     double S[D][D + 2]) {
+  double a[D];  // d u_k / d x_R
+#pragma unroll
+  for (int k = 0; k < D; ++k) a[k] = (g[1 + k] - s.vel[k] * g[0]) * s.irho;
+  double st = (g[D + 1] - s.e * g[0]) * s.irho;
+#pragma unroll
+  for (int k = 0; k < D; ++k) st = fma(-a[k], s.vel[k], st);
+  const double dTR = ph.gMa2 * ph.gm1 * st;
+  const double tt = (2.0 / 3.0) * s.mu * a[R];
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    S[i][0] = 0.0;
+    if (i == R) {
+      double en = s.kap * dTR;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const double tau = k == R ? 2.0 * s.mu * a[R] - tt : s.mu * a[k];
+        S[i][1 + k] = tau;
+        en = fma(s.vel[k], tau, en);
+      }
+      S[i][D + 1] = en;
+    } else {
+#pragma unroll
+      for (int k = 0; k < D; ++k) S[i][1 + k] = k == R ? s.mu * a[i] : (k == i ? -tt : 0.0);
+      S[i][D + 1] = s.vel[R] * s.mu * a[i] - s.vel[i] * tt;
+    }
+  }
+}
+
+// numerical_flux for the normal sgn e_R
+template <int D, int R>
+__device__ inline void numerical_flux_axis(const double* QL, const double* QRin, int bctype,
+                                           const double* x, double t,
+                                           const double dQa[D][D + 2], double sgn, double beta,
+                                           const Phys& ph, double* Hn, double S[D][D + 2]) {
+  constexpr int NV = D + 2;
+  double QR[NV], Qa[NV];
+  if (bctype > 0) {
+    boundary_state<D>(bctype, ph, x, t, QL, QR);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Qa[v] = QR[v];
+  } else {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      QR[v] = QRin[v];
+      Qa[v] = 0.5 * (QL[v] + QR[v]);
+    }
+  }
+  if (ph.riemann == DG_RIEMANN_HLLC) {
+    double n[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) n[k] = k == R ? sgn : 0.0;
+    hllc_flux<D>(QL, QR, n, ph, Hn);
+  } else {
+    roe_flux_axis<D, R>(QL, QR, sgn, ph, Hn);
+  }
+  if (ph.viscous) {
+    ViscPrim<D> pa;
+    visc_prim<D>(Qa, ph, pa);
+    double g[NV], Gr[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) g[v] = sgn * (QL[v] - QR[v]);
+    viscous_rank1<D, R>(pa, g, ph, S);
+    viscous_row<D, R>(pa, dQa, ph, Gr);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Hn[v] -= sgn * (Gr[v] - beta * S[R][v]);
+  } else {
+#pragma unroll
+    for (int j = 0; j < D; ++j)
+#pragma unroll
+      for (int v = 0; v < NV; ++v) S[j][v] = 0.0;
+  }
+}
+
 }  // namespace dg

@@ -392,10 +392,7 @@ __global__ void __launch_bounds__(256) brj_block_kernel(
   }
   __syncthreads();
   // M^-1 on the row (test) index: |J|^-1 (M1^-1)^(x)DIM, axis by axis
-  const ElemGeo g = geo[e];
-  double idet = 1.0;
-#pragma unroll
-  for (int r = 0; r < DIM; ++r) idet *= 2.0 / g.h[r];
+  const double idet = geo[e].idet;
   T* src = X;
   T* dst = Y;
   for (int ax = 0; ax < DIM; ++ax) {
@@ -422,7 +419,9 @@ __global__ void __launch_bounds__(256) brj_block_kernel(
     const int m = i / NM, n = i % NM;
     double val = -dta * idet * (double)src[n * NM + m];
     if (k == l && m == n) val += 1.0;
-    out[(long long)(k * NM + m) * ld + l * NM + n] = (T)val;
+    // stored transposed: the inverse of the transpose is the transpose of the
+    // inverse, which the column-streaming block GEMV reads
+    out[(long long)(l * NM + n) * ld + k * NM + m] = (T)val;
   }
 }
 
@@ -504,6 +503,134 @@ __global__ void __launch_bounds__(512) brj_invert_kernel(T* __restrict__ blocks,
       for (int i = threadIdx.x; i < nb; i += blockDim.x) {
         T a = A[(long long)i * ld + kk];
         A[(long long)i * ld + kk] = A[(long long)i * ld + pr];
+        A[(long long)i * ld + pr] = a;
+      }
+    __syncthreads();
+  }
+}
+
+// Blocked in-place Gauss-Jordan inversion with partial pivoting, one block per
+// element.  Pivot columns K = [k0, k0+B) are processed as a panel held in
+// shared memory (row interchanges applied to whole rows at once); afterwards
+// the panel holds the columns K of the composite transformation T_K, and every
+// other column c is updated in one pass, A[:, c] += (T_K - E_K) A[K, c], a
+// rank-B update, so the block is read and written once per panel instead of
+// once per pivot.  The inverse's columns are un-permuted at the end.
+template <typename T, int B>
+__global__ void __launch_bounds__(256) brj_invert_blocked_kernel(T* __restrict__ blocks, int nb,
+                                                                 int ld, int* __restrict__ fail) {
+  extern __shared__ unsigned char smraw[];
+  T* P = reinterpret_cast<T*>(smraw);     // [nb][B] panel
+  T* Ak = P + (size_t)nb * B;             // [B][nb] old pivot rows
+  T* prow = Ak + (size_t)B * nb;          // [B] scaled pivot row of the panel
+  T* fcol = prow + B;                     // [nb] multipliers
+  int* perm = reinterpret_cast<int*>(fcol + nb);
+  __shared__ T redv[256];
+  __shared__ int redi[256];
+  T* A = blocks + (long long)blockIdx.x * nb * ld;
+  for (int k0 = 0; k0 < nb; k0 += B) {
+    const int bw = nb - k0 < B ? nb - k0 : B;
+    for (int i = threadIdx.x; i < nb * B; i += blockDim.x) {
+      const int r = i / B, j = i % B;
+      P[i] = j < bw ? A[(long long)r * ld + k0 + j] : (T)0;
+    }
+    __syncthreads();
+    for (int j = 0; j < bw; ++j) {
+      const int k = k0 + j;
+      T best = (T)-1;
+      int bi = k;
+      for (int i = k + threadIdx.x; i < nb; i += blockDim.x) {
+        const T v = fabs(P[i * B + j]);
+        if (v > best) {
+          best = v;
+          bi = i;
+        }
+      }
+      redv[threadIdx.x] = best;
+      redi[threadIdx.x] = bi;
+      __syncthreads();
+      for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+          const T o = redv[threadIdx.x + s];
+          const int oi = redi[threadIdx.x + s];
+          if (o > redv[threadIdx.x] || (o == redv[threadIdx.x] && oi < redi[threadIdx.x])) {
+            redv[threadIdx.x] = o;
+            redi[threadIdx.x] = oi;
+          }
+        }
+        __syncthreads();
+      }
+      const int pr = redi[0];
+      const T pmag = redv[0];
+      __syncthreads();
+      if (!(pmag > (T)0)) {
+        if (threadIdx.x == 0) atomicExch(fail, 1);
+        return;
+      }
+      if (threadIdx.x == 0) perm[k] = pr;
+      if (pr != k) {
+        for (int jj = threadIdx.x; jj < B; jj += blockDim.x) {
+          const T a = P[k * B + jj];
+          P[k * B + jj] = P[pr * B + jj];
+          P[pr * B + jj] = a;
+        }
+        for (int c = threadIdx.x; c < nb; c += blockDim.x) {
+          if (c >= k0 && c < k0 + bw) continue;
+          const T a = A[(long long)k * ld + c];
+          A[(long long)k * ld + c] = A[(long long)pr * ld + c];
+          A[(long long)pr * ld + c] = a;
+        }
+      }
+      __syncthreads();
+      const T ipiv = (T)1 / P[k * B + j];
+      for (int jj = threadIdx.x; jj < B; jj += blockDim.x)
+        prow[jj] = jj == j ? ipiv : P[k * B + jj] * ipiv;
+      for (int i = threadIdx.x; i < nb; i += blockDim.x) fcol[i] = P[i * B + j];
+      __syncthreads();
+      for (int i2 = threadIdx.x; i2 < nb * B; i2 += blockDim.x) {
+        const int i = i2 / B, jj = i2 % B;
+        if (i == k) {
+          P[i2] = prow[jj];
+        } else {
+          const T a = jj == j ? (T)0 : P[i2];
+          P[i2] = a - fcol[i] * prow[jj];
+        }
+      }
+      __syncthreads();
+    }
+    // old rows K of the columns outside the panel (after the interchanges)
+    for (int i = threadIdx.x; i < B * nb; i += blockDim.x) {
+      const int j = i / nb, c = i % nb;
+      Ak[i] = (j < bw && (c < k0 || c >= k0 + bw)) ? A[(long long)(k0 + j) * ld + c] : (T)0;
+    }
+    __syncthreads();
+    // A[:, c] += (T_K - E_K) A[K, c] for c outside the panel; panel columns <- T_K
+    for (int c = threadIdx.x; c < nb; c += blockDim.x) {
+      if (c >= k0 && c < k0 + bw) continue;
+      T ak[B];
+#pragma unroll
+      for (int j = 0; j < B; ++j) ak[j] = Ak[j * nb + c];
+      for (int i = 0; i < nb; ++i) {
+        const T* u = P + i * B;
+        T acc = A[(long long)i * ld + c];
+        const int dj = i - k0;
+#pragma unroll
+        for (int j = 0; j < B; ++j) acc += (u[j] - (j == dj ? (T)1 : (T)0)) * ak[j];
+        A[(long long)i * ld + c] = acc;
+      }
+    }
+    for (int i = threadIdx.x; i < nb * B; i += blockDim.x) {
+      const int r = i / B, j = i % B;
+      if (j < bw) A[(long long)r * ld + k0 + j] = P[i];
+    }
+    __syncthreads();
+  }
+  for (int k = nb - 1; k >= 0; --k) {
+    const int pr = perm[k];
+    if (pr != k)
+      for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+        const T a = A[(long long)i * ld + k];
+        A[(long long)i * ld + k] = A[(long long)i * ld + pr];
         A[(long long)i * ld + pr] = a;
       }
     __syncthreads();
@@ -783,10 +910,7 @@ __global__ void __launch_bounds__(128) brj_offdiag_kernel(
     src = dst;
     dst = t;
   }
-  const ElemGeo g = geo[e];
-  double idet = 1.0;
-#pragma unroll
-  for (int r = 0; r < DIM; ++r) idet *= 2.0 / g.h[r];
+  const double idet = geo[e].idet;
   const double sc = dta * idet;
   for (int i = threadIdx.x; i < NV * NM; i += blockDim.x) {
     const long long gi = (long long)e * NV * NM + i;
@@ -841,10 +965,11 @@ struct BRJImpl {
     }
     int* fail = (int*)(m->scratch + 16);
     DG_CUDA(cudaMemsetAsync(fail, 0, sizeof(int), s));
-    const size_t ism = sizeof(T) * 2 * nb + sizeof(int) * nb;
-    DG_CUDA(cudaFuncSetAttribute(brj_invert_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)ism));
-    DG_PROF(K_BRJ_INVERT, s, brj_invert_kernel<T><<<E, 512, ism, s>>>(blk, nb, ld, fail));
+    constexpr int IB = 32;  // panel width of the blocked inversion
+    const size_t ism = sizeof(T) * ((size_t)2 * nb * IB + IB + nb) + sizeof(int) * nb;
+    DG_CUDA(cudaFuncSetAttribute(brj_invert_blocked_kernel<T, IB>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism));
+    DG_PROF(K_BRJ_INVERT, s, brj_invert_blocked_kernel<T, IB><<<E, 256, ism, s>>>(blk, nb, ld, fail));
     DG_LAUNCHED(1);
     if (pc->precision == DG_PREC_BF16) {
       const long long n = (long long)E * nb * ld;
@@ -867,21 +992,120 @@ struct BRJImpl {
   }
 };
 
+// out = omega D^-1 y + (1-omega) qprev with the block stored transposed
+// (At[c][r] = (D^-1)[r][c], rows padded to ld): each thread owns VW
+// consecutive rows and streams the columns with one 16-byte load per column,
+// so a warp reads 512 contiguous bytes per column and needs no reduction;
+// SPLIT thread groups share the columns and add their partial sums in shared
+// memory.  Arithmetic in TA (FP64 for FP64 blocks, FP32 otherwise).
+template <typename TB>
+struct Vec16;
+template <>
+struct Vec16<double> {
+  static constexpr int W = 2;
+  using TA = double;
+  __device__ static void load(const double* p, double* o) {
+    const double2 v = __ldcs(reinterpret_cast<const double2*>(p));
+    o[0] = v.x;
+    o[1] = v.y;
+  }
+};
+template <>
+struct Vec16<float> {
+  static constexpr int W = 4;
+  using TA = float;
+  __device__ static void load(const float* p, float* o) {
+    const float4 v = __ldcs(reinterpret_cast<const float4*>(p));
+    o[0] = v.x;
+    o[1] = v.y;
+    o[2] = v.z;
+    o[3] = v.w;
+  }
+};
+template <>
+struct Vec16<__nv_bfloat16> {
+  static constexpr int W = 8;
+  using TA = float;
+  __device__ static void load(const __nv_bfloat16* p, float* o) {
+    const uint4 v = __ldcs(reinterpret_cast<const uint4*>(p));
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const float2 f = __bfloat1622float2(h[t]);
+      o[2 * t] = f.x;
+      o[2 * t + 1] = f.y;
+    }
+  }
+};
+
+template <typename TB>
+__global__ void __launch_bounds__(256) brj_diag_cm_kernel(const TB* __restrict__ blocks, int nb,
+                                                          int ld, int split,
+                                                          const double* __restrict__ y,
+                                                          const double* __restrict__ qprev,
+                                                          double omega, double* __restrict__ out) {
+  using V = Vec16<TB>;
+  using TA = typename V::TA;
+  constexpr int W = V::W;
+  extern __shared__ unsigned char smraw[];
+  TA* sy = reinterpret_cast<TA*>(smraw);                 // [nb]
+  TA* part = sy + nb;                                    // [split][ld]
+  const int e = blockIdx.x;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) sy[i] = (TA)y[(long long)e * nb + i];
+  __syncthreads();
+  const int nrq = ld / W;                                // row groups
+  const int rq = threadIdx.x % nrq, sp = threadIdx.x / nrq;
+  const int chunk = (nb + split - 1) / split;
+  const int c0 = sp * chunk, c1 = min(nb, c0 + chunk);
+  TA acc[W];
+#pragma unroll
+  for (int t = 0; t < W; ++t) acc[t] = (TA)0;
+  if (sp < split) {
+    const TB* A = blocks + (long long)e * nb * ld + rq * W;
+#pragma unroll 4
+    for (int c = c0; c < c1; ++c) {
+      TA a[W];
+      V::load(A + (long long)c * ld, a);
+      const TA yc = sy[c];
+#pragma unroll
+      for (int t = 0; t < W; ++t) acc[t] += a[t] * yc;
+    }
+#pragma unroll
+    for (int t = 0; t < W; ++t) part[sp * ld + rq * W + t] = acc[t];
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < nb; r += blockDim.x) {
+    TA s2 = (TA)0;
+    for (int k = 0; k < split; ++k) s2 += part[k * ld + r];
+    const long long gi = (long long)e * nb + r;
+    out[gi] = omega == 1.0 ? (double)s2 : omega * (double)s2 + (1.0 - omega) * qprev[gi];
+  }
+}
+
+template <typename TB>
+static dg_status diag_launch(const void* blocks, int E, int nb, int ld, const double* y,
+                             const double* qprev, double omega, double* out, cudaStream_t s) {
+  using V = Vec16<TB>;
+  const int nrq = ld / V::W;
+  int split = 256 / nrq;
+  if (split < 1) split = 1;
+  const int threads = ((nrq * split + 31) / 32) * 32;
+  if (threads > 256 && split == 1) return DG_ERR_UNSUPPORTED;  // ld > 256 W: not built
+  const size_t sm = sizeof(typename V::TA) * ((size_t)nb + (size_t)split * ld);
+  DG_PROF(K_BRJ_DIAG, s, brj_diag_cm_kernel<TB><<<E, threads, sm, s>>>(
+      (const TB*)blocks, nb, ld, split, y, qprev, omega, out));
+  DG_LAUNCHED(1);
+  return DG_OK;
+}
+
 static dg_status diag_apply(dg_precond_s* pc, const double* y, const double* qprev, double* out,
                             cudaStream_t s) {
   const int E = pc->mesh->E, nb = pc->nb, ld = round_up8(nb);
-  if (pc->precision == DG_PREC_FP64) {
-    DG_PROF(K_BRJ_DIAG, s, brj_diag_kernel<double, double><<<E, 256, sizeof(double) * nb, s>>>(
-        (const double*)pc->blocks, nb, ld, y, qprev, pc->omega, out));
-  } else if (pc->precision == DG_PREC_FP32) {
-    DG_PROF(K_BRJ_DIAG, s, brj_diag_f32_kernel<<<E, 256, sizeof(float) * ld, s>>>(
-        (const float*)pc->blocks, nb, ld, y, qprev, pc->omega, out));
-  } else {
-    DG_PROF(K_BRJ_DIAG, s, brj_diag_bf16_kernel<<<E, 256, sizeof(float) * ld, s>>>((const __nv_bfloat16*)pc->blocks, nb,
-                                                           ld, y, qprev, pc->omega, out));
-  }
-  DG_LAUNCHED(1);
-  return DG_OK;
+  if (pc->precision == DG_PREC_FP64)
+    return diag_launch<double>(pc->blocks, E, nb, ld, y, qprev, pc->omega, out, s);
+  if (pc->precision == DG_PREC_FP32)
+    return diag_launch<float>(pc->blocks, E, nb, ld, y, qprev, pc->omega, out, s);
+  return diag_launch<__nv_bfloat16>(pc->blocks, E, nb, ld, y, qprev, pc->omega, out, s);
 }
 
 #define DG_PREC_INSTANCES(X)                                                                  \

@@ -88,27 +88,16 @@ __global__ void __launch_bounds__(256) vol_kernel(const __grid_constant__ Tables
     double U[NV], dU[DIM][NV], H[DIM][NV];
     double rh[DIM];
 #pragma unroll
-    for (int r = 0; r < DIM; ++r) rh[r] = 2.0 / g.h[r];
+    for (int r = 0; r < DIM; ++r) rh[r] = g.rh[r];
 #pragma unroll
     for (int vv = 0; vv < NV; ++vv) {
       U[vv] = sQ[(eb * NV + vv) * NQ + q];
 #pragma unroll
       for (int r = 0; r < DIM; ++r) dU[r][vv] = sG[((r * EPB + eb) * NV + vv) * NQ + q] * rh[r];
     }
-    euler_flux<DIM>(U, ph, H);
-    if (ph.viscous) {
-      double G[DIM][NV];
-      viscous_flux<DIM>(U, dU, ph, G);
-#pragma unroll
-      for (int r = 0; r < DIM; ++r)
-#pragma unroll
-        for (int vv = 0; vv < NV; ++vv) H[r][vv] -= G[r][vv];
-    }
+    ns_volume_flux<DIM>(U, dU, ph, H);
     double wJ = sw[c[0]] * sw[c[1]] * (DIM == 3 ? sw[c[2]] : 1.0);
-    double detJ = 1.0;
-#pragma unroll
-    for (int r = 0; r < DIM; ++r) detJ *= 0.5 * g.h[r];
-    wJ *= detJ;
+    wJ *= g.detJ;
     double* hb = hbuf + (long long)e * DIM * NV * NQ + q;
 #pragma unroll
     for (int r = 0; r < DIM; ++r) {
@@ -148,7 +137,7 @@ __global__ void __launch_bounds__(256) vol_kernel(const __grid_constant__ Tables
     double acc = 0.0;
 #pragma unroll
     for (int k = 0; k < Q; ++k) acc = fma(lw[k], src[base + k * str], acc);
-    if (fld > 0) acc *= 2.0 / geo[e].h[fld - 1];
+    if (fld > 0) acc *= geo[e].rh[fld - 1];
     tbuf[(long long)e * NTR + ((lf * (1 + DIM) + fld) * NV + vv) * NF + p] = acc;
   }
 }
@@ -197,14 +186,14 @@ __global__ void __launch_bounds__(128) face_kernel(const __grid_constant__ Table
 #pragma unroll
     for (int j = 0; j < DIM; ++j) dQL[j][vv] = tl[((1 + j) * NV + vv) * NF];
   }
-  double hmin = gL.h[r], cfac;
-  double hR[DIM];
+  double rmax = gL.rh[r], cfac;  // 2 / min(h_L, h_R)
+  double rhR[DIM];
   int bctype = 0;
   if (eR >= 0) {
     const ElemGeo gR = geo[eR];
-    hmin = fmin(hmin, gR.h[r]);
+    rmax = fmax(rmax, gR.rh[r]);
 #pragma unroll
-    for (int k = 0; k < DIM; ++k) hR[k] = gR.h[k];
+    for (int k = 0; k < DIM; ++k) rhR[k] = gR.rh[k];
     const double* tr = tbuf + (long long)eR * NTR + (fR * (1 + DIM)) * NV * NF + p;
 #pragma unroll
     for (int vv = 0; vv < NV; ++vv) {
@@ -224,25 +213,33 @@ __global__ void __launch_bounds__(128) face_kernel(const __grid_constant__ Table
     cfac = 1.0;
   }
   double Hn[NV], S[DIM][NV];
-  const double beta = (double)((P + 1) * (P + 1)) / hmin;
-  numerical_flux<DIM>(QL, QR, bctype, x, t, dQa, r, sgn, beta, ph, Hn, S);
+  const double beta = (double)((P + 1) * (P + 1)) * 0.5 * rmax;  // (P+1)^2 / h
+  if (r == 0)
+    numerical_flux_axis<DIM, 0>(QL, QR, bctype, x, t, dQa, sgn, beta, ph, Hn, S);
+  else if (r == 1)
+    numerical_flux_axis<DIM, 1>(QL, QR, bctype, x, t, dQa, sgn, beta, ph, Hn, S);
+  else
+    numerical_flux_axis<DIM, DIM - 1>(QL, QR, bctype, x, t, dQa, sgn, beta, ph, Hn, S);
   double* fl = fbuf + (long long)eL * NTR + (fL * (1 + DIM)) * NV * NF + p;
-  const double cs = cfac * ph.beta_s * wJf;
+  const double cs = ph.viscous ? cfac * ph.beta_s * wJf : 0.0;
+  double csL[DIM];
+#pragma unroll
+  for (int j = 0; j < DIM; ++j) csL[j] = cs * gL.rh[j];
 #pragma unroll
   for (int vv = 0; vv < NV; ++vv) {
     fl[vv * NF] = -Hn[vv] * wJf;
 #pragma unroll
-    for (int j = 0; j < DIM; ++j)
-      fl[((1 + j) * NV + vv) * NF] = ph.viscous ? cs * (2.0 / gL.h[j]) * S[j][vv] : 0.0;
+    for (int j = 0; j < DIM; ++j) fl[((1 + j) * NV + vv) * NF] = csL[j] * S[j][vv];
   }
   if (eR >= 0) {
     double* fr = fbuf + (long long)eR * NTR + (fR * (1 + DIM)) * NV * NF + p;
 #pragma unroll
+    for (int j = 0; j < DIM; ++j) csL[j] = cs * rhR[j];
+#pragma unroll
     for (int vv = 0; vv < NV; ++vv) {
       fr[vv * NF] = Hn[vv] * wJf;
 #pragma unroll
-      for (int j = 0; j < DIM; ++j)
-        fr[((1 + j) * NV + vv) * NF] = ph.viscous ? cs * (2.0 / hR[j]) * S[j][vv] : 0.0;
+      for (int j = 0; j < DIM; ++j) fr[((1 + j) * NV + vv) * NF] = csL[j] * S[j][vv];
     }
   }
 }
@@ -356,10 +353,7 @@ __global__ void __launch_bounds__(256) lift_kernel(const __grid_constant__ Table
     const int eb = i / (NV * NM);
     const int e = e0 + eb;
     if (e >= E) continue;
-    const ElemGeo g = geo[e];
-    double idet = 1.0;
-#pragma unroll
-    for (int r = 0; r < DIM; ++r) idet *= 2.0 / g.h[r];
+    const double idet = geo[e].idet;
     const long long gi = (long long)e * NV * NM + (i - eb * NV * NM);
     double R = sR[i] * idet;
     if (force) R += force[gi];
@@ -425,9 +419,7 @@ __global__ void __launch_bounds__(256) project_kernel(const __grid_constant__ Ta
     const int eb = i / (NV * NM);
     const int e = e0 + eb;
     if (e >= E) continue;
-    const ElemGeo g = geo[e];
-    double idet = 1.0;
-    for (int r = 0; r < DIM; ++r) idet *= 2.0 / g.h[r];
+    const double idet = geo[e].idet;
     out[(long long)e * NV * NM + (i - eb * NV * NM)] = sH[i] * idet;
   }
 }
