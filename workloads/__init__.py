@@ -12,4 +12,4 @@ from .configs import (  # noqa: F401
     RIEMANN_ROE, RIEMANN_HLLC, FORCING_NONE, FORCING_POISEUILLE,
     vortex_case, poiseuille_case, tgv_case, cylinder_case, small_tgv_case,
 )
-from .random import random_direction, perturbation  # noqa: F401
+from .random import random_direction, perturbation, mlp_params  # noqa: F401
