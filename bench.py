@@ -35,6 +35,9 @@ if ROOT not in sys.path:
 WORKLOAD = {"n": 16, "P": 3, "Q": 6, "Re": 1600.0, "Ma": 0.1, "cfl": 0.10, "dt_factor": 10.0}
 SAMPLE_N = 3          # CPU sample: the same case on 3^3 elements (same P, Q, CFL)
 FREEZE = 10
+# DRAM bytes (read + write) per element and launch from one ncu capture of the
+# kernel as it stands (profiles/); a kernel changed since then has no entry
+TRAFFIC_PER_ELEM = {("brj_diag", "fp32", 3, 6): 418_300.0}
 
 
 def tgv_dt(n, P, Ma, cfl=0.10, factor=10.0):
@@ -139,12 +142,25 @@ def run_ours(args, rank, world):
     case = w.tgv_case(n=wl["n"], P=wl["P"], Q=wl["Q"], Re=wl["Re"], Ma=wl["Ma"])
     dt = tgv_dt(wl["n"], wl["P"], wl["Ma"], wl["cfl"], wl["dt_factor"])
     m = dgl.Mesh.from_case(case)
+    tuning = dgl.apply_tuning(m)          # stored autotuning choice for this (dim, P, Q)
     ndof = m.info["n_dof"]
     E = m.info["n_elem"]
     nb = m.info["n_var"] * m.info["n_mode"]
     u = m.project(0.0)
     pc = dgl.Precond(m)
     kw = dict(restart=30, rtol=5e-2, alpha=1e-3, J=7, precision=args.precision)
+    if args.guess != "plain":
+        # initial guess S_m + previous stage increment (+ learned MLP correction, one
+        # per stage, 2 x 256 hidden, seeded weights with a zero output layer,
+        # trained online during the warm-up and the timed steps)
+        nb = m.info["n_var"] * m.info["n_mode"]
+        params = None
+        if args.guess == "learned":
+            params = (w.mlp_params(3 * nb, 256, nb, seed=101, zero_last=True)
+                      + w.mlp_params(3 * nb, 256, nb, seed=102, zero_last=True))
+        kw["guess"] = dgl.Guess(m, params, stages=2, hidden=256, lr=1e-3)
+        kw["guess_train_iters"] = 4
+        args.warmup = max(args.warmup, 6)
     state = {"k": 0, "t": 0.0}
     stats = []
 
@@ -202,6 +218,10 @@ def run_ours(args, rank, world):
     avg_ms = prof[dom][1] / prof[dom][0]
     roof = {"kernel": dom, "launches": prof[dom][0], "avg_ms": avg_ms,
             "share": prof[dom][1] / total_k, "traffic": None}
+    tkey = (dom, args.precision, wl["P"], wl["Q"])
+    if tkey in TRAFFIC_PER_ELEM:
+        roof["traffic"] = TRAFFIC_PER_ELEM[tkey] * E
+        roof["traffic_source"] = "ncu dram bytes of a 512-element capture scaled by elements"
     clock_mhz = clk.get("sm_max_mhz") or pk.get("sm_max_mhz", 2070.0)
     if bound == "hbm":
         roof.update(bound="hbm", achieved=work / (avg_ms / 1e3) / 1e9, peak=pk["hbm_gbs"], unit="GB/s",
@@ -270,8 +290,15 @@ def run_ours(args, rank, world):
         "config": {"workload": f"tgv{wl['n']}^3_P{wl['P']}_Q{wl['Q']}_sdirk2_dt{wl['dt_factor']:g}xexplicit",
                    "n_dof": ndof, "dt": dt, "newton_alpha": 1e-3, "gmres": "restart 30, rtol 5e-2",
                    "precond": f"BRJ(7) {args.precision} blocks, rebuilt every {FREEZE} steps",
+                   "initial_guess": {"plain": "S_m (plain)",
+                                     "extrap": "S_m + previous stage increment",
+                                     "learned": "S_m + previous stage increment + per-element "
+                                                "MLP correction (2x256, BF16, online Adam)"}[args.guess],
                    "l2": "working set > L2 (BRJ blocks %.2f GB read per sweep)" % (E * nb * nb * prec_bytes / 1e9),
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": f"replicas x{world}",
+                   "launch_shapes": ({k: tuning[k] for k in ("vol_epb", "vol_threads", "lift_epb",
+                                                             "lift_threads")}
+                                     if tuning else "built-in defaults")},
         "newton_per_step": sum(newton) / len(newton),
         "gmres_per_step": sum(gm) / len(gm),
         "residual_gdofs": ndof / (res_ms / 1e3) / 1e9,
@@ -367,6 +394,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "bf16"])
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--guess", default="plain", choices=["plain", "extrap", "learned"],
+                    help="Newton initial guess: S_m, S_m + previous stage increment, or that plus "
+                         "the learned MLP correction")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--elems", type=int, default=WORKLOAD["n"],
                     help="elements per direction (16 = the benchmark; smaller only for profiler captures)")

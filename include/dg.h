@@ -99,6 +99,21 @@ dg_status dg_mesh_create(const dg_mesh_desc* mesh, const dg_physics* phys, void*
 dg_status dg_mesh_destroy(dg_mesh_t m);
 dg_status dg_mesh_info(dg_mesh_t m, dg_mesh_info_t* info);
 
+/* Autotuning of the sum-factorisation kernels (no counterpart in the paper,
+ * whose kernels ran on CPUs): dg_autotune times every launch shape (elements
+ * per CTA, threads per CTA) of the volume and lift kernels that fits one CTA's
+ * shared memory, reps launches each, on the projected analytic field, and keeps
+ * the fastest for this mesh; result receives the choice and its times (ms per
+ * launch; *_default: the built-in shape).  dg_set_tune applies a shape taken
+ * from a stored tuning table (DG_ERR_ARG if it is not a candidate for this
+ * (dim, P, Q)).  Results do not depend on the shape. */
+typedef struct {
+  int vol_epb, vol_threads, lift_epb, lift_threads;
+  double vol_ms, lift_ms, vol_ms_default, lift_ms_default;
+} dg_tune_result;
+dg_status dg_autotune(dg_mesh_t m, int reps, dg_tune_result* result, void* stream);
+dg_status dg_set_tune(dg_mesh_t m, const dg_tune_result* t);
+
 /* u = L2 projection of the workload's analytic field at time t (Sec. 3.1,
  * Eq. coeff: M u = B^T Lambda(wJ) U(x_q)). */
 dg_status dg_project(dg_mesh_t m, double t, double* u, void* stream);
@@ -119,11 +134,17 @@ dg_status dg_jvp(dg_mesh_t m, const double* u, const double* r_u, double t, cons
 
 enum { DG_PREC_FP64 = 0, DG_PREC_FP32 = 1, DG_PREC_BF16 = 2 };
 /* BRJ(J) settings (Sec. 4.2.2, Eq. precond-Jacobi): J sweeps (>= 1),
- * relaxation omega, storage/arithmetic precision of the blocks. */
+ * relaxation omega, storage/arithmetic precision of the blocks.  graphs != 0
+ * replays the 2J-1 launches of one apply as a CUDA graph, captured once per
+ * (q, out) pointer pair on the handle's own stream and fenced to the caller's
+ * stream with events (same arithmetic, fewer launches from the host); the
+ * graphs are dropped on every rebuild and bypassed while dg_profile_enable is
+ * on.  An apply with graphs on must not itself run inside a stream capture. */
 typedef struct {
   int J;
   int precision;
   double omega;
+  int graphs;
 } dg_prec_cfg;
 
 /* Build (or rebuild in place, when *inout is not NULL and was built for the
@@ -199,14 +220,64 @@ typedef struct {
   int use_precond;
   dg_gmres_cfg gmres;
   dg_prec_cfg prec;
+  struct dg_guess_s* guess; /* optional learned initial guess (NULL: S_m) */
+  int guess_train_iters;    /* Adam steps per converged stage */
 } dg_sdirk_cfg;
 typedef struct {
   int newton_iters, gmres_iters, stages, precond_built;
   int stage_newton[4], stage_gmres[4];
   double stage_res0[4], stage_res[4];
+  int guess_used; /* stages that started from the learned guess */
 } dg_step_stats;
 dg_status sdirk_step(dg_mesh_t m, const dg_sdirk_cfg* cfg, double* u_inout, double t, double dt,
                      dg_precond_t* p_inout, dg_step_stats* stats, void* stream);
+
+/* Learned Newton initial guess.  The paper's guess for stage m is S_m
+ * (Eq. Newton-initial-guess); this optional extension starts Newton from
+ *   S_m + d_prev + y (x) tau_m,
+ * where d_prev is the converged increment u^m - S_m of the same stage in the
+ * previous step (an extrapolation in time) and y a per-element MLP per stage,
+ *   x_e = [u^n/s0, (u^n-u^{n-1})/s1, d_prev/s2]   (s_k[v]: per-variable RMS),
+ *   a1 = tanh(x W1 + b1), a2 = tanh(a1 W2 + b2), y = a2 W3 + b3,
+ * trained online with Adam on the remainder (u^m - S_m - d_prev)/tau_m
+ * (tau_m[v]: its per-variable RMS), BF16 operands and FP32 accumulation in
+ * every product, FP32 master parameters.  mlp = 0 keeps only the
+ * extrapolation.  The guess only seeds Newton: sdirk_step keeps S_m when the
+ * guess's ||N|| is not smaller, and stops Newton at the absolute tolerance
+ * alpha ||N(S_m)|| (the plain method's criterion) in both cases.  Training
+ * data are the converged stages of the steps taken (dg_guess_train, called by
+ * sdirk_step when cfg.guess is set). */
+typedef struct dg_guess_s* dg_guess_t;
+typedef struct {
+  int stages, hidden, mlp;
+  float lr, beta1, beta2, eps;
+  float gate; /* use the MLP correction of a stage once its training loss is
+                 below gate x that of a zero correction (<= 0: 0.2) */
+} dg_guess_cfg;
+/* params (ignored when mlp = 0): host FP32 arrays, for each stage s the six arrays
+ * params[6s+0..5] = W1 [3 N_v N_m][hidden], b1 [hidden], W2 [hidden][hidden],
+ * b2 [hidden], W3 [hidden][N_v N_m], b3 [N_v N_m] (row-major), copied. */
+dg_status dg_guess_create(dg_mesh_t m, const dg_guess_cfg* cfg, const float* const* params,
+                          dg_guess_t* out);
+dg_status dg_guess_destroy(dg_guess_t g);
+/* Append a step solution u (device) to the two-entry history (u^n, u^{n-1}). */
+dg_status dg_guess_push(dg_guess_t g, const double* u, void* stream);
+/* *ready = 1 when the history is full and stage `stage` has a previous increment. */
+dg_status dg_guess_ready(dg_guess_t g, int stage, int* ready);
+/* out = S + d_prev (+ MLP correction) for stage `stage` (device vectors). */
+dg_status dg_guess_predict(dg_guess_t g, int stage, const double* S, double* out, void* stream);
+/* Record the converged stage: iters Adam steps on the target
+ * (u - S - d_prev)/tau of stage `stage` (all elements one batch; skipped until
+ * a previous increment exists), then d_prev = u - S.  loss_first/last (host,
+ * may be NULL): loss before the first and after the last step (-1 when no
+ * training happened); grads_host (may be NULL, entries may be NULL): the six
+ * FP32 gradients at the entry parameters.  iters = 0 evaluates without
+ * updating the parameters. */
+dg_status dg_guess_train(dg_guess_t g, int stage, const double* S, const double* u, int iters,
+                         double* loss_first, double* loss_last, float* const* grads_host,
+                         void* stream);
+/* Copy the six FP32 master parameters of a stage to host arrays. */
+dg_status dg_guess_params(dg_guess_t g, int stage, float* const* host_out);
 
 /* Number of CUDA kernels this library has launched since it was loaded
  * (all handles, all streams); a diagnostic counter for benchmarks. */

@@ -121,12 +121,15 @@ class Mesh:
 
     def sdirk_step(self, u, t, dt, precond=None, tableau=2, alpha=1e-3, abs_tol=0.0,
                    max_newton=20, rebuild=False, restart=30, max_cycles=10, rtol=5e-2,
-                   J=7, precision="fp64", omega=1.0, use_precond=True, stream=None):
+                   J=7, precision="fp64", omega=1.0, use_precond=True, guess=None,
+                   guess_train_iters=4, graphs=False, stream=None):
         """One SDIRK step in place on u; `precond` is a Precond holder whose
-        handle is built (or reused, frozen) by the library."""
+        handle is built (or reused, frozen) by the library; `guess` an optional
+        Guess (learned initial guess, trained on the converged stages)."""
         cfg = _lib.SdirkCfg(tableau, alpha, abs_tol, max_newton, int(rebuild), int(use_precond),
                             _lib.GmresCfg(restart, max_cycles, rtol),
-                            _lib.PrecCfg(J, _lib.PREC[precision], omega))
+                            _lib.PrecCfg(J, _lib.PREC[precision], omega, int(graphs)),
+                            guess.handle if guess is not None else None, guess_train_iters)
         st = _lib.StepStats()
         holder = precond if precond is not None else Precond(self)
         code = self._lib.sdirk_step(self.handle, ctypes.byref(cfg), _ptr(u), t, dt,
@@ -147,8 +150,9 @@ class Precond:
         self.handle = ctypes.c_void_p()
         self._lib = lib()
 
-    def build(self, u, t=0.0, dt_a=0.0, J=7, precision="fp64", omega=1.0, stream=None):
-        cfg = _lib.PrecCfg(J, _lib.PREC[precision], omega)
+    def build(self, u, t=0.0, dt_a=0.0, J=7, precision="fp64", omega=1.0, graphs=False,
+              stream=None):
+        cfg = _lib.PrecCfg(J, _lib.PREC[precision], omega, int(graphs))
         _check("dg_precond_build", self._lib.dg_precond_build(
             self.mesh.handle, _ptr(u), t, dt_a, ctypes.byref(cfg), ctypes.byref(self.handle),
             _stream(stream)))
@@ -187,3 +191,95 @@ def profile_read(cap=32):
     n = ctypes.c_int()
     _check("dg_profile_read", lib().dg_profile_read(arr, cap, ctypes.byref(n)))
     return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].ms)) for i in range(n.value)}
+
+
+class Guess:
+    """Holder of a learned-initial-guess handle (dg_guess_t): the previous
+    step's stage increment plus, when `params` is given, one MLP correction per
+    SDIRK stage (`params`: the 6*stages FP32 host arrays W1, b1, W2, b2, W3, b3
+    of each stage, initial values); params=None keeps the extrapolation only."""
+
+    def __init__(self, mesh, params=None, stages=2, hidden=256, lr=1e-3, beta1=0.9,
+                 beta2=0.999, eps=1e-8, gate=0.2):
+        import numpy as np
+        self.mesh = mesh
+        self._lib = lib()
+        self._arrs = [np.ascontiguousarray(p, dtype=np.float32) for p in (params or [])]
+        ptrs = (ctypes.c_void_p * max(1, len(self._arrs)))(*[a.ctypes.data for a in self._arrs])
+        cfg = _lib.GuessCfg(stages, hidden if params else 0, 1 if params else 0, lr, beta1, beta2,
+                            eps, gate)
+        self.handle = ctypes.c_void_p()
+        _check("dg_guess_create", self._lib.dg_guess_create(mesh.handle, ctypes.byref(cfg), ptrs,
+                                                            ctypes.byref(self.handle)))
+        self.shapes = [a.shape for a in self._arrs[:6]]
+
+    def push(self, u, stream=None):
+        _check("dg_guess_push", self._lib.dg_guess_push(self.handle, _ptr(u), _stream(stream)))
+
+    def ready(self, stage):
+        r = ctypes.c_int()
+        _check("dg_guess_ready", self._lib.dg_guess_ready(self.handle, stage, ctypes.byref(r)))
+        return bool(r.value)
+
+    def predict(self, stage, S, out=None, stream=None):
+        out = self.mesh.empty() if out is None else out
+        _check("dg_guess_predict", self._lib.dg_guess_predict(self.handle, stage, _ptr(S),
+                                                              _ptr(out), _stream(stream)))
+        return out
+
+    def train(self, stage, S, u, iters=1, grads=False, stream=None):
+        """Adam steps on target u - S; returns (loss before, loss after, grads at
+        entry or None)."""
+        import numpy as np
+        l0, l1 = ctypes.c_double(), ctypes.c_double()
+        g = [np.zeros(s, dtype=np.float32) for s in self.shapes] if grads else None
+        gp = (ctypes.c_void_p * 6)(*[a.ctypes.data for a in g]) if grads else None
+        _check("dg_guess_train", self._lib.dg_guess_train(
+            self.handle, stage, _ptr(S), _ptr(u), iters, ctypes.byref(l0), ctypes.byref(l1), gp,
+            _stream(stream)))
+        return l0.value, l1.value, g
+
+    def params(self, stage):
+        import numpy as np
+        out = [np.zeros(s, dtype=np.float32) for s in self.shapes]
+        ptrs = (ctypes.c_void_p * 6)(*[a.ctypes.data for a in out])
+        _check("dg_guess_params", self._lib.dg_guess_params(self.handle, stage, ptrs))
+        return out
+
+    def close(self):
+        if self.handle:
+            self._lib.dg_guess_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+TUNING_TABLE = __import__("os").path.join(__import__("os").path.dirname(__file__), "tuning.json")
+
+
+def autotune(mesh, reps=5, stream=None):
+    """Time the launch shapes of the sum-factorisation kernels on `mesh`, keep
+    the fastest, and return the choice (a dict) with its timings."""
+    r = _lib.TuneResult()
+    _check("dg_autotune", lib().dg_autotune(mesh.handle, reps, ctypes.byref(r), _stream(stream)))
+    return {f: getattr(r, f) for f, _ in _lib.TuneResult._fields_}
+
+
+def apply_tuning(mesh, table_path=TUNING_TABLE):
+    """Apply the stored tuning-table entry of this mesh's (dim, P, Q), if any."""
+    import json
+    import os
+    if not os.path.exists(table_path):
+        return None
+    key = f"{mesh.info['dim']}d_P{mesh.info['P']}_Q{mesh.info['Q']}"
+    entry = json.load(open(table_path)).get(key)
+    if entry is None:
+        return None
+    r = _lib.TuneResult(entry["vol_epb"], entry["vol_threads"], entry["lift_epb"],
+                        entry["lift_threads"], 0.0, 0.0, 0.0, 0.0)
+    _check("dg_set_tune", lib().dg_set_tune(mesh.handle, ctypes.byref(r)))
+    return entry

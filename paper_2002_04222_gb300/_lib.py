@@ -48,7 +48,8 @@ class MeshInfo(ctypes.Structure):
 
 
 class PrecCfg(ctypes.Structure):
-    _fields_ = [("J", ctypes.c_int), ("precision", ctypes.c_int), ("omega", ctypes.c_double)]
+    _fields_ = [("J", ctypes.c_int), ("precision", ctypes.c_int), ("omega", ctypes.c_double),
+                ("graphs", ctypes.c_int)]
 
 
 class GmresCfg(ctypes.Structure):
@@ -63,14 +64,29 @@ class GmresStats(ctypes.Structure):
 class SdirkCfg(ctypes.Structure):
     _fields_ = [("tableau", ctypes.c_int), ("alpha", ctypes.c_double), ("abs_tol", ctypes.c_double),
                 ("max_newton", ctypes.c_int), ("rebuild", ctypes.c_int), ("use_precond", ctypes.c_int),
-                ("gmres", GmresCfg), ("prec", PrecCfg)]
+                ("gmres", GmresCfg), ("prec", PrecCfg), ("guess", ctypes.c_void_p),
+                ("guess_train_iters", ctypes.c_int)]
 
 
 class StepStats(ctypes.Structure):
     _fields_ = [("newton_iters", ctypes.c_int), ("gmres_iters", ctypes.c_int), ("stages", ctypes.c_int),
                 ("precond_built", ctypes.c_int), ("stage_newton", ctypes.c_int * 4),
                 ("stage_gmres", ctypes.c_int * 4), ("stage_res0", ctypes.c_double * 4),
-                ("stage_res", ctypes.c_double * 4)]
+                ("stage_res", ctypes.c_double * 4), ("guess_used", ctypes.c_int)]
+
+
+class GuessCfg(ctypes.Structure):
+    _fields_ = [("stages", ctypes.c_int), ("hidden", ctypes.c_int), ("mlp", ctypes.c_int),
+                ("lr", ctypes.c_float),
+                ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float),
+                ("gate", ctypes.c_float)]
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [("vol_epb", ctypes.c_int), ("vol_threads", ctypes.c_int), ("lift_epb", ctypes.c_int),
+                ("lift_threads", ctypes.c_int), ("vol_ms", ctypes.c_double),
+                ("lift_ms", ctypes.c_double), ("vol_ms_default", ctypes.c_double),
+                ("lift_ms_default", ctypes.c_double)]
 
 
 class KernelTime(ctypes.Structure):
@@ -95,6 +111,16 @@ SIGNATURES = {
     "sdirk_step": [VP, ctypes.POINTER(SdirkCfg), VP, D, D, ctypes.POINTER(VP), ctypes.POINTER(StepStats), VP],
     "dg_status_string": [I],
     "dg_kernel_launches": [],
+    "dg_autotune": [VP, I, ctypes.POINTER(TuneResult), VP],
+    "dg_set_tune": [VP, ctypes.POINTER(TuneResult)],
+    "dg_guess_create": [VP, ctypes.POINTER(GuessCfg), ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(VP)],
+    "dg_guess_destroy": [VP],
+    "dg_guess_push": [VP, VP, VP],
+    "dg_guess_ready": [VP, I, ctypes.POINTER(I)],
+    "dg_guess_predict": [VP, I, VP, VP, VP],
+    "dg_guess_train": [VP, I, VP, VP, I, ctypes.POINTER(D), ctypes.POINTER(D),
+                       ctypes.POINTER(ctypes.c_void_p), VP],
+    "dg_guess_params": [VP, I, ctypes.POINTER(ctypes.c_void_p)],
     "dg_profile_enable": [I],
     "dg_profile_read": [ctypes.POINTER(KernelTime), I, ctypes.POINTER(I)],
 }

@@ -53,6 +53,12 @@ dg_status dot(const double* a, const double* b, long long n, double* partial, do
   return DG_OK;
 }
 
+dg_status finish_sum(const double* partial, int np, double* out, cudaStream_t s) {
+  finish_kernel<<<1, RT, 0, s>>>(partial, np, 1, out);
+  DG_LAUNCHED(1);
+  return DG_OK;
+}
+
 // partial[i*RED_BLOCKS + b] = chunk-b part of V_i . w for i in [8*blockIdx.y, +8)
 __global__ void __launch_bounds__(RT) multi_dot_kernel(const double* __restrict__ V, int k,
                                                        const double* __restrict__ w, long long n,

@@ -38,6 +38,8 @@ static cudaEvent_t take_event() {
   return e;
 }
 
+bool profiling_on() { return g_prof; }
+
 int prof_begin(int id, cudaStream_t s) {
   if (!g_prof) return -1;
   ProfRec r{id, take_event(), take_event()};
@@ -362,6 +364,7 @@ dg_status dg_mesh_create(const dg_mesh_desc* md, const dg_physics* ph, void* str
   m->nf = d == 2 ? md->Q : md->Q * md->Q;
   m->ndof = (long long)E * m->nv * m->nm;
   build_tables(md->P, md->Q, m->tab);
+  init_tune(m);
   Phys& p = m->phys;
   std::memset(&p, 0, sizeof(p));
   p.gamma = ph->gamma;
@@ -442,6 +445,24 @@ dg_status dg_mesh_info(dg_mesh_t m, dg_mesh_info_t* info) {
   info->n_quad = m->nq;
   info->n_faces = m->F;
   info->n_dof = m->ndof;
+  return DG_OK;
+}
+
+dg_status dg_autotune(dg_mesh_t m, int reps, dg_tune_result* result, void* stream) {
+  if (!m || !result || reps < 1) return DG_ERR_ARG;
+  dg_tune_result r{};
+  DG_TRY(autotune(m, reps, &r, (cudaStream_t)stream));
+  *result = r;
+  return DG_OK;
+}
+
+dg_status dg_set_tune(dg_mesh_t m, const dg_tune_result* t) {
+  if (!m || !t) return DG_ERR_ARG;
+  if (!tune_valid(m, t)) return DG_ERR_ARG;
+  m->tune.vol_epb = t->vol_epb;
+  m->tune.vol_threads = t->vol_threads;
+  m->tune.lift_epb = t->lift_epb;
+  m->tune.lift_threads = t->lift_threads;
   return DG_OK;
 }
 
@@ -662,7 +683,7 @@ dg_status sdirk_step(dg_mesh_t m, const dg_sdirk_cfg* cfg, double* u_n, double t
   double A[3][3], b[3], c[3];
   int M;
   tableau(cfg->tableau, A, b, c, &M);
-  if (!m->stage) DG_CUDA(cudaMalloc(&m->stage, sizeof(double) * (size_t)n * 7));
+  if (!m->stage) DG_CUDA(cudaMalloc(&m->stage, sizeof(double) * (size_t)n * 10));
   double* Ev[3] = {m->stage, m->stage + n, m->stage + 2 * n};
   double* Sv = m->stage + 3 * n;
   double* U = m->stage + 4 * n;
@@ -680,6 +701,12 @@ dg_status sdirk_step(dg_mesh_t m, const dg_sdirk_cfg* cfg, double* u_n, double t
     P = *p_inout;
   }
   dg_status result = DG_OK;
+  dg_guess_s* G = cfg->guess;
+  // candidate buffers for the learned guess (swapped with U, R, N when taken)
+  double* U2 = m->stage + 7 * n;
+  double* R2 = m->stage + 8 * n;
+  double* N2 = m->stage + 9 * n;
+  if (G && guess_history_empty(G)) DG_TRY(dg_guess_push(G, u_n, s));
   for (int i = 0; i < M; ++i) {
     // S_i = u^n + sum_{j<i} a_ij E^j
     DG_CUDA(cudaMemcpyAsync(Sv, u_n, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
@@ -692,10 +719,33 @@ dg_status sdirk_step(dg_mesh_t m, const dg_sdirk_cfg* cfg, double* u_n, double t
     DG_TRY(host_norm(m, Nn, &res, s));
     const double res0 = res;
     const double tol = cfg->abs_tol > 0.0 ? cfg->abs_tol : cfg->alpha * res0;
+    // with a learned guess the criterion stays alpha ||N(S_i)||, as an absolute tolerance
+    const bool abs_mode = cfg->abs_tol > 0.0 || G != nullptr;
+    if (G) {
+      int ready = 0;
+      DG_TRY(dg_guess_ready(G, i, &ready));
+      if (ready) {
+        DG_TRY(dg_guess_predict(G, i, Sv, U2, s));
+        DG_TRY(dg_residual(m, U2, ti, R2, s));
+        DG_TRY(newton_resid(N2, U2, Sv, R2, dta, n, s));
+        double resc;
+        const dg_status ns = host_norm(m, N2, &resc, s);
+        if (ns != DG_OK && ns != DG_ERR_NONFINITE) return ns;
+        // a non-finite candidate (e.g. a predicted state without positive
+        // density) is rejected like any guess that does not lower ||N||
+        if (ns == DG_OK && resc < res0) {
+          std::swap(U, U2);
+          std::swap(R, R2);
+          std::swap(Nn, N2);
+          res = resc;
+          st.guess_used++;
+        }
+      }
+    }
     int it = 0, gits = 0;
     bool conv = false;
     while (true) {
-      if (res <= 0.0 || ((it > 0 || cfg->abs_tol > 0.0) && res < tol)) {
+      if (res <= 0.0 || ((it > 0 || abs_mode) && res < tol)) {
         conv = true;
         break;
       }
@@ -721,8 +771,13 @@ dg_status sdirk_step(dg_mesh_t m, const dg_sdirk_cfg* cfg, double* u_n, double t
     }
     // E^i = dt R(u^i) from the residual of the converged iterate
     DG_TRY(axpby(Ev[i], dt, R, 0.0, n, s));
+    // the converged stage trains the stage's network (needs a full history)
+    // (and its increment becomes the extrapolation base of the next step)
+    if (G && conv)
+      DG_TRY(dg_guess_train(G, i, Sv, U, cfg->guess_train_iters, nullptr, nullptr, nullptr, s));
   }
   for (int i = 0; i < M; ++i) DG_TRY(axpby(u_n, b[i], Ev[i], 1.0, n, s));
+  if (G) DG_TRY(dg_guess_push(G, u_n, s));
   DG_CUDA(cudaStreamSynchronize(s));
   if (stats) *stats = st;
   return result;

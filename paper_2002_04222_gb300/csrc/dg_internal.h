@@ -44,11 +44,19 @@ struct ElemGeo {
 
 struct dg_precond_s;
 
+namespace dg {
+// launch shape of the sum-factorisation kernels (elements and threads per CTA)
+struct Tune {
+  int vol_epb, vol_threads, lift_epb, lift_threads;
+};
+}  // namespace dg
+
 struct dg_mesh_s {
   int dim, P, Q, E, nv, nm, nq, nf, F;
   long long ndof;
   dg::Tables tab;
   dg::Phys phys;
+  dg::Tune tune;
   // device buffers
   dg::ElemGeo* geo = nullptr;   // [E]
   int32_t* faces = nullptr;     // [F][6]
@@ -97,6 +105,7 @@ enum KernelId {
 };
 int prof_begin(int id, cudaStream_t s);
 void prof_end(int handle, cudaStream_t s);
+bool profiling_on();
 #define DG_PROF(id, stream, ...)                    \
   do {                                              \
     const int _ph = ::dg::prof_begin(id, stream);   \
@@ -119,15 +128,24 @@ struct EvalArgs {
   double alpha, beta;  // JVP combination
   double t;
   double* out;
+  bool skip_vol = false, skip_lift = false;  // autotuning times the kernels separately
 };
 dg_status launch_residual(dg_mesh_s* m, const EvalArgs& a, cudaStream_t s);
 dg_status launch_project(dg_mesh_s* m, int what, double t, double* out, cudaStream_t s);
 bool supported(int dim, int P, int Q);
+void init_tune(dg_mesh_s* m);
+dg_status autotune(dg_mesh_s* m, int reps, dg_tune_result* res, cudaStream_t s);
+bool tune_valid(dg_mesh_s* m, const dg_tune_result* t);
+
+// learned initial guess (dg_learned.cu)
+bool guess_history_empty(const dg_guess_s* g);
+bool guess_history_full(const dg_guess_s* g);
 
 // dense vector kernels (dg_blas.cu)
 constexpr int RED_BLOCKS = 296;   // 2 per SM: fixed, so reductions repeat bitwise
 dg_status dot(const double* a, const double* b, long long n, double* partial, double* out,
               cudaStream_t s);
+dg_status finish_sum(const double* partial, int np, double* out, cudaStream_t s);
 dg_status multi_dot(const double* V, int k, const double* w, long long n, double* partial,
                     double* out, cudaStream_t s);
 dg_status multi_axpy(double* w, const double* V, int k, const double* h, long long n,

@@ -1098,14 +1098,14 @@ static dg_status diag_launch(const void* blocks, int E, int nb, int ld, const do
   return DG_OK;
 }
 
-static dg_status diag_apply(dg_precond_s* pc, const double* y, const double* qprev, double* out,
-                            cudaStream_t s) {
+static dg_status diag_apply(dg_precond_s* pc, double omega, const double* y, const double* qprev,
+                            double* out, cudaStream_t s) {
   const int E = pc->mesh->E, nb = pc->nb, ld = round_up8(nb);
   if (pc->precision == DG_PREC_FP64)
-    return diag_launch<double>(pc->blocks, E, nb, ld, y, qprev, pc->omega, out, s);
+    return diag_launch<double>(pc->blocks, E, nb, ld, y, qprev, omega, out, s);
   if (pc->precision == DG_PREC_FP32)
-    return diag_launch<float>(pc->blocks, E, nb, ld, y, qprev, pc->omega, out, s);
-  return diag_launch<__nv_bfloat16>(pc->blocks, E, nb, ld, y, qprev, pc->omega, out, s);
+    return diag_launch<float>(pc->blocks, E, nb, ld, y, qprev, omega, out, s);
+  return diag_launch<__nv_bfloat16>(pc->blocks, E, nb, ld, y, qprev, omega, out, s);
 }
 
 #define DG_PREC_INSTANCES(X)                                                                  \
@@ -1139,28 +1139,78 @@ static dg_status dispatch_offdiag(dg_precond_s* pc, const double* qh, const doub
   return DG_ERR_UNSUPPORTED;
 }
 
-dg_status precond_apply_impl(dg_precond_s* pc, const double* q, double* out, cudaStream_t s) {
+// the J sweeps of Eq. precond-Jacobi as kernel launches on stream s
+static dg_status precond_sweeps(dg_precond_s* pc, const double* q, double* out, cudaStream_t s) {
   // sweep 1 from qh = 0: D^-1 q (the relaxation term vanishes)
   double* cur = pc->J == 1 ? out : pc->qh;
-  {
-    const double om = pc->omega;
-    const int E = pc->mesh->E, nb = pc->nb, ld = round_up8(nb);
-    (void)E;
-    (void)ld;
-    (void)nb;
-    dg_precond_s tmp = *pc;
-    tmp.omega = 1.0;
-    DG_TRY(diag_apply(&tmp, q, nullptr, cur, s));
-    if (om != 1.0) DG_TRY(axpby(cur, 0.0, cur, om, pc->mesh->ndof, s));
-  }
+  DG_TRY(diag_apply(pc, 1.0, q, nullptr, cur, s));
+  if (pc->omega != 1.0) DG_TRY(axpby(cur, 0.0, cur, pc->omega, pc->mesh->ndof, s));
   for (int j = 1; j < pc->J; ++j) {
     DG_TRY(dispatch_offdiag(pc, cur, q, pc->y, s));
     double* nxt = j == pc->J - 1 ? out : pc->qh;
     if (nxt != cur && pc->omega != 1.0)
       DG_CUDA(cudaMemcpyAsync(nxt, cur, sizeof(double) * pc->mesh->ndof, cudaMemcpyDeviceToDevice, s));
-    DG_TRY(diag_apply(pc, pc->y, nxt, nxt, s));
+    DG_TRY(diag_apply(pc, pc->omega, pc->y, nxt, nxt, s));
     cur = nxt;
   }
+  return DG_OK;
+}
+
+static constexpr size_t kMaxGraphs = 128;
+
+void precond_drop_graphs(dg_precond_s* pc) {
+  for (auto& g : pc->graphs) cudaGraphExecDestroy(g.exec);
+  pc->graphs.clear();
+}
+
+// With graphs enabled, the sweeps for each (q, out) pair are captured once on
+// the handle's own stream and replayed as one graph launch, fenced to the
+// caller's stream with events (the captured kernels see fixed pointers, so
+// the Krylov slots of GMRES each get one graph, reused for the handle's life;
+// a rebuild drops them).  Per-kernel profiling bypasses the graphs.
+dg_status precond_apply_impl(dg_precond_s* pc, const double* q, double* out, cudaStream_t s) {
+  if (!pc->use_graphs || profiling_on()) return precond_sweeps(pc, q, out, s);
+  if (!pc->cs) {
+    DG_CUDA(cudaStreamCreateWithFlags(&pc->cs, cudaStreamNonBlocking));
+    DG_CUDA(cudaEventCreateWithFlags(&pc->ev_in, cudaEventDisableTiming));
+    DG_CUDA(cudaEventCreateWithFlags(&pc->ev_out, cudaEventDisableTiming));
+  }
+  cudaGraphExec_t exec = nullptr;
+  long long kernels = 0;
+  for (auto& g : pc->graphs)
+    if (g.q == q && g.out == out) {
+      exec = g.exec;
+      kernels = g.kernels;
+    }
+  if (!exec) {
+    cudaGraph_t graph = nullptr;
+    const long long before = dg_kernel_launches();
+    DG_CUDA(cudaStreamBeginCapture(pc->cs, cudaStreamCaptureModeThreadLocal));
+    const dg_status st = precond_sweeps(pc, q, out, pc->cs);
+    kernels = dg_kernel_launches() - before;
+    const cudaError_t ce = cudaStreamEndCapture(pc->cs, &graph);
+    if (st != DG_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return st;
+    }
+    DG_CUDA(ce);
+    const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    DG_CUDA(ie);
+    if (pc->graphs.size() >= kMaxGraphs) {  // callers cycling through many buffers
+      cudaGraphExecDestroy(pc->graphs.front().exec);
+      pc->graphs.erase(pc->graphs.begin());
+    }
+    pc->graphs.push_back({q, out, exec, kernels});
+  }
+  // the capture counted the graph's kernels once; each replay launches them again
+  else
+    __atomic_fetch_add(&g_launches, kernels, __ATOMIC_RELAXED);
+  DG_CUDA(cudaEventRecord(pc->ev_in, s));
+  DG_CUDA(cudaStreamWaitEvent(pc->cs, pc->ev_in, 0));
+  DG_CUDA(cudaGraphLaunch(exec, pc->cs));
+  DG_CUDA(cudaEventRecord(pc->ev_out, pc->cs));
+  DG_CUDA(cudaStreamWaitEvent(s, pc->ev_out, 0));
   return DG_OK;
 }
 
@@ -1178,6 +1228,10 @@ static void free_precond(dg_precond_s* p) {
   cudaFree(p->qh);
   cudaFree(p->y);
   cudaFree(p->work);
+  precond_drop_graphs(p);
+  if (p->cs) cudaStreamDestroy(p->cs);
+  if (p->ev_in) cudaEventDestroy(p->ev_in);
+  if (p->ev_out) cudaEventDestroy(p->ev_out);
   delete p;
 }
 
@@ -1256,6 +1310,9 @@ dg_status dg_precond_build(dg_mesh_t m, const double* u, double t, double dt_a,
     }
     *inout = p;
   }
+  // the captured sweeps hold J, omega and the launch shapes: a rebuild re-captures
+  precond_drop_graphs(p);
+  p->use_graphs = cfg->graphs;
   p->J = cfg->J;
   p->omega = cfg->omega;
   p->dt_a = dt_a;

@@ -19,9 +19,21 @@ struct dg_precond_s {
   void* work = nullptr;   // build workspace
   size_t work_bytes = 0;
   int wchunk = 1;          // elements per pass of the weights workspace
+  // graph replay of the apply (one instantiated graph per (q, out) pair)
+  struct Graph {
+    const double* q;
+    double* out;
+    cudaGraphExec_t exec;
+    long long kernels;     // kernel launches the graph holds
+  };
+  int use_graphs = 0;
+  std::vector<Graph> graphs;
+  cudaStream_t cs = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
 };
 
 namespace dg {
 dg_status precond_apply_impl(dg_precond_s* p, const double* q, double* out, cudaStream_t s);
+void precond_drop_graphs(dg_precond_s* p);
 inline dg_mesh_s* precond_mesh(dg_precond_s* p) { return p->mesh; }
 }  // namespace dg

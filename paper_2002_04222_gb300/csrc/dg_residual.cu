@@ -13,6 +13,7 @@
 // FP64 throughout: on GB300 this path is bound by the FP64 pipe, so every
 // stage is written to issue as few FP64 instructions as possible.
 #include <cstdio>
+#include <vector>
 #include "dg_internal.h"
 #include "dg_physics.cuh"
 #include "dg_sumfact.cuh"
@@ -28,9 +29,9 @@ __global__ void __launch_bounds__(256) vol_kernel(const __grid_constant__ Tables
                                                   const double* __restrict__ v,
                                                   const double* __restrict__ epsp,
                                                   double* __restrict__ hbuf,
-                                                  double* __restrict__ tbuf) {
+                                                  double* __restrict__ tbuf, const int EPB) {
   using C = Cfg<DIM, P, Q>;
-  constexpr int N = C::N, NV = C::NV, NM = C::NM, NQ = C::NQ, NF = C::NF, EPB = C::EPB;
+  constexpr int N = C::N, NV = C::NV, NM = C::NM, NQ = C::NQ, NF = C::NF;
   constexpr int Q2 = C::Q2, N2 = C::N2;
   extern __shared__ double sm[];
   double* sB = sm;
@@ -284,9 +285,10 @@ __global__ void __launch_bounds__(256) lift_kernel(const __grid_constant__ Table
                                                    const double* __restrict__ v,
                                                    const double* __restrict__ r_u,
                                                    const double* __restrict__ epsp, double alpha,
-                                                   double beta, double* __restrict__ out) {
+                                                   double beta, double* __restrict__ out,
+                                                   const int EPB) {
   using C = Cfg<DIM, P, Q>;
-  constexpr int N = C::N, NV = C::NV, NM = C::NM, NQ = C::NQ, NF = C::NF, EPB = C::EPB;
+  constexpr int N = C::N, NV = C::NV, NM = C::NM, NQ = C::NQ, NF = C::NF;
   constexpr int Q2 = C::Q2;
   constexpr int NTR = 2 * DIM * (1 + DIM) * NV * NF;
   extern __shared__ double sm[];
@@ -428,23 +430,53 @@ __global__ void __launch_bounds__(256) project_kernel(const __grid_constant__ Ta
 template <int DIM, int P, int Q>
 static dg_status run_residual(dg_mesh_s* m, const EvalArgs& a, cudaStream_t s) {
   using C = Cfg<DIM, P, Q>;
-  const int nb = (m->E + C::EPB - 1) / C::EPB;
-  const size_t vsm = sizeof(double) * C::VOL_SM, lsm = sizeof(double) * C::LIFT_SM;
+  const int vepb = m->tune.vol_epb, vnt = m->tune.vol_threads;
+  const int lepb = m->tune.lift_epb, lnt = m->tune.lift_threads;
+  const size_t vsm = sizeof(double) * C::vol_sm(vepb), lsm = sizeof(double) * C::lift_sm(lepb);
   DG_CUDA(cudaFuncSetAttribute(vol_kernel<DIM, P, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)vsm));
   DG_CUDA(cudaFuncSetAttribute(lift_kernel<DIM, P, Q>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm));
-  DG_PROF(K_VOL, s, vol_kernel<DIM, P, Q><<<nb, C::NT, vsm, s>>>(m->tab, m->phys, m->geo, m->E, a.u, a.v, a.eps,
-                                               m->hbuf, m->tbuf));
-  DG_LAUNCHED(1);
-  const int nfp = m->F * C::NF;
-  DG_PROF(K_FACE, s, face_kernel<DIM, P, Q><<<(nfp + 127) / 128, 128, 0, s>>>(m->tab, m->phys, m->geo, m->faces,
-                                                           m->F, a.t, m->tbuf, m->fbuf));
-  DG_LAUNCHED(1);
-  DG_PROF(K_LIFT, s, lift_kernel<DIM, P, Q><<<nb, C::NT, lsm, s>>>(m->tab, m->geo, m->E, m->hbuf, m->fbuf, m->force,
-                                                a.v, a.r_u, a.eps, a.alpha, a.beta, a.out));
-  DG_LAUNCHED(1);
+  if (!a.skip_vol) {
+    DG_PROF(K_VOL, s, vol_kernel<DIM, P, Q><<<(m->E + vepb - 1) / vepb, vnt, vsm, s>>>(
+        m->tab, m->phys, m->geo, m->E, a.u, a.v, a.eps, m->hbuf, m->tbuf, vepb));
+    DG_LAUNCHED(1);
+    const int nfp = m->F * C::NF;
+    DG_PROF(K_FACE, s, face_kernel<DIM, P, Q><<<(nfp + 127) / 128, 128, 0, s>>>(
+        m->tab, m->phys, m->geo, m->faces, m->F, a.t, m->tbuf, m->fbuf));
+    DG_LAUNCHED(1);
+  }
+  if (!a.skip_lift) {
+    DG_PROF(K_LIFT, s, lift_kernel<DIM, P, Q><<<(m->E + lepb - 1) / lepb, lnt, lsm, s>>>(
+        m->tab, m->geo, m->E, m->hbuf, m->fbuf, m->force, a.v, a.r_u, a.eps, a.alpha, a.beta, a.out,
+        lepb));
+    DG_LAUNCHED(1);
+  }
   return DG_OK;
+}
+
+template <int DIM, int P, int Q>
+static void default_tune(dg_mesh_s* m) {
+  using C = Cfg<DIM, P, Q>;
+  m->tune.vol_epb = m->tune.lift_epb = C::EPB;
+  m->tune.vol_threads = m->tune.lift_threads = C::NT;
+}
+
+// candidate (elements per CTA, threads per CTA) launch shapes of the
+// sum-factorisation kernels that fit the shared memory of one CTA
+template <int DIM, int P, int Q>
+static void tune_candidates(std::vector<int2>& vol, std::vector<int2>& lift) {
+  using C = Cfg<DIM, P, Q>;
+  const int epbs3[] = {1, 2, 3, 4};
+  const int epbs2[] = {1, 2, 4, 8, 16, 32};
+  const int nts[] = {64, 128, 192, 256};
+  const size_t cap = 200 * 1024;
+  for (int e : (DIM == 3 ? std::vector<int>(epbs3, epbs3 + 4) : std::vector<int>(epbs2, epbs2 + 6)))
+    for (int t : nts) {
+      if (DIM == 3 && t < 128) continue;
+      if (sizeof(double) * C::vol_sm(e) <= cap) vol.push_back(make_int2(e, t));
+      if (sizeof(double) * C::lift_sm(e) <= cap) lift.push_back(make_int2(e, t));
+    }
 }
 
 template <int DIM, int P, int Q>
@@ -486,6 +518,107 @@ dg_status launch_project(dg_mesh_s* m, int what, double t, double* out, cudaStre
   DG_INSTANCES(DG_RUN)
 #undef DG_RUN
   return DG_ERR_UNSUPPORTED;
+}
+
+template <int DIM, int P, int Q>
+static dg_status run_autotune(dg_mesh_s* m, int reps, dg_tune_result* res, cudaStream_t s) {
+  std::vector<int2> vc, lc;
+  tune_candidates<DIM, P, Q>(vc, lc);
+  // a valid state to time on: the projected analytic field
+  DG_TRY(launch_project(m, 0, 0.0, m->w1, s));
+  EvalArgs a{};
+  a.u = m->w1;
+  a.out = m->w2;
+  cudaEvent_t e0, e1;
+  DG_CUDA(cudaEventCreate(&e0));
+  DG_CUDA(cudaEventCreate(&e1));
+  const Tune keep = m->tune;
+  auto time_it = [&](bool vol) -> double {
+    EvalArgs b = a;
+    b.skip_vol = !vol;
+    b.skip_lift = vol;
+    run_residual<DIM, P, Q>(m, b, s);  // warm-up
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < reps; ++r) run_residual<DIM, P, Q>(m, b, s);
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    return ms / reps;
+  };
+  // volume + face kernels (the face kernel's launch is fixed and adds the same time to each)
+  double best = 1e30, dflt = 0.0;
+  Tune t = keep;
+  for (const int2& c : vc) {
+    m->tune.vol_epb = c.x;
+    m->tune.vol_threads = c.y;
+    const double ms = time_it(true);
+    if (c.x == keep.vol_epb && c.y == keep.vol_threads) dflt = ms;
+    if (ms < best) {
+      best = ms;
+      t.vol_epb = c.x;
+      t.vol_threads = c.y;
+    }
+  }
+  res->vol_ms = best;
+  res->vol_ms_default = dflt;
+  m->tune.vol_epb = t.vol_epb;
+  m->tune.vol_threads = t.vol_threads;
+  run_residual<DIM, P, Q>(m, a, s);  // traces and fluxes for the lift timing
+  best = 1e30;
+  for (const int2& c : lc) {
+    m->tune.lift_epb = c.x;
+    m->tune.lift_threads = c.y;
+    const double ms = time_it(false);
+    if (c.x == keep.lift_epb && c.y == keep.lift_threads) dflt = ms;
+    if (ms < best) {
+      best = ms;
+      t.lift_epb = c.x;
+      t.lift_threads = c.y;
+    }
+  }
+  res->lift_ms = best;
+  res->lift_ms_default = dflt;
+  m->tune = t;
+  res->vol_epb = t.vol_epb;
+  res->vol_threads = t.vol_threads;
+  res->lift_epb = t.lift_epb;
+  res->lift_threads = t.lift_threads;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  DG_CUDA(cudaGetLastError());
+  return DG_OK;
+}
+
+void init_tune(dg_mesh_s* m) {
+#define DG_RUN(D_, P_, Q_) \
+  if (m->dim == D_ && m->P == P_ && m->Q == Q_) default_tune<D_, P_, Q_>(m);
+  DG_INSTANCES(DG_RUN)
+#undef DG_RUN
+}
+
+dg_status autotune(dg_mesh_s* m, int reps, dg_tune_result* res, cudaStream_t s) {
+#define DG_RUN(D_, P_, Q_) \
+  if (m->dim == D_ && m->P == P_ && m->Q == Q_) return run_autotune<D_, P_, Q_>(m, reps, res, s);
+  DG_INSTANCES(DG_RUN)
+#undef DG_RUN
+  return DG_ERR_UNSUPPORTED;
+}
+
+bool tune_valid(dg_mesh_s* m, const dg_tune_result* t) {
+  bool ok = false;
+#define DG_RUN(D_, P_, Q_)                                                            \
+  if (m->dim == D_ && m->P == P_ && m->Q == Q_) {                                     \
+    std::vector<int2> vc, lc;                                                         \
+    tune_candidates<D_, P_, Q_>(vc, lc);                                              \
+    bool v = false, l = false;                                                        \
+    for (const int2& c : vc) v |= c.x == t->vol_epb && c.y == t->vol_threads;         \
+    for (const int2& c : lc) l |= c.x == t->lift_epb && c.y == t->lift_threads;       \
+    ok = v && l;                                                                      \
+  }
+  DG_INSTANCES(DG_RUN)
+#undef DG_RUN
+  return ok;
 }
 
 }  // namespace dg

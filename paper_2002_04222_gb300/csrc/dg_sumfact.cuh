@@ -23,6 +23,11 @@ struct Cfg {
   // shared memory (doubles) per block
   static constexpr int VOL_SM = TAB + EPB * (NV * NM + (1 + DIM) * NV * NQ + (DIM == 2 ? NV * NQ : 0));
   static constexpr int LIFT_SM = TAB + EPB * ((DIM + 1) * NV * NQ + 2 * NV * NQ);
+  // shared memory (doubles) for a runtime number of elements per block
+  static constexpr int vol_sm(int e) {
+    return TAB + e * (NV * NM + (1 + DIM) * NV * NQ + (DIM == 2 ? NV * NQ : 0));
+  }
+  static constexpr int lift_sm(int e) { return TAB + e * ((DIM + 1) * NV * NQ + 2 * NV * NQ); }
 };
 
 // Y[r][o] = sum_k M[o_ax*MS0 + k*MS1] X[r][i(o, k)] for every replica r

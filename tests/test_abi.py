@@ -49,7 +49,8 @@ def test_struct_layouts_match_header():
                "dg_mesh_info_t": _lib.MeshInfo, "dg_prec_cfg": _lib.PrecCfg,
                "dg_gmres_cfg": _lib.GmresCfg, "dg_gmres_stats": _lib.GmresStats,
                "dg_sdirk_cfg": _lib.SdirkCfg, "dg_step_stats": _lib.StepStats,
-               "dg_kernel_time": _lib.KernelTime}
+               "dg_kernel_time": _lib.KernelTime, "dg_guess_cfg": _lib.GuessCfg,
+               "dg_tune_result": _lib.TuneResult}
     lines = ["#include <stdio.h>", "#include <stddef.h>", f'#include "{HEADER}"', "int main(void){"]
     for cname, cls in structs.items():
         lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')

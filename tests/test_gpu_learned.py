@@ -1,0 +1,110 @@
+"""The learned Newton initial guess on the GPU: loss and gradients of the
+BF16/FP32 MLP kernels against the FP64 oracle MLP (same BF16 rounding
+points), training reduces the loss, and inside SDIRK the guess (previous
+stage increment + learned correction) cuts Newton iterations at the plain
+method's tolerance alpha ||N(S_m)|| while reaching the same solution."""
+import numpy as np
+import pytest
+import torch
+
+import workloads as w
+from oracle import learned as ol
+from oracle.dg import DG
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dgl():
+    import paper_2002_04222_gb300 as dgl
+    return dgl
+
+
+def fields(shape, seed, n=6):
+    rng = np.random.default_rng(seed)
+    base = 1.0 + 0.1 * rng.standard_normal(shape)
+    return [base + 0.01 * (k + 1) * rng.standard_normal(shape) for k in range(n)]
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def test_guess_loss_and_gradients_match_oracle(dgl):
+    c = w.small_tgv_case((3, 2, 2), P=1)
+    m = dgl.Mesh.from_case(c)
+    E, nv, nm = m.shape
+    nb = nv * nm
+    hidden = 32
+    params = w.mlp_params(3 * nb, hidden, nb, seed=3) + w.mlp_params(3 * nb, hidden, nb, seed=4)
+    g = dgl.Guess(m, params, stages=2, hidden=hidden)
+    h1, h0, S, u1, u = fields((E, nv, nm), 5, 5)
+    g.push(dev(h1))
+    g.push(dev(h0))
+    g.train(1, dev(S), dev(u1), iters=0)          # sets d_prev = u1 - S (no history of it yet)
+    l0, _, grads = g.train(1, dev(S), dev(u), iters=0, grads=True)
+    dprev = u1 - S
+    x = ol.features([h0, h1], dprev, nv)
+    rem = (u - S - dprev).reshape(E, -1)
+    tau = ol.var_rms(rem, nv)
+    T = (rem.reshape(E, nv, nm) / tau[None, :, None]).reshape(E, -1)
+    L, ref = ol.MLP(params[6:12]).loss_and_grads(x, T)
+    assert abs(l0 - L) < 1e-3 * L, (l0, L)
+    for a, b in zip(grads, ref):
+        assert np.linalg.norm(a - b) < 2e-2 * np.linalg.norm(b), (np.linalg.norm(a - b), np.linalg.norm(b))
+
+
+def test_guess_training_reduces_loss(dgl):
+    c = w.small_tgv_case((3, 2, 2), P=2)
+    m = dgl.Mesh.from_case(c)
+    E, nv, nm = m.shape
+    nb = nv * nm
+    params = w.mlp_params(3 * nb, 64, nb, seed=7) * 2
+    g = dgl.Guess(m, params, stages=2, hidden=64, lr=3e-3)
+    h1, h0, S, u1 = fields((E, nv, nm), 6, 4)
+    g.push(dev(h1))
+    g.push(dev(h0))
+    g.train(0, dev(S), dev(u1), iters=0)
+    dprev = u1 - S
+    u = S + dprev + 0.5 * (h0 - h1)                # a remainder the features express
+    l0, l1, _ = g.train(0, dev(S), dev(u), iters=200)
+    assert l1 < 0.1 * l0, (l0, l1)
+
+
+def test_learned_guess_cuts_newton_iterations(dgl):
+    """Vortex 8x8 P=2, SDIRK2 dt = 0.02: starting from the previous step's stage
+    increment (with or without the learned correction) needs fewer Newton
+    iterations than S_m at the same tolerance alpha ||N(S_m)||, and all three
+    forms reach the same solution to that tolerance."""
+    c = w.vortex_case(n=8, P=2)
+    dg = DG(c.mesh, c.P, c.Q, c.phys)
+    u0 = dev(dg.project_exact())
+    m = dgl.Mesh.from_case(c)
+    E, nv, nm = m.shape
+    nb = nv * nm
+    dt, nsteps, last = 0.02, 12, 6
+    params = (w.mlp_params(3 * nb, 64, nb, seed=11, zero_last=True)
+              + w.mlp_params(3 * nb, 64, nb, seed=12, zero_last=True))
+    runs = {}
+    for mode in ("plain", "extrapolated", "learned"):
+        u = u0.clone()
+        pc = dgl.Precond(m)
+        guess = None
+        if mode == "extrapolated":
+            guess = dgl.Guess(m, None, stages=2)
+        elif mode == "learned":
+            guess = dgl.Guess(m, params, stages=2, hidden=64, lr=1e-3)
+        its, used = [], 0
+        for k in range(nsteps):
+            st = m.sdirk_step(u, k * dt, dt, precond=pc, rebuild=(k % 10 == 0), restart=20, J=7,
+                              guess=guess, guess_train_iters=10)
+            assert st["converged"]
+            its.append(st["newton_iters"])
+            used += st["guess_used"]
+        runs[mode] = (u.cpu().numpy(), its, used)
+    up, itp, _ = runs["plain"]
+    for mode in ("extrapolated", "learned"):
+        ul, itl, used = runs[mode]
+        assert used > 0, mode
+        assert sum(itl[-last:]) < sum(itp[-last:]), (mode, itp, itl)
+        assert np.linalg.norm(ul - up) / np.linalg.norm(up) < 1e-3, mode
