@@ -76,8 +76,24 @@ enum { DG_FORCING_NONE = 0, DG_FORCING_POISEUILLE = 1 };
  * (mu_law 0) or Sutherland's law with T_inf_K kelvin (mu_law 1), heat flux
  * -mu/(Ma^2 Pr (gamma-1)) grad T.  viscous = 0 gives the Euler equations.
  * field / fpar select the analytic field used by dg_project, by Dirichlet
- * boundaries and by the wall temperature (vortex: u0, v0, phi, xc, yc,
- * scale; Poiseuille: theta, L, dp/dx).  bc[i] is the type of boundary i. */
+ * and far-field boundaries and by the wall temperature (vortex: u0, v0, phi,
+ * xc, yc, scale; Poiseuille: theta, L, dp/dx; uniform: rho, u, v, w, T, or
+ * the stream (1, 1, 0, 0, 1) when fpar[0] = 0; cylinder: that stream).
+ * bc[i] is the type of boundary i:
+ *   DG_BC_DIRICHLET  exterior and viscous state = the analytic field
+ *   DG_BC_ISO_WALL   no-slip wall at the analytic wall temperature
+ *   DG_BC_ADIA_WALL  no-slip adiabatic wall: Riemann flux against the
+ *                    interior state with reversed normal momentum, viscous
+ *                    state (rho_L, 0, p_L/(gamma-1)), zero energy component
+ *                    of the viscous normal flux and of S_j
+ *   DG_BC_FARFIELD   characteristic state from the Riemann invariants
+ *                    u_n +- 2c/(gamma-1) (outgoing from the interior,
+ *                    incoming from the analytic field), entropy and
+ *                    tangential velocity from the upwind side
+ * (Sec. 4.3 lists the adiabatic no-slip wall and the Riemann-invariant far
+ * field without formulas, Sec. 6.4 applies the latter on the outer boundary
+ * of the cylinder; these are the textbook one-dimensional characteristic and
+ * reflection forms.) */
 typedef struct {
   double gamma, Pr, Ma, Re, T_inf_K, beta_s;
   int viscous, mu_law, riemann, forcing, field;

@@ -122,20 +122,25 @@ class DG:
             QR = self.values(u, self.Bf[g["fR"]], g["eR"])
             dQR = self.gradients(u, self.Df[g["fR"]], g["ginvR"], g["eR"])
             return QL, QR, 0.5 * (QL + QR), 0.5 * (dQL + dQR), dQL, dQR
-        QB = phy.boundary_state(self.ph, g["bctype"], g["x"], t, QL, g["n"])
-        return QL, QB, QB, dQL, dQL, None
+        Qr, Qb, _ = phy.boundary_states(self.ph, g["bctype"], g["x"], t, QL, g["n"])
+        return QL, Qr, Qb, dQL, dQL, None
 
-    def face_flux(self, g, QL, QR, Qa, dQa, t, QLfixed_bc=True):
+    def face_flux(self, g, QL, QR, Qa, dQa, t):
         """Numerical normal flux H^n = F^n - G^n and symmetric fluxes S_j on the
-        face points of group g (owner-side normal)."""
+        face points of group g (owner-side normal).  QR is the exterior state
+        of the Riemann flux and Qa the state of the viscous flux; the jump is
+        Q_L - Q_R on interior faces and Q_L - Q_b on boundary faces."""
         n = g["n"]
         Fh = phy.riemann_flux(QL, QR, n, self.ph)
         if not self.ph.viscous:
             return Fh, None
-        jump = QL - QR
+        jump = QL - (QR if g["bctype"] is None else Qa)
         S = phy.viscous_flux(Qa, n[..., :, None] * jump[..., None, :], self.ph)   # [f][p][i][v]
         Gv = phy.viscous_flux(Qa, dQa, self.ph) - g["beta"][:, None, None, None] * S
         Gh = np.einsum("fpi,fpiv->fpv", n, Gv)
+        if g["bctype"] == phy.BC_ADIA_WALL:
+            Gh[..., -1] = 0.0
+            S[..., -1] = 0.0
         return Fh - Gh, S
 
     def lift_S(self, S, wJ, Dmat, ginv):

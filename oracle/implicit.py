@@ -215,8 +215,7 @@ class BRJ:
         if g["bctype"] is None:
             Qa = 0.5 * (QL + QR)
         else:
-            QR = phy.boundary_state(dg.ph, g["bctype"], g["x"], t, QL, g["n"])
-            Qa = QR
+            QR, Qa, _ = phy.boundary_states(dg.ph, g["bctype"], g["x"], t, QL, g["n"])
         Hh, _ = dg.face_flux(g, QL, QR, Qa, dQa, t)
         return Hh
 

@@ -172,6 +172,10 @@ def exact_state(ph, x, t):
         vel = np.zeros(shp + (d,))
         vel[..., 0] = 1.0
         T = np.ones(shp)
+        if ph.fid == FIELD_UNIFORM and len(ph.fpar) >= 5 and ph.fpar[0] > 0:
+            rho = rho * ph.fpar[0]
+            vel = np.broadcast_to(np.asarray(ph.fpar[1:1 + d], float), shp + (d,)).copy()
+            T = T * ph.fpar[4]
     elif ph.fid == FIELD_VORTEX:
         # isentropic vortex (Sec. 6.1) on [0,1]^2 = [0,10]^2 scaled by 1/s, with the
         # sign of the u perturbation that makes it a vortex, and T from the radial
@@ -238,18 +242,71 @@ def wall_temperature(ph, x):
     return np.ones(x.shape[:-1])
 
 
-def boundary_state(ph, bctype, x, t, UL, n):
-    """Weakly imposed boundary state U_b used as the exterior state of the
-    Riemann flux and as the state of the viscous boundary flux."""
+def farfield_state(ph, UL, Uinf, n):
+    """Characteristic far-field state (Sec. 4.3 lists a Riemann-invariant
+    condition, used on the outer boundary of the cylinder of Sec. 6.4, without
+    its formulas; this is the textbook one-dimensional reading along the
+    outward normal n).  With c the speed of sound, the outgoing invariant
+    R+ = u_n + 2c/(gamma-1) is taken from the interior state UL and the
+    incoming R- = u_n - 2c/(gamma-1) from the free stream Uinf; their half sum
+    and quarter difference give u_n and c on the boundary.  Entropy p/rho^gamma
+    and the tangential velocity come from the upwind side (interior where the
+    boundary normal velocity leaves the domain).  Supersonic normal flow
+    (|u_n| >= c in the interior) takes the whole state from the upwind side."""
+    g = ph.gamma
+    rho, vel, p, _ = primitives(UL, ph)
+    ri, vi, pi, _ = primitives(Uinf, ph)
+    c = np.sqrt(g * p / rho)
+    ci = np.sqrt(g * pi / ri)
+    un = np.sum(vel * n, axis=-1)
+    uni = np.sum(vi * n, axis=-1)
+    Rp = un + 2.0 * c / (g - 1.0)
+    Rm = uni - 2.0 * ci / (g - 1.0)
+    unb = 0.5 * (Rp + Rm)
+    cb = 0.25 * (g - 1.0) * (Rp - Rm)
+    out = (unb > 0.0)[..., None]
+    s_up = np.where(unb > 0.0, p / rho ** g, pi / ri ** g)
+    v_up = np.where(out, vel, vi)
+    vt = v_up - np.sum(v_up * n, axis=-1)[..., None] * n
+    rb = (cb * cb / (g * s_up)) ** (1.0 / (g - 1.0))
+    pb = rb * cb * cb / g
+    Ub = conservative(rb, vt + unb[..., None] * n, pb, ph)
+    Ub = np.where((un >= c)[..., None], UL, Ub)
+    Ub = np.where((un <= -c)[..., None], Uinf, Ub)
+    return Ub
+
+
+def boundary_states(ph, bctype, x, t, UL, n):
+    """Weakly imposed boundary data on the face points of a physical boundary:
+    (U_r, U_b, adiabatic).  U_r is the exterior state of the Riemann flux, U_b
+    the state of the viscous flux and of the interior-penalty jump Q_L - U_b
+    (the interior gradient is used on the boundary).  On an adiabatic wall the
+    energy components of the viscous normal flux G^n and of S_j vanish (zero
+    heat flux through the wall; the wall state has zero velocity, so the
+    viscous work is zero too).
+      Dirichlet:      U_r = U_b = the workload's analytic state
+      isothermal wall U_r = U_b = (rho_L, 0, rho_L T_w / (gamma (gamma-1) Ma^2))
+      adiabatic wall  U_r = interior state with the normal momentum reversed,
+                      U_b = (rho_L, 0, p_L / (gamma-1))  (wall temperature = T_L)
+      far field       U_r = U_b = farfield_state(UL, analytic state)"""
     g, Ma = ph.gamma, ph.Ma
-    d = x.shape[-1]
     if bctype == BC_DIRICHLET:
-        return exact_state(ph, x, t)
+        Ue = exact_state(ph, x, t)
+        return Ue, Ue, False
     if bctype == BC_ISO_WALL:
         Tw = wall_temperature(ph, x)
         rho = UL[..., 0]
         Ub = np.zeros_like(UL)
         Ub[..., 0] = rho
         Ub[..., -1] = rho * Tw / (g * (g - 1.0) * Ma ** 2)
-        return Ub
+        return Ub, Ub, False
+    if bctype == BC_ADIA_WALL:
+        rho, vel, p, _ = primitives(UL, ph)
+        vm = vel - 2.0 * np.sum(vel * n, axis=-1)[..., None] * n
+        Ur = conservative(rho, vm, p, ph)
+        Ub = conservative(rho, np.zeros_like(vel), p, ph)
+        return Ur, Ub, True
+    if bctype == BC_FARFIELD:
+        Ub = farfield_state(ph, UL, exact_state(ph, x, t), n)
+        return Ub, Ub, False
     raise NotImplementedError(f"boundary type {bctype}")

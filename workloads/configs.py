@@ -6,7 +6,7 @@ forcing) are implemented separately by the oracle and by the CUDA library.
 """
 from dataclasses import dataclass, field as dc_field
 import numpy as np
-from .mesh import box_mesh, clustered_spacing, ogrid_mesh
+from .mesh import box_mesh, clustered_spacing, mapped_box_mesh, ogrid_mesh
 
 # boundary-condition types (entry of the per-boundary table)
 BC_PERIODIC = 0      # never in the table: periodic faces are interior faces
@@ -21,6 +21,8 @@ FIELD_VORTEX = 1
 FIELD_POISEUILLE = 2
 FIELD_TGV = 3
 FIELD_CYLINDER = 4   # uniform stream (1, 0, 0) at T = 1, rho = 1
+# FIELD_UNIFORM is the uniform state fpar = (rho, u, v, w, T), or the stream
+# (1, 1, 0, 0, 1) when fpar is empty
 
 RIEMANN_ROE = 0
 RIEMANN_HLLC = 1
@@ -118,3 +120,59 @@ def cylinder_case(n_r=64, n_theta=96, n_z=12, P=3, Q=None, Re=3900.0, Ma=0.2):
     m = ogrid_mesh(n_r, n_theta, n_z, 0.5, 20.0, 1.08, np.pi)
     ph = Physics(Ma=Ma, Re=Re, fid=FIELD_CYLINDER, bc=[BC_ADIA_WALL, BC_FARFIELD])
     return Case(f"cylinder{n_r}x{n_theta}x{n_z}_P{P}", m, P, Q, ph)
+
+
+def wavy_box_case(shape=(3, 3, 2), P=2, Q=None, amp=0.12, Re=1600.0, Ma=0.1,
+                  riemann=RIEMANN_ROE):
+    """Periodic box [-pi, pi]^3 on quadratic hexes whose nodes are displaced by
+    a smooth periodic field (every element curved, faces conforming), with the
+    Taylor-Green field."""
+    Q = int(np.ceil(3 * (P + 1) / 2)) if Q is None else Q
+    lines = [np.linspace(-np.pi, np.pi, n + 1) for n in shape]
+
+    def wave(X):
+        x, y, z = X[..., 0], X[..., 1], X[..., 2]
+        return np.stack([x + amp * np.sin(y) * np.sin(z),
+                         y + amp * np.sin(z + 0.5) * np.sin(x),
+                         z + amp * np.sin(x) * np.sin(y + 0.3)], -1)
+
+    m = mapped_box_mesh(lines, (True, True, True), wave, order=2)
+    ph = Physics(Ma=Ma, Re=Re, fid=FIELD_TGV, riemann=riemann)
+    return Case(f"wavy{shape}_P{P}", m, P, Q, ph)
+
+
+def rotation_matrix(dim, angles=(0.5, -0.3, 0.8)):
+    """A proper rotation: about z in 2-D; z-y-x Euler angles in 3-D."""
+    a, b, c = angles
+    Rz = np.array([[np.cos(a), -np.sin(a), 0], [np.sin(a), np.cos(a), 0], [0, 0, 1]])
+    if dim == 2:
+        return Rz[:2, :2]
+    Ry = np.array([[np.cos(b), 0, np.sin(b)], [0, 1, 0], [-np.sin(b), 0, np.cos(b)]])
+    Rx = np.array([[1, 0, 0], [0, np.cos(c), -np.sin(c)], [0, np.sin(c), np.cos(c)]])
+    return Rz @ Ry @ Rx
+
+
+def rotated_box_case(shape=(3, 2, 2), P=2, Q=None, order=1, Re=1600.0, Ma=0.1,
+                     riemann=RIEMANN_ROE):
+    """The periodic box of small_tgv_case rigidly rotated (straight-sided
+    elements with non-diagonal metrics; order 2 writes the same elements with
+    27 nodes)."""
+    dim = len(shape)
+    Q = int(np.ceil(3 * (P + 1) / 2)) if Q is None else Q
+    lines = [np.linspace(-np.pi, np.pi, n + 1) for n in shape]
+    R = rotation_matrix(dim)
+    m = mapped_box_mesh(lines, (True,) * dim, lambda X: X @ R.T, order=order)
+    m.meta["rotation"] = R
+    ph = Physics(Ma=Ma, Re=Re, fid=FIELD_TGV if dim == 3 else FIELD_UNIFORM, riemann=riemann)
+    return Case(f"rotated{shape}_P{P}_g{order}", m, P, Q, ph)
+
+
+def small_cylinder_case(n_r=3, n_theta=8, n_z=2, P=2, Q=None, Re=3900.0, Ma=0.2,
+                        r_out=3.0, bc=(BC_ADIA_WALL, BC_FARFIELD)):
+    """A coarse O-grid (radius 0.5 to r_out) with the cylinder workload's
+    boundary conditions, for parity cases."""
+    Q = int(np.ceil(3 * (P + 1) / 2)) if Q is None else Q
+    m = ogrid_mesh(n_r, n_theta, n_z, 0.5, r_out, 1.08, np.pi)
+    ph = Physics(Ma=Ma, Re=Re, fid=FIELD_CYLINDER, bc=list(bc))
+    return Case(f"cylinder{n_r}x{n_theta}x{n_z}_P{P}", m, P, Q, ph)
+

@@ -83,6 +83,31 @@ def box_mesh(lines, periodic, side_bc=None):
     return Mesh(dim, 1, nodes, faces, shape, tuple(periodic))
 
 
+def mapped_box_mesh(lines, periodic, fn, order=2, side_bc=None):
+    """The tensor grid of `lines` with every element's (order+1)^d equispaced
+    reference nodes sent through the point map `fn` (x[..., d] -> x[..., d]).
+    Neighbours evaluate fn at the same points of a shared face, so the faces
+    stay conforming; with a map whose displacement is periodic the periodic
+    faces match too.  order = 1 with a linear fn gives straight-sided
+    (possibly rotated or sheared) elements."""
+    dim = len(lines)
+    shape = tuple(len(l) - 1 for l in lines)
+    if side_bc is None:
+        side_bc = [-1] * (2 * dim)
+    E = int(np.prod(shape))
+    na = (order + 1) ** dim
+    cell = np.stack(np.unravel_index(np.arange(E), shape[::-1])[::-1], -1)      # [E][d] (i, j[, k])
+    a = np.stack(np.unravel_index(np.arange(na), (order + 1,) * dim)[::-1], -1)  # [na][d]
+    X = np.zeros((E, na, dim))
+    for r in range(dim):
+        lo = lines[r][cell[:, r]]
+        hi = lines[r][cell[:, r] + 1]
+        X[:, :, r] = lo[:, None] + (hi - lo)[:, None] * a[None, :, r] / order
+    nodes = fn(X)
+    faces = _faces_structured(shape, periodic, side_bc)
+    return Mesh(dim, order, nodes, faces, shape, tuple(periodic))
+
+
 def ogrid_mesh(n_r, n_theta, n_z, r_in, r_out, ratio, span):
     """Quadratic (27-node) hexes of an O-grid around a cylinder of radius r_in:
     direction 0 = radial (geometric growth `ratio`), 1 = azimuthal (periodic),
@@ -92,16 +117,11 @@ def ogrid_mesh(n_r, n_theta, n_z, r_in, r_out, ratio, span):
     rl = r_in + (r_out - r_in) * np.concatenate([[0.0], np.cumsum(h)]) / h.sum()
     tl = np.linspace(0.0, 2 * np.pi, n_theta + 1)
     zl = np.linspace(0.0, span, n_z + 1)
-    shape = (n_r, n_theta, n_z)
-    E = n_r * n_theta * n_z
-    nodes = np.zeros((E, 27, 3))
-    for e in range(E):
-        i, j, k = np.unravel_index(e, shape[::-1])[::-1]
-        for a in range(27):
-            a0, a1, a2 = a % 3, (a // 3) % 3, a // 9
-            r = rl[i] + 0.5 * a0 * (rl[i + 1] - rl[i])
-            th = tl[j] + 0.5 * a1 * (tl[j + 1] - tl[j])
-            z = zl[k] + 0.5 * a2 * (zl[k + 1] - zl[k])
-            nodes[e, a] = (r * np.cos(th), r * np.sin(th), z)
-    faces = _faces_structured(shape, (False, True, True), [0, 1, -1, -1, -1, -1])
-    return Mesh(3, 2, nodes, faces, shape, (False, True, True))
+
+    def polar(X):
+        r, th, z = X[..., 0], X[..., 1], X[..., 2]
+        return np.stack([r * np.cos(th), r * np.sin(th), z], -1)
+
+    m = mapped_box_mesh([rl, tl, zl], (False, True, True), polar, order=2,
+                        side_bc=[0, 1, -1, -1, -1, -1])
+    return m
