@@ -33,6 +33,10 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 WORKLOAD = {"n": 16, "P": 3, "Q": 6, "Re": 1600.0, "Ma": 0.1, "cfl": 0.10, "dt_factor": 10.0}
+# turbulent cylinder of Sec. 6.4 on a curved O-grid (quadratic hexes): SDIRK3 at
+# CFL 40 on the smallest cell, BF16 BRJ blocks, learned Newton guess
+CYLINDER = {"n_r": 64, "n_theta": 96, "n_z": 12, "P": 3, "Q": 6, "Re": 3900.0, "Ma": 0.2,
+            "cfl": 40.0, "seed": 5}
 SAMPLE_N = 3          # CPU sample: the same case on 3^3 elements (same P, Q, CFL)
 FREEZE = 10
 # DRAM bytes (read + write) per element and launch from one ncu capture of the
@@ -45,6 +49,31 @@ def tgv_dt(n, P, Ma, cfl=0.10, factor=10.0):
     c + |u| = 1/Ma + 1 (T = 1, |u| <= 1 for the Taylor-Green field)."""
     dx = 2 * math.pi / n
     return factor * cfl * 2.0 * dx / (0.2 * (1.0 / Ma + 1.0) * P * P)
+
+
+def cylinder_dt(wl):
+    """dt of Eq. CFL (c_lambda = 0.2, d_RK = 2) at CFL 40 on the smallest cell
+    (the first radial cell at the wall), c + |u| = 1/Ma + 1."""
+    h = 1.08 ** (wl["n_r"] - 1 - __import__("numpy").arange(wl["n_r"]))
+    dr = (20.0 - 0.5) * 1.0 / h.sum()            # first cell (geometric growth 1.08)
+    return wl["cfl"] * 2.0 * dr / (0.2 * (1.0 / wl["Ma"] + 1.0) * wl["P"] ** 2)
+
+
+def cylinder_initial(m, wl):
+    """Uniform stream (1, 0, 0) at T = 1 plus a piecewise-constant 1% velocity
+    perturbation N(0, 1) x 0.01 per element (numpy PCG64, seed 5)."""
+    import numpy as np
+    import torch
+    import workloads as w
+    u = m.project(0.0)
+    E, nv, nm = m.shape
+    n = wl["P"] + 1
+    idx = np.indices((n,) * 3).reshape(3, -1)
+    one = np.all((idx == 0) | (idx == n - 1), axis=0).astype(np.float64)  # vertex modes
+    du = np.zeros((E, nv, nm))
+    du[:, 1:4, :] = w.perturbation((E, 3), wl["seed"])[:, :, None] * one[None, None, :]
+    u += torch.from_numpy(du).to(u.device)
+    return u
 
 
 def peaks():
@@ -138,17 +167,26 @@ def run_ours(args, rank, world):
 
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
-    wl = WORKLOAD
-    case = w.tgv_case(n=wl["n"], P=wl["P"], Q=wl["Q"], Re=wl["Re"], Ma=wl["Ma"])
-    dt = tgv_dt(wl["n"], wl["P"], wl["Ma"], wl["cfl"], wl["dt_factor"])
+    cyl = args.workload == "cylinder"
+    wl = CYLINDER if cyl else WORKLOAD
+    if cyl:
+        case = w.cylinder_case(wl["n_r"], wl["n_theta"], wl["n_z"], P=wl["P"], Q=wl["Q"],
+                               Re=wl["Re"], Ma=wl["Ma"])
+        dt = cylinder_dt(wl)
+    else:
+        case = w.tgv_case(n=wl["n"], P=wl["P"], Q=wl["Q"], Re=wl["Re"], Ma=wl["Ma"])
+        dt = tgv_dt(wl["n"], wl["P"], wl["Ma"], wl["cfl"], wl["dt_factor"])
     m = dgl.Mesh.from_case(case)
     tuning = dgl.apply_tuning(m)          # stored autotuning choice for this (dim, P, Q)
     ndof = m.info["n_dof"]
     E = m.info["n_elem"]
     nb = m.info["n_var"] * m.info["n_mode"]
-    u = m.project(0.0)
+    u = cylinder_initial(m, wl) if cyl else m.project(0.0)
     pc = dgl.Precond(m)
-    kw = dict(restart=30, rtol=5e-2, alpha=1e-3, J=7, precision=args.precision)
+    tableau = 3 if cyl else 2
+    nstage = tableau
+    kw = dict(restart=30, rtol=5e-2, alpha=1e-3, J=7, precision=args.precision, tableau=tableau,
+              graphs=True)
     if args.guess != "plain":
         # initial guess S_m + previous stage increment (+ learned MLP correction, one
         # per stage, 2 x 256 hidden, seeded weights with a zero output layer,
@@ -156,9 +194,10 @@ def run_ours(args, rank, world):
         nb = m.info["n_var"] * m.info["n_mode"]
         params = None
         if args.guess == "learned":
-            params = (w.mlp_params(3 * nb, 256, nb, seed=101, zero_last=True)
-                      + w.mlp_params(3 * nb, 256, nb, seed=102, zero_last=True))
-        kw["guess"] = dgl.Guess(m, params, stages=2, hidden=256, lr=1e-3)
+            params = []
+            for st in range(nstage):
+                params += w.mlp_params(3 * nb, 256, nb, seed=101 + st, zero_last=True)
+        kw["guess"] = dgl.Guess(m, params, stages=nstage, hidden=256, lr=1e-3)
         kw["guess_train_iters"] = 4
         args.warmup = max(args.warmup, 6)
     state = {"k": 0, "t": 0.0}
@@ -273,9 +312,19 @@ def run_ours(args, rank, world):
 
     newton = [s["newton_iters"] for s in timed_stats]
     gm = [s["gmres_iters"] for s in timed_stats]
+    if cyl:
+        metric = ("SDIRK3 step throughput at fixed Newton tolerance (DOF-steps/s); curved O-grid "
+                  f"{wl['n_r']}x{wl['n_theta']}x{wl['n_z']} quadratic hexes P=3, CFL 40")
+        wname = (f"cylinder_ogrid{wl['n_r']}x{wl['n_theta']}x{wl['n_z']}_P{wl['P']}_Q{wl['Q']}"
+                 f"_sdirk3_cfl{wl['cfl']:g}")
+        data = "synthetic (uniform stream + seeded 1% velocity perturbation)"
+    else:
+        metric = ("SDIRK2 step throughput at fixed Newton tolerance (DOF-steps/s); "
+                  "TGV 16^3 hexes P=3, 10x explicit dt")
+        wname = f"tgv{wl['n']}^3_P{wl['P']}_Q{wl['Q']}_sdirk2_dt{wl['dt_factor']:g}xexplicit"
+        data = "synthetic (analytic Taylor-Green initial field)"
     out = {
-        "metric": "SDIRK2 step throughput at fixed Newton tolerance (DOF-steps/s); "
-                  "TGV 16^3 hexes P=3, 10x explicit dt",
+        "metric": metric,
         "value": value,
         "unit": "DOF*step/s",
         "n_gpus": world,
@@ -286,8 +335,8 @@ def run_ours(args, rank, world):
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f64",
-        "data": "synthetic (analytic Taylor-Green initial field)",
-        "config": {"workload": f"tgv{wl['n']}^3_P{wl['P']}_Q{wl['Q']}_sdirk2_dt{wl['dt_factor']:g}xexplicit",
+        "data": data,
+        "config": {"workload": wname,
                    "n_dof": ndof, "dt": dt, "newton_alpha": 1e-3, "gmres": "restart 30, rtol 5e-2",
                    "precond": f"BRJ(7) {args.precision} blocks, rebuilt every {FREEZE} steps",
                    "initial_guess": {"plain": "S_m (plain)",
@@ -398,10 +447,19 @@ def main():
                     help="Newton initial guess: S_m, S_m + previous stage increment, or that plus "
                          "the learned MLP correction")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="tgv", choices=["tgv", "cylinder"],
+                    help="tgv: the Taylor-Green benchmark (default); cylinder: the curved O-grid "
+                         "workload (SDIRK3, BF16 blocks, learned guess unless overridden)")
     ap.add_argument("--elems", type=int, default=WORKLOAD["n"],
                     help="elements per direction (16 = the benchmark; smaller only for profiler captures)")
     args = ap.parse_args()
     WORKLOAD["n"] = args.elems
+    if args.workload == "cylinder":
+        args.no_cpu_baseline = True    # the oracle sample is the Taylor-Green case
+        if "--precision" not in sys.argv:
+            args.precision = "bf16"
+        if "--guess" not in sys.argv:
+            args.guess = "learned"
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":

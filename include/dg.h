@@ -53,8 +53,15 @@ typedef struct dg_precond_s* dg_precond_t; /* BRJ blocks + trace Jacobians */
 /* Mesh of quadrilaterals (dim 2) or hexahedra (dim 3), Sec. 3.1.
  * nodes[e][a][x]: geometry nodes of element e, a = tensor index of the
  *   (geom_order+1)^dim equispaced reference nodes (first direction fastest).
- *   This build accepts geom_order = 1 with axis-aligned elements (others:
- *   DG_ERR_UNSUPPORTED).
+ *   geom_order = 1 (straight-sided) or 2 (quadratic: 9 / 27 nodes).  Meshes
+ *   whose elements are all axis-aligned boxes take kernels with a diagonal
+ *   metric and the tensor-product inverse mass matrix; any other mesh
+ *   (curved, rotated or sheared elements) takes the general-geometry kernels:
+ *   per-point metrics d xi/d x and w|J| at the volume and face points,
+ *   owner-side unit normals and surface weights by Nanson's formula, and a
+ *   dense inverse element mass matrix (Sec. 3.1: M = B^T Lambda(wJ) B), all
+ *   computed once on the device; (dim, P, Q) without general-geometry kernels
+ *   and elements with non-positive |J| give DG_ERR_UNSUPPORTED / DG_ERR_ARG.
  * faces[f][6] = (eL, fL, eR, fR, orient, bc): local face 2r is xi_r = -1,
  *   2r+1 is xi_r = +1; interior and periodic faces have eR >= 0 and bc = -1,
  *   physical boundary faces eR = fR = -1 and bc = index into dg_physics.bc.
@@ -173,7 +180,9 @@ typedef struct {
  * off-diagonal product. */
 dg_status dg_precond_build(dg_mesh_t m, const double* u, double t, double dt_a,
                            const dg_prec_cfg* cfg, dg_precond_t* inout, void* stream);
-/* out = P^-1 q by the BRJ(J) iteration from q^0 = 0 (Eq. precond-Jacobi).
+/* FP64 blocks need 2 nm^2 doubles of shared memory per CTA (up to P = 3 in
+ * 3-D) and, on general-geometry meshes, P <= 2; otherwise DG_ERR_UNSUPPORTED.
+ * out = P^-1 q by the BRJ(J) iteration from q^0 = 0 (Eq. precond-Jacobi).
  * out must not alias q. */
 dg_status dg_precond_apply(dg_precond_t p, const double* q, double* out, void* stream);
 dg_status dg_precond_destroy(dg_precond_t p);

@@ -279,6 +279,12 @@ static void free_mesh(dg_mesh_s* m) {
   cudaFree(m->hbuf);
   cudaFree(m->tbuf);
   cudaFree(m->fbuf);
+  cudaFree(m->vgeo);
+  cudaFree(m->vx);
+  cudaFree(m->fgeo);
+  cudaFree(m->fdat);
+  cudaFree(m->fbeta);
+  cudaFree(m->minv);
   cudaFree(m->force);
   cudaFree(m->scratch);
   cudaFree(m->red);
@@ -299,27 +305,28 @@ dg_status dg_mesh_create(const dg_mesh_desc* md, const dg_physics* ph, void* str
   if (d != 2 && d != 3) return DG_ERR_ARG;
   if (md->P < 1 || md->Q < 1 || md->n_elem < 1 || md->n_faces < 1) return DG_ERR_ARG;
   if (md->P + 1 > NMAX || md->Q > QMAX) return DG_ERR_UNSUPPORTED;
-  if (md->geom_order != 1) return DG_ERR_UNSUPPORTED;
+  if (md->geom_order != 1 && md->geom_order != 2) return DG_ERR_UNSUPPORTED;
   if (!supported(d, md->P, md->Q)) return DG_ERR_UNSUPPORTED;
   if (ph->n_bc < 0 || ph->n_bc > 8) return DG_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   const int E = md->n_elem, F = md->n_faces;
-  // geometry: axis-aligned boxes only
+  // axis-aligned affine boxes take the diagonal-metric kernels; any other
+  // element (quadratic, rotated, sheared) the general-geometry kernels
   std::vector<ElemGeo> geo(E);
+  bool boxes = md->geom_order == 1;
   const int nn = 1 << d;
-  for (int e = 0; e < E; ++e) {
+  for (int e = 0; e < E && boxes; ++e) {
     const double* X = md->nodes + (size_t)e * nn * d;
     ElemGeo g{};
     for (int r = 0; r < d; ++r) {
       g.x0[r] = X[r];
       g.h[r] = X[(1 << r) * d + r] - X[r];
-      if (!(g.h[r] > 0.0)) return DG_ERR_UNSUPPORTED;
+      if (!(g.h[r] > 0.0)) boxes = false;
     }
-    for (int a = 0; a < nn; ++a)
+    for (int a = 0; a < nn && boxes; ++a)
       for (int r = 0; r < d; ++r) {
         double expect = g.x0[r] + (((a >> r) & 1) ? g.h[r] : 0.0);
-        if (std::fabs(X[a * d + r] - expect) > 1e-12 * (1.0 + std::fabs(expect)))
-          return DG_ERR_UNSUPPORTED;
+        if (std::fabs(X[a * d + r] - expect) > 1e-12 * (1.0 + std::fabs(expect))) boxes = false;
       }
     g.detJ = 1.0;
     for (int r = 0; r < 3; ++r) {
@@ -329,6 +336,8 @@ dg_status dg_mesh_create(const dg_mesh_desc* md, const dg_physics* ph, void* str
     g.idet = 1.0 / g.detJ;
     geo[e] = g;
   }
+  if (!boxes) std::fill(geo.begin(), geo.end(), ElemGeo{});
+  if (!boxes && !supported_curved(d, md->P, md->Q)) return DG_ERR_UNSUPPORTED;
   // connectivity: every (element, local face) exactly once, aligned sides
   std::vector<int> seen((size_t)E * 2 * d, 0);
   for (int f = 0; f < F; ++f) {
@@ -344,7 +353,9 @@ dg_status dg_mesh_create(const dg_mesh_desc* md, const dg_physics* ph, void* str
     } else {
       if (bc < 0 || bc >= ph->n_bc) return DG_ERR_ARG;
       int t = ph->bc[bc];
-      if (t != DG_BC_DIRICHLET && t != DG_BC_ISO_WALL) return DG_ERR_UNSUPPORTED;
+      if (t != DG_BC_DIRICHLET && t != DG_BC_ISO_WALL && t != DG_BC_ADIA_WALL &&
+          t != DG_BC_FARFIELD)
+        return DG_ERR_UNSUPPORTED;
     }
   }
   for (size_t i = 0; i < seen.size(); ++i)
@@ -415,6 +426,14 @@ dg_status dg_mesh_create(const dg_mesh_desc* md, const dg_physics* ph, void* str
   if (err != cudaSuccess) {
     free_mesh(m);
     return cuda_status(err);
+  }
+  if (!boxes) {
+    m->curved = 1;
+    dg_status st = build_general_geometry(m, md->nodes, md->geom_order, s);
+    if (st != DG_OK) {
+      free_mesh(m);
+      return st;
+    }
   }
   if (ph->forcing) {
     dg_status st = launch_project(m, 1, 0.0, m->force, s);

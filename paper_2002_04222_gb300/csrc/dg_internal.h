@@ -40,6 +40,16 @@ struct ElemGeo {
   double detJ, idet;  // |J| = prod h/2 and its inverse
 };
 
+// device pointers of the general-geometry data, passed by value to kernels
+struct GenGeo {
+  const double* vgeo;   // [E][DIM*DIM+1][NQ]
+  const double* vx;     // [E][DIM][NQ]
+  const double* fgeo;   // [E][2DIM][DIM*DIM][NF]
+  const double* fdat;   // [F][2DIM+1][NF]
+  const double* fbeta;  // [F]
+  const double* minv;   // [E][NM][NM]
+};
+
 }  // namespace dg
 
 struct dg_precond_s;
@@ -58,7 +68,16 @@ struct dg_mesh_s {
   dg::Phys phys;
   dg::Tune tune;
   // device buffers
-  dg::ElemGeo* geo = nullptr;   // [E]
+  dg::ElemGeo* geo = nullptr;   // [E] axis-aligned affine elements (curved = 0)
+  // general elements (curved = 1: quadratic, or straight-sided but not
+  // axis-aligned): per-point metrics, face data and dense inverse mass matrices
+  int curved = 0;
+  double* vgeo = nullptr;       // [E][dim*dim+1][nq]: d xi_r/d x_j (r-major), then w|J|
+  double* vx = nullptr;         // [E][dim][nq] coordinates of the volume points
+  double* fgeo = nullptr;       // [E][2dim][dim*dim][nf] d xi_r/d x_j at the face points
+  double* fdat = nullptr;       // [F][2dim+1][nf] owner normal n, w^G J^G, coordinates x
+  double* fbeta = nullptr;      // [F] interior-penalty factor (P+1)^2 / h
+  double* minv = nullptr;       // [E][nm][nm] inverse element mass matrices
   int32_t* faces = nullptr;     // [F][6]
   double* hbuf = nullptr;       // [E][dim][nv][nq]   weighted volume fluxes
   double* tbuf = nullptr;       // [E][2dim][(1+dim)nv][nf] face traces
@@ -131,8 +150,13 @@ struct EvalArgs {
   bool skip_vol = false, skip_lift = false;  // autotuning times the kernels separately
 };
 dg_status launch_residual(dg_mesh_s* m, const EvalArgs& a, cudaStream_t s);
+dg_status build_general_geometry(dg_mesh_s* m, const double* nodes_host, int g, cudaStream_t s);
 dg_status launch_project(dg_mesh_s* m, int what, double t, double* out, cudaStream_t s);
 bool supported(int dim, int P, int Q);
+bool supported_curved(int dim, int P, int Q);  // general-geometry instances
+inline GenGeo gen_geo(const dg_mesh_s* m) {
+  return GenGeo{m->vgeo, m->vx, m->fgeo, m->fdat, m->fbeta, m->minv};
+}
 void init_tune(dg_mesh_s* m);
 dg_status autotune(dg_mesh_s* m, int reps, dg_tune_result* res, cudaStream_t s);
 bool tune_valid(dg_mesh_s* m, const dg_tune_result* t);

@@ -279,6 +279,10 @@ __device__ inline void exact_state(int D, const Phys& ph, const double* x, doubl
     double p = pinf + (cos(2 * X) + cos(2 * Y)) * (cos(2 * Z) + 2.0) / 16.0;
     rho = p / pinf;
     temp = 1.0;
+  } else if (ph.field == DG_FIELD_UNIFORM && ph.fpar[0] > 0.0) {  // (rho, u, v, w, T)
+    rho = ph.fpar[0];
+    for (int k = 0; k < D; ++k) vel[k] = ph.fpar[1 + k];
+    temp = ph.fpar[4];
   } else {  // uniform / cylinder free stream
     vel[0] = 1.0;
   }
@@ -305,46 +309,123 @@ __device__ inline double wall_temperature(const Phys& ph, const double* x) {
   return 1.0;
 }
 
-// Weakly imposed boundary state (exterior state of the Riemann flux and the
-// state of the viscous boundary flux).
+// Characteristic far-field state from the interior state UL and the free
+// stream Ui along the outward unit normal n: outgoing invariant
+// u_n + 2c/(gamma-1) from UL, incoming u_n - 2c/(gamma-1) from Ui, entropy and
+// tangential velocity from the upwind side; supersonic normal flow takes the
+// upwind state whole.
 template <int D>
-__device__ inline void boundary_state(int bctype, const Phys& ph, const double* x, double t,
-                                      const double* UL, double* UB) {
-  if (bctype == DG_BC_ISO_WALL) {
-    double Tw = wall_temperature(ph, x);
-    UB[0] = UL[0];
+__device__ inline void farfield_state(const Phys& ph, const double* UL, const double* Ui,
+                                      const double* n, double* UB) {
+  double irL, vL[D], pL, TL, iri, vi[D], pi, Ti;
+  primitives<D>(UL, ph, irL, vL, pL, TL);
+  primitives<D>(Ui, ph, iri, vi, pi, Ti);
+  const double g = ph.gamma;
+  const double cL = sqrt(g * pL * irL), ci = sqrt(g * pi * iri);
+  double un = 0.0, uni = 0.0;
 #pragma unroll
-    for (int k = 0; k < D; ++k) UB[1 + k] = 0.0;
-    UB[D + 1] = UL[0] * Tw / (ph.gamma * ph.gm1 * ph.Ma * ph.Ma);
-  } else {  // DG_BC_DIRICHLET
-    exact_state(D, ph, x, t, UB);
+  for (int k = 0; k < D; ++k) {
+    un += vL[k] * n[k];
+    uni += vi[k] * n[k];
   }
+  if (un >= cL) {
+#pragma unroll
+    for (int v = 0; v < D + 2; ++v) UB[v] = UL[v];
+    return;
+  }
+  if (un <= -cL) {
+#pragma unroll
+    for (int v = 0; v < D + 2; ++v) UB[v] = Ui[v];
+    return;
+  }
+  const double Rp = un + 2.0 * cL / ph.gm1, Rm = uni - 2.0 * ci / ph.gm1;
+  const double unb = 0.5 * (Rp + Rm), cb = 0.25 * ph.gm1 * (Rp - Rm);
+  const bool out = unb > 0.0;
+  const double sup = out ? pL / pow(UL[0], g) : pi / pow(Ui[0], g);
+  const double* vu = out ? vL : vi;
+  double vun = 0.0;
+#pragma unroll
+  for (int k = 0; k < D; ++k) vun += vu[k] * n[k];
+  const double rb = pow(cb * cb / (g * sup), 1.0 / ph.gm1);
+  const double pb = rb * cb * cb / g;
+  double ke = 0.0;
+  UB[0] = rb;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    const double vb = vu[k] - vun * n[k] + unb * n[k];
+    UB[1 + k] = rb * vb;
+    ke += vb * vb;
+  }
+  UB[D + 1] = pb / ph.gm1 + 0.5 * rb * ke;
 }
 
-// Numerical normal flux H^n = F^n - G^n on a face with owner-side normal
-// n = sgn e_r (Sec. 3.1, with the adjoint-consistent interior penalty):
-//   S_i  = G_i({Q}, n (x) [Q]),  [Q] = Q_L - Q_R,
-//   G^n  = n . (G({Q}, {grad Q}) - beta_p S),
-// where on a boundary face Q_R = {Q} = the boundary state built from Q_L and
-// {grad Q} is the interior gradient.  dQa is the face-average gradient.
+// Weakly imposed boundary data (the boundary types of dg.h): QR the exterior
+// state of the Riemann flux, QB the state of the viscous flux and of the
+// penalty jump Q_L - Q_B.  Returns true on an adiabatic wall, where the
+// energy components of G^n and S_j vanish.
 template <int D>
-__device__ inline void numerical_flux(const double* QL, const double* QRin, int bctype,
-                                      const double* x, double t, const double dQa[D][D + 2],
-                                      int r, double sgn, double beta, const Phys& ph,
-                                      double* Hn, double S[D][D + 2]) {
+__device__ inline bool boundary_states(int bctype, const Phys& ph, const double* x, double t,
+                                       const double* UL, const double* n, double* QR,
+                                       double* QB) {
   constexpr int NV = D + 2;
-  double QR[NV], Qa[NV], n[D];
+  if (bctype == DG_BC_ISO_WALL) {
+    const double Tw = wall_temperature(ph, x);
+    QB[0] = UL[0];
 #pragma unroll
-  for (int k = 0; k < D; ++k) n[k] = k == r ? sgn : 0.0;
+    for (int k = 0; k < D; ++k) QB[1 + k] = 0.0;
+    QB[D + 1] = UL[0] * Tw / (ph.gamma * ph.gm1 * ph.Ma * ph.Ma);
+  } else if (bctype == DG_BC_ADIA_WALL) {
+    double ir, vel[D], p, T;
+    primitives<D>(UL, ph, ir, vel, p, T);
+    double mn = 0.0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) mn += UL[1 + k] * n[k];
+    QR[0] = UL[0];
+#pragma unroll
+    for (int k = 0; k < D; ++k) QR[1 + k] = UL[1 + k] - 2.0 * mn * n[k];
+    QR[D + 1] = UL[D + 1];
+    QB[0] = UL[0];
+#pragma unroll
+    for (int k = 0; k < D; ++k) QB[1 + k] = 0.0;
+    QB[D + 1] = p / ph.gm1;
+    return true;
+  } else if (bctype == DG_BC_FARFIELD) {
+    double Ui[NV];
+    exact_state(D, ph, x, t, Ui);
+    farfield_state<D>(ph, UL, Ui, n, QB);
+  } else {  // DG_BC_DIRICHLET
+    exact_state(D, ph, x, t, QB);
+  }
+#pragma unroll
+  for (int v = 0; v < NV; ++v) QR[v] = QB[v];
+  return false;
+}
+
+// Numerical normal flux H^n = F^n - G^n on a face with owner-side unit
+// normal n (Sec. 3.1, with the adjoint-consistent interior penalty):
+//   S_i  = G_i({Q}, n (x) [Q]),  [Q] = Q_L - Q_R  (Q_L - Q_B on a boundary),
+//   G^n  = n . (G({Q}, {grad Q}) - beta_p S),
+// where on a boundary face the Riemann flux takes the exterior state Q_R and
+// {Q} = Q_B (boundary_states) with the interior gradient.  dQa is the
+// face-average gradient.
+template <int D>
+__device__ inline void numerical_flux_n(const double* QL, const double* QRin, int bctype,
+                                        const double* x, double t, const double dQa[D][D + 2],
+                                        const double* n, double beta, const Phys& ph,
+                                        double* Hn, double S[D][D + 2]) {
+  constexpr int NV = D + 2;
+  double QR[NV], Qa[NV], jump[NV];
+  bool adiabatic = false;
   if (bctype > 0) {
-    boundary_state<D>(bctype, ph, x, t, QL, QR);
+    adiabatic = boundary_states<D>(bctype, ph, x, t, QL, n, QR, Qa);
 #pragma unroll
-    for (int v = 0; v < NV; ++v) Qa[v] = QR[v];
+    for (int v = 0; v < NV; ++v) jump[v] = QL[v] - Qa[v];
   } else {
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       QR[v] = QRin[v];
       Qa[v] = 0.5 * (QL[v] + QR[v]);
+      jump[v] = QL[v] - QR[v];
     }
   }
   riemann_flux<D>(QL, QR, n, ph, Hn);
@@ -353,18 +434,39 @@ __device__ inline void numerical_flux(const double* QL, const double* QRin, int 
 #pragma unroll
     for (int j = 0; j < D; ++j)
 #pragma unroll
-      for (int v = 0; v < NV; ++v) gS[j][v] = j == r ? sgn * (QL[v] - QR[v]) : 0.0;
+      for (int v = 0; v < NV; ++v) gS[j][v] = n[j] * jump[v];
     viscous_flux<D>(Qa, gS, ph, S);
     double Gv[D][NV];
     viscous_flux<D>(Qa, dQa, ph, Gv);
 #pragma unroll
-    for (int v = 0; v < NV; ++v) Hn[v] -= sgn * (Gv[r][v] - beta * S[r][v]);
+    for (int v = 0; v < NV; ++v) {
+      if (adiabatic && v == NV - 1) continue;
+      double gn = 0.0;
+#pragma unroll
+      for (int j = 0; j < D; ++j) gn += n[j] * (Gv[j][v] - beta * S[j][v]);
+      Hn[v] -= gn;
+    }
+    if (adiabatic)
+#pragma unroll
+      for (int j = 0; j < D; ++j) S[j][NV - 1] = 0.0;
   } else {
 #pragma unroll
     for (int j = 0; j < D; ++j)
 #pragma unroll
       for (int v = 0; v < NV; ++v) S[j][v] = 0.0;
   }
+}
+
+// the same for the axis normal n = sgn e_r
+template <int D>
+__device__ inline void numerical_flux(const double* QL, const double* QRin, int bctype,
+                                      const double* x, double t, const double dQa[D][D + 2],
+                                      int r, double sgn, double beta, const Phys& ph,
+                                      double* Hn, double S[D][D + 2]) {
+  double n[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) n[k] = k == r ? sgn : 0.0;
+  numerical_flux_n<D>(QL, QRin, bctype, x, t, dQa, n, beta, ph, Hn, S);
 }
 
 // ------------------------------------------------------------ fused / axis-specialised forms
@@ -582,16 +684,21 @@ __device__ inline void numerical_flux_axis(const double* QL, const double* QRin,
                                            const double dQa[D][D + 2], double sgn, double beta,
                                            const Phys& ph, double* Hn, double S[D][D + 2]) {
   constexpr int NV = D + 2;
-  double QR[NV], Qa[NV];
+  double QR[NV], Qa[NV], Qj[NV];
+  bool adiabatic = false;
   if (bctype > 0) {
-    boundary_state<D>(bctype, ph, x, t, QL, QR);
+    double n[D];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) Qa[v] = QR[v];
+    for (int k = 0; k < D; ++k) n[k] = k == R ? sgn : 0.0;
+    adiabatic = boundary_states<D>(bctype, ph, x, t, QL, n, QR, Qa);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Qj[v] = Qa[v];
   } else {
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       QR[v] = QRin[v];
       Qa[v] = 0.5 * (QL[v] + QR[v]);
+      Qj[v] = QR[v];
     }
   }
   if (ph.riemann == DG_RIEMANN_HLLC) {
@@ -607,11 +714,15 @@ __device__ inline void numerical_flux_axis(const double* QL, const double* QRin,
     visc_prim<D>(Qa, ph, pa);
     double g[NV], Gr[NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) g[v] = sgn * (QL[v] - QR[v]);
+    for (int v = 0; v < NV; ++v) g[v] = sgn * (QL[v] - Qj[v]);
     viscous_rank1<D, R>(pa, g, ph, S);
     viscous_row<D, R>(pa, dQa, ph, Gr);
 #pragma unroll
-    for (int v = 0; v < NV; ++v) Hn[v] -= sgn * (Gr[v] - beta * S[R][v]);
+    for (int v = 0; v < NV; ++v)
+      if (!(adiabatic && v == NV - 1)) Hn[v] -= sgn * (Gr[v] - beta * S[R][v]);
+    if (adiabatic)
+#pragma unroll
+      for (int j = 0; j < D; ++j) S[j][NV - 1] = 0.0;
   } else {
 #pragma unroll
     for (int j = 0; j < D; ++j)

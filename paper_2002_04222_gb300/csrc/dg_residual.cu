@@ -1,5 +1,7 @@
-// DG residual R(u) = M^-1 L(u, t) of Sec. 3.1 (Eq. matrix-form-equations) on
-// axis-aligned affine quads/hexes, in three FP64 kernels:
+// DG residual R(u) = M^-1 L(u, t) of Sec. 3.1 (Eq. matrix-form-equations) in
+// three FP64 kernels, each in two geometry variants: axis-aligned affine
+// quads/hexes (diagonal metric, tensor-product inverse mass) and general
+// elements (curved or rotated: per-point metrics, dense inverse mass):
 //   vol_kernel   sum-factorised BwdTrans (B), collocation derivatives on the
 //                Gauss grid (D_j), fused Euler + viscous volume flux H_j
 //                weighted by w|J| and the reference metric, and the face
@@ -21,10 +23,11 @@
 namespace dg {
 
 // ---------------------------------------------------------------- kernel 1
-template <int DIM, int P, int Q>
+template <int DIM, int P, int Q, bool CV>
 __global__ void __launch_bounds__(256) vol_kernel(const __grid_constant__ Tables tab,
                                                   const __grid_constant__ Phys ph,
-                                                  const ElemGeo* __restrict__ geo, int E,
+                                                  const ElemGeo* __restrict__ geo,
+                                                  const __grid_constant__ GenGeo gg, int E,
                                                   const double* __restrict__ u,
                                                   const double* __restrict__ v,
                                                   const double* __restrict__ epsp,
@@ -83,6 +86,44 @@ __global__ void __launch_bounds__(256) vol_kernel(const __grid_constant__ Tables
     const int eb = idx / NQ, q = idx - eb * NQ;
     const int e = e0 + eb;
     if (e >= E) continue;
+    if constexpr (CV) {
+      // general element: grad = sum_r (d xi_r/dx) d_r, contravariant flux
+      // w|J| sum_j (d xi_r/d x_j) H_j
+      const double* gp = gg.vgeo + (long long)e * (DIM * DIM + 1) * NQ + q;
+      double gi[DIM][DIM];
+#pragma unroll
+      for (int r = 0; r < DIM; ++r)
+#pragma unroll
+        for (int j = 0; j < DIM; ++j) gi[r][j] = gp[(r * DIM + j) * NQ];
+      const double wJ = gp[DIM * DIM * NQ];
+      double U[NV], dU[DIM][NV], H[DIM][NV];
+#pragma unroll
+      for (int vv = 0; vv < NV; ++vv) {
+        U[vv] = sQ[(eb * NV + vv) * NQ + q];
+        double dr[DIM];
+#pragma unroll
+        for (int r = 0; r < DIM; ++r) dr[r] = sG[((r * EPB + eb) * NV + vv) * NQ + q];
+#pragma unroll
+        for (int j = 0; j < DIM; ++j) {
+          double a = 0.0;
+#pragma unroll
+          for (int r = 0; r < DIM; ++r) a = fma(gi[r][j], dr[r], a);
+          dU[j][vv] = a;
+        }
+      }
+      ns_volume_flux<DIM>(U, dU, ph, H);
+      double* hb = hbuf + (long long)e * DIM * NV * NQ + q;
+#pragma unroll
+      for (int r = 0; r < DIM; ++r)
+#pragma unroll
+        for (int vv = 0; vv < NV; ++vv) {
+          double a = 0.0;
+#pragma unroll
+          for (int j = 0; j < DIM; ++j) a = fma(gi[r][j], H[j][vv], a);
+          hb[(r * NV + vv) * NQ] = wJ * a;
+        }
+      continue;
+    }
     const ElemGeo g = geo[e];
     int c[3];
     grid_coords<DIM, Q>(q, c);
@@ -109,6 +150,55 @@ __global__ void __launch_bounds__(256) vol_kernel(const __grid_constant__ Tables
   }
   // face traces of Q and grad Q by Lagrange extrapolation along the normal
   constexpr int NTR = 2 * DIM * (1 + DIM) * NV * NF;
+  if constexpr (CV) {
+    // general element: extrapolate the value and the DIM reference
+    // derivatives (polynomials along the line), then map the derivatives with
+    // the metric of the face point
+    constexpr int NTV = 2 * DIM * NV * NF;
+    for (int idx = threadIdx.x; idx < EPB * NTV; idx += blockDim.x) {
+      const int eb = idx / NTV;
+      int rem = idx - eb * NTV;
+      const int e = e0 + eb;
+      if (e >= E) continue;
+      const int p = rem % NF;
+      rem /= NF;
+      const int vv = rem % NV;
+      const int lf = rem / NV;
+      const int r = lf >> 1;
+      const double* lw = sl + (lf & 1) * Q;
+      int c[3] = {0, 0, 0};
+      if (DIM == 2) {
+        c[1 - r] = p;
+      } else {
+        const int t0 = r == 0 ? 1 : 0, t1 = r == 2 ? 1 : 2;
+        c[t0] = p % Q;
+        c[t1] = p / Q;
+      }
+      const int base = c[0] + Q * c[1] + Q * Q * c[2];
+      const int str = r == 0 ? 1 : (r == 1 ? Q : Q * Q);
+      double ext[1 + DIM];
+#pragma unroll
+      for (int fld = 0; fld <= DIM; ++fld) {
+        const double* src = fld == 0 ? sQ + (eb * NV + vv) * NQ
+                                     : sG + (((fld - 1) * EPB + eb) * NV + vv) * NQ;
+        double acc = 0.0;
+#pragma unroll
+        for (int k = 0; k < Q; ++k) acc = fma(lw[k], src[base + k * str], acc);
+        ext[fld] = acc;
+      }
+      const double* gp = gg.fgeo + ((long long)e * 2 * DIM + lf) * DIM * DIM * NF + p;
+      double* tb = tbuf + (long long)e * NTR + (lf * (1 + DIM) * NV + vv) * NF + p;
+      tb[0] = ext[0];
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) {
+        double a = 0.0;
+#pragma unroll
+        for (int rr = 0; rr < DIM; ++rr) a = fma(gp[(rr * DIM + j) * NF], ext[1 + rr], a);
+        tb[(1 + j) * NV * NF] = a;
+      }
+    }
+    return;
+  }
   for (int idx = threadIdx.x; idx < EPB * NTR; idx += blockDim.x) {
     const int eb = idx / NTR;
     int rem = idx - eb * NTR;
@@ -245,6 +335,114 @@ __global__ void __launch_bounds__(128) face_kernel(const __grid_constant__ Table
   }
 }
 
+// general elements: one thread per face point with the owner-side normal,
+// surface weight and coordinates of the point, the face's penalty factor, and
+// each side's metric at the point for the symmetric-flux lift
+template <int DIM, int P, int Q>
+__global__ void __launch_bounds__(128) face_kernel_gen(const __grid_constant__ Phys ph,
+                                                       const __grid_constant__ GenGeo gg,
+                                                       const int32_t* __restrict__ faces, int F,
+                                                       double t, const double* __restrict__ tbuf,
+                                                       double* __restrict__ fbuf) {
+  using C = Cfg<DIM, P, Q>;
+  constexpr int NV = C::NV, NF = C::NF;
+  constexpr int NTR = 2 * DIM * (1 + DIM) * NV * NF;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= F * NF) return;
+  const int f = idx / NF, p = idx - f * NF;
+  const int eL = faces[f * 6 + 0], fL = faces[f * 6 + 1];
+  const int eR = faces[f * 6 + 2], fR = faces[f * 6 + 3], bc = faces[f * 6 + 5];
+  const double* fd = gg.fdat + (long long)f * (2 * DIM + 1) * NF + p;
+  double n[DIM], x[3] = {0, 0, 0};
+#pragma unroll
+  for (int j = 0; j < DIM; ++j) {
+    n[j] = fd[j * NF];
+    x[j] = fd[(DIM + 1 + j) * NF];
+  }
+  const double wJf = fd[DIM * NF];
+  double QL[NV], QR[NV], dQa[DIM][NV];
+  const double* tl = tbuf + (long long)eL * NTR + (fL * (1 + DIM)) * NV * NF + p;
+#pragma unroll
+  for (int vv = 0; vv < NV; ++vv) {
+    QL[vv] = tl[vv * NF];
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) dQa[j][vv] = tl[((1 + j) * NV + vv) * NF];
+  }
+  int bctype = 0;
+  double cfac = 1.0;
+  if (eR >= 0) {
+    const double* tr = tbuf + (long long)eR * NTR + (fR * (1 + DIM)) * NV * NF + p;
+#pragma unroll
+    for (int vv = 0; vv < NV; ++vv) {
+      QR[vv] = tr[vv * NF];
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) dQa[j][vv] = 0.5 * (dQa[j][vv] + tr[((1 + j) * NV + vv) * NF]);
+    }
+    cfac = 0.5;
+  } else {
+    bctype = ph.bc[bc];
+#pragma unroll
+    for (int vv = 0; vv < NV; ++vv) QR[vv] = 0.0;
+  }
+  double Hn[NV], S[DIM][NV];
+  numerical_flux_n<DIM>(QL, QR, bctype, x, t, dQa, n, gg.fbeta[f], ph, Hn, S);
+  const double cs = ph.viscous ? cfac * ph.beta_s * wJf : 0.0;
+#pragma unroll
+  for (int side = 0; side < 2; ++side) {
+    const int e = side == 0 ? eL : eR, lf = side == 0 ? fL : fR;
+    if (e < 0) break;
+    const double* gp = gg.fgeo + ((long long)e * 2 * DIM + lf) * DIM * DIM * NF + p;
+    double* fo = fbuf + (long long)e * NTR + (lf * (1 + DIM)) * NV * NF + p;
+    const double sg = side == 0 ? -wJf : wJf;
+#pragma unroll
+    for (int vv = 0; vv < NV; ++vv) fo[vv * NF] = sg * Hn[vv];
+#pragma unroll
+    for (int r = 0; r < DIM; ++r) {
+      double gr[DIM];
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) gr[j] = cs * gp[(r * DIM + j) * NF];
+#pragma unroll
+      for (int vv = 0; vv < NV; ++vv) {
+        double a = 0.0;
+#pragma unroll
+        for (int j = 0; j < DIM; ++j) a = fma(gr[j], S[j][vv], a);
+        fo[((1 + r) * NV + vv) * NF] = a;
+      }
+    }
+  }
+}
+
+// B^T on G [EPB][NV][NQ] -> result in R [EPB][NV][NM] (general elements: the
+// dense inverse mass matrix is applied by the caller)
+template <int DIM, int P, int Q>
+__device__ __forceinline__ void bt_only(double* sG, double* t1, double* t2, double* sR,
+                                        const double* sB, int nrep) {
+  using C = Cfg<DIM, P, Q>;
+  constexpr int N = C::N, Q2 = C::Q2, N2 = C::N2;
+  if (DIM == 2) {
+    contract<Q, Q, 1, 1, N, 1, N, false>(sG, t1, sB, nrep);
+    __syncthreads();
+    contract<Q, N, 1, 0, N, 1, N, false>(t1, sR, sB, nrep);
+  } else {
+    contract<Q, Q, Q2, 2, N, 1, N, false>(sG, t1, sB, nrep);
+    __syncthreads();
+    contract<Q, Q, N2, 1, N, 1, N, false>(t1, t2, sB, nrep);
+    __syncthreads();
+    contract<Q, N, N2, 0, N, 1, N, false>(t2, sR, sB, nrep);
+  }
+  __syncthreads();
+}
+
+// out = M_e^-1 x for the coefficient vector x (NM values in shared memory)
+template <int NM>
+__device__ __forceinline__ double dense_minv_row(const double* __restrict__ Mi, int m,
+                                                 const double* x) {
+  double a = 0.0;
+#pragma unroll 8
+  for (int k = 0; k < NM; ++k) a = fma(Mi[(long long)k * NM + m], x[k], a);  // M^-1 symmetric
+  return a;
+}
+
 // B^T then |J|^-1 (M1^-1)^(x)d on G [EPB][NV][NQ] -> result in R [EPB][NV][NM]
 template <int DIM, int P, int Q>
 __device__ __forceinline__ void bt_minv(double* sG, double* t1, double* t2, double* sR,
@@ -276,9 +474,10 @@ __device__ __forceinline__ void bt_minv(double* sG, double* t1, double* t2, doub
 }
 
 // ---------------------------------------------------------------- kernel 3
-template <int DIM, int P, int Q>
+template <int DIM, int P, int Q, bool CV>
 __global__ void __launch_bounds__(256) lift_kernel(const __grid_constant__ Tables tab,
-                                                   const ElemGeo* __restrict__ geo, int E,
+                                                   const ElemGeo* __restrict__ geo,
+                                                   const __grid_constant__ GenGeo gg, int E,
                                                    const double* __restrict__ hbuf,
                                                    const double* __restrict__ fbuf,
                                                    const double* __restrict__ force,
@@ -350,14 +549,22 @@ __global__ void __launch_bounds__(256) lift_kernel(const __grid_constant__ Table
     __syncthreads();
   }
   double* sR = sH;  // reuse
-  bt_minv<DIM, P, Q>(sG, t1, t2, sR, sB, sMi, nrep);
+  if constexpr (CV)
+    bt_only<DIM, P, Q>(sG, t1, t2, sR, sB, nrep);
+  else
+    bt_minv<DIM, P, Q>(sG, t1, t2, sR, sB, sMi, nrep);
   for (int i = threadIdx.x; i < EPB * NV * NM; i += blockDim.x) {
     const int eb = i / (NV * NM);
     const int e = e0 + eb;
     if (e >= E) continue;
-    const double idet = geo[e].idet;
     const long long gi = (long long)e * NV * NM + (i - eb * NV * NM);
-    double R = sR[i] * idet;
+    double R;
+    if constexpr (CV) {
+      const int m = i % NM;
+      R = dense_minv_row<NM>(gg.minv + (long long)e * NM * NM, m, sR + (i - m));
+    } else {
+      R = sR[i] * geo[e].idet;
+    }
     if (force) R += force[gi];
     if (r_u) {
       const double ie = epsp[1];
@@ -369,10 +576,11 @@ __global__ void __launch_bounds__(256) lift_kernel(const __grid_constant__ Table
 }
 
 // L2 projection of the analytic field (what = 0) or of the forcing (what = 1)
-template <int DIM, int P, int Q>
+template <int DIM, int P, int Q, bool CV>
 __global__ void __launch_bounds__(256) project_kernel(const __grid_constant__ Tables tab,
                                                       const __grid_constant__ Phys ph,
-                                                      const ElemGeo* __restrict__ geo, int E,
+                                                      const ElemGeo* __restrict__ geo,
+                                                      const __grid_constant__ GenGeo gg, int E,
                                                       int what, double t,
                                                       double* __restrict__ out) {
   using C = Cfg<DIM, P, Q>;
@@ -396,14 +604,19 @@ __global__ void __launch_bounds__(256) project_kernel(const __grid_constant__ Ta
 #pragma unroll
     for (int vv = 0; vv < NV; ++vv) U[vv] = 0.0;
     if (e < E) {
-      const ElemGeo g = geo[e];
-      int c[3];
-      grid_coords<DIM, Q>(q, c);
       double x[3] = {0, 0, 0};
       double wJ = 1.0;
-      for (int r = 0; r < DIM; ++r) {
-        x[r] = g.x0[r] + 0.5 * (tab.x[c[r]] + 1.0) * g.h[r];
-        wJ *= sw[c[r]] * 0.5 * g.h[r];
+      if constexpr (CV) {
+        for (int r = 0; r < DIM; ++r) x[r] = gg.vx[((long long)e * DIM + r) * NQ + q];
+        wJ = gg.vgeo[((long long)e * (DIM * DIM + 1) + DIM * DIM) * NQ + q];
+      } else {
+        const ElemGeo g = geo[e];
+        int c[3];
+        grid_coords<DIM, Q>(q, c);
+        for (int r = 0; r < DIM; ++r) {
+          x[r] = g.x0[r] + 0.5 * (tab.x[c[r]] + 1.0) * g.h[r];
+          wJ *= sw[c[r]] * 0.5 * g.h[r];
+        }
       }
       if (what == 0)
         exact_state(DIM, ph, x, t, U);
@@ -416,43 +629,67 @@ __global__ void __launch_bounds__(256) project_kernel(const __grid_constant__ Ta
     for (int vv = 0; vv < NV; ++vv) sG[(eb * NV + vv) * NQ + q] = U[vv];
   }
   __syncthreads();
-  bt_minv<DIM, P, Q>(sG, t1, t2, sH, sB, sMi, EPB * NV);
+  if constexpr (CV)
+    bt_only<DIM, P, Q>(sG, t1, t2, sH, sB, EPB * NV);
+  else
+    bt_minv<DIM, P, Q>(sG, t1, t2, sH, sB, sMi, EPB * NV);
   for (int i = threadIdx.x; i < EPB * NV * NM; i += blockDim.x) {
     const int eb = i / (NV * NM);
     const int e = e0 + eb;
     if (e >= E) continue;
-    const double idet = geo[e].idet;
-    out[(long long)e * NV * NM + (i - eb * NV * NM)] = sH[i] * idet;
+    double val;
+    if constexpr (CV) {
+      const int m = i % NM;
+      val = dense_minv_row<NM>(gg.minv + (long long)e * NM * NM, m, sH + (i - m));
+    } else {
+      val = sH[i] * geo[e].idet;
+    }
+    out[(long long)e * NV * NM + (i - eb * NV * NM)] = val;
   }
 }
 
 // ---------------------------------------------------------------- launchers
-template <int DIM, int P, int Q>
-static dg_status run_residual(dg_mesh_s* m, const EvalArgs& a, cudaStream_t s) {
+template <int DIM, int P, int Q, bool CV>
+static dg_status run_residual_g(dg_mesh_s* m, const EvalArgs& a, cudaStream_t s) {
   using C = Cfg<DIM, P, Q>;
   const int vepb = m->tune.vol_epb, vnt = m->tune.vol_threads;
   const int lepb = m->tune.lift_epb, lnt = m->tune.lift_threads;
   const size_t vsm = sizeof(double) * C::vol_sm(vepb), lsm = sizeof(double) * C::lift_sm(lepb);
-  DG_CUDA(cudaFuncSetAttribute(vol_kernel<DIM, P, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)vsm));
-  DG_CUDA(cudaFuncSetAttribute(lift_kernel<DIM, P, Q>,
+  const GenGeo gg = gen_geo(m);
+  DG_CUDA(cudaFuncSetAttribute(vol_kernel<DIM, P, Q, CV>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vsm));
+  DG_CUDA(cudaFuncSetAttribute(lift_kernel<DIM, P, Q, CV>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm));
   if (!a.skip_vol) {
-    DG_PROF(K_VOL, s, vol_kernel<DIM, P, Q><<<(m->E + vepb - 1) / vepb, vnt, vsm, s>>>(
-        m->tab, m->phys, m->geo, m->E, a.u, a.v, a.eps, m->hbuf, m->tbuf, vepb));
+    DG_PROF(K_VOL, s, vol_kernel<DIM, P, Q, CV><<<(m->E + vepb - 1) / vepb, vnt, vsm, s>>>(
+        m->tab, m->phys, m->geo, gg, m->E, a.u, a.v, a.eps, m->hbuf, m->tbuf, vepb));
     DG_LAUNCHED(1);
     const int nfp = m->F * C::NF;
-    DG_PROF(K_FACE, s, face_kernel<DIM, P, Q><<<(nfp + 127) / 128, 128, 0, s>>>(
-        m->tab, m->phys, m->geo, m->faces, m->F, a.t, m->tbuf, m->fbuf));
+    if constexpr (CV) {
+      DG_PROF(K_FACE, s, face_kernel_gen<DIM, P, Q><<<(nfp + 127) / 128, 128, 0, s>>>(
+          m->phys, gg, m->faces, m->F, a.t, m->tbuf, m->fbuf));
+    } else {
+      DG_PROF(K_FACE, s, face_kernel<DIM, P, Q><<<(nfp + 127) / 128, 128, 0, s>>>(
+          m->tab, m->phys, m->geo, m->faces, m->F, a.t, m->tbuf, m->fbuf));
+    }
     DG_LAUNCHED(1);
   }
   if (!a.skip_lift) {
-    DG_PROF(K_LIFT, s, lift_kernel<DIM, P, Q><<<(m->E + lepb - 1) / lepb, lnt, lsm, s>>>(
-        m->tab, m->geo, m->E, m->hbuf, m->fbuf, m->force, a.v, a.r_u, a.eps, a.alpha, a.beta, a.out,
-        lepb));
+    DG_PROF(K_LIFT, s, lift_kernel<DIM, P, Q, CV><<<(m->E + lepb - 1) / lepb, lnt, lsm, s>>>(
+        m->tab, m->geo, gg, m->E, m->hbuf, m->fbuf, m->force, a.v, a.r_u, a.eps, a.alpha, a.beta,
+        a.out, lepb));
     DG_LAUNCHED(1);
   }
   return DG_OK;
+}
+
+template <int DIM, int P, int Q>
+static dg_status run_residual(dg_mesh_s* m, const EvalArgs& a, cudaStream_t s) {
+  if (m->curved) {
+    if constexpr (has_curved<DIM, P, Q>()) return run_residual_g<DIM, P, Q, true>(m, a, s);
+    return DG_ERR_UNSUPPORTED;
+  }
+  return run_residual_g<DIM, P, Q, false>(m, a, s);
 }
 
 template <int DIM, int P, int Q>
@@ -479,22 +716,40 @@ static void tune_candidates(std::vector<int2>& vol, std::vector<int2>& lift) {
     }
 }
 
-template <int DIM, int P, int Q>
-static dg_status run_project(dg_mesh_s* m, int what, double t, double* out, cudaStream_t s) {
+template <int DIM, int P, int Q, bool CV>
+static dg_status run_project_g(dg_mesh_s* m, int what, double t, double* out, cudaStream_t s) {
   using C = Cfg<DIM, P, Q>;
   const int nb = (m->E + C::EPB - 1) / C::EPB;
   const size_t lsm = sizeof(double) * C::LIFT_SM;
-  DG_CUDA(cudaFuncSetAttribute(project_kernel<DIM, P, Q>,
+  DG_CUDA(cudaFuncSetAttribute(project_kernel<DIM, P, Q, CV>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm));
-  DG_PROF(K_PROJECT, s, project_kernel<DIM, P, Q><<<nb, C::NT, lsm, s>>>(m->tab, m->phys, m->geo, m->E, what, t, out));
+  DG_PROF(K_PROJECT, s, project_kernel<DIM, P, Q, CV><<<nb, C::NT, lsm, s>>>(
+      m->tab, m->phys, m->geo, gen_geo(m), m->E, what, t, out));
   DG_LAUNCHED(1);
   return DG_OK;
+}
+
+template <int DIM, int P, int Q>
+static dg_status run_project(dg_mesh_s* m, int what, double t, double* out, cudaStream_t s) {
+  if (m->curved) {
+    if constexpr (has_curved<DIM, P, Q>()) return run_project_g<DIM, P, Q, true>(m, what, t, out, s);
+    return DG_ERR_UNSUPPORTED;
+  }
+  return run_project_g<DIM, P, Q, false>(m, what, t, out, s);
 }
 
 // (dim, P, Q) instances built into the library
 #define DG_INSTANCES(X)                                                                       \
   X(2, 1, 3) X(2, 2, 3) X(2, 2, 4) X(2, 3, 5) X(2, 4, 6) X(2, 5, 7) X(2, 6, 8) X(3, 1, 3) \
   X(3, 2, 4) X(3, 2, 5) X(3, 3, 5) X(3, 3, 6) X(3, 4, 6) X(3, 4, 8)
+
+bool supported_curved(int dim, int P, int Q) {
+#define DG_SUP(D_, P_, Q_) \
+  if (dim == D_ && P == P_ && Q == Q_) return true;
+  DG_CURVED_INSTANCES(DG_SUP)
+#undef DG_SUP
+  return false;
+}
 
 bool supported(int dim, int P, int Q) {
 #define DG_SUP(D_, P_, Q_) \

@@ -30,6 +30,17 @@ struct Cfg {
   static constexpr int lift_sm(int e) { return TAB + e * ((DIM + 1) * NV * NQ + 2 * NV * NQ); }
 };
 
+// (dim, P, Q) instances with general-geometry (curved / rotated) kernels
+#define DG_CURVED_INSTANCES(X) X(2, 2, 4) X(2, 3, 5) X(3, 1, 3) X(3, 2, 5) X(3, 3, 6) X(3, 4, 8)
+template <int D, int P, int Q>
+constexpr bool has_curved() {
+#define DG_HC(D_, P_, Q_) \
+  if (D == D_ && P == P_ && Q == Q_) return true;
+  DG_CURVED_INSTANCES(DG_HC)
+#undef DG_HC
+  return false;
+}
+
 // Y[r][o] = sum_k M[o_ax*MS0 + k*MS1] X[r][i(o, k)] for every replica r
 // (element x variable) and output index o; axis AX changes extent NIN -> NOUT.
 template <int I0, int I1, int I2, int AX, int NOUT, int MS0, int MS1, bool ACC>
