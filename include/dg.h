@@ -85,7 +85,9 @@ enum { DG_FORCING_NONE = 0, DG_FORCING_POISEUILLE = 1 };
  * field / fpar select the analytic field used by dg_project, by Dirichlet
  * and far-field boundaries and by the wall temperature (vortex: u0, v0, phi,
  * xc, yc, scale; Poiseuille: theta, L, dp/dx; uniform: rho, u, v, w, T, or
- * the stream (1, 1, 0, 0, 1) when fpar[0] = 0; cylinder: that stream).
+ * the stream (1, 1, 0, 0, 1) when fpar[0] = 0; cylinder: that stream,
+ * brought to rest at the wall radius fpar[0] by the factor
+ * 1 - exp(-(r - fpar[0]) / fpar[1]) when fpar[1] > 0).
  * bc[i] is the type of boundary i:
  *   DG_BC_DIRICHLET  exterior and viscous state = the analytic field
  *   DG_BC_ISO_WALL   no-slip wall at the analytic wall temperature

@@ -176,6 +176,10 @@ def exact_state(ph, x, t):
             rho = rho * ph.fpar[0]
             vel = np.broadcast_to(np.asarray(ph.fpar[1:1 + d], float), shp + (d,)).copy()
             T = T * ph.fpar[4]
+        if ph.fid == FIELD_CYLINDER and len(ph.fpar) >= 2 and ph.fpar[1] > 0:
+            # stream brought to rest at the wall r = fpar[0] over the length fpar[1]
+            r = np.sqrt(x[..., 0] ** 2 + x[..., 1] ** 2)
+            vel = vel * (1.0 - np.exp(-np.maximum(r - ph.fpar[0], 0.0) / ph.fpar[1]))[..., None]
     elif ph.fid == FIELD_VORTEX:
         # isentropic vortex (Sec. 6.1) on [0,1]^2 = [0,10]^2 scaled by 1/s, with the
         # sign of the u perturbation that makes it a vortex, and T from the radial

@@ -283,6 +283,10 @@ __device__ inline void exact_state(int D, const Phys& ph, const double* x, doubl
     rho = ph.fpar[0];
     for (int k = 0; k < D; ++k) vel[k] = ph.fpar[1 + k];
     temp = ph.fpar[4];
+  } else if (ph.field == DG_FIELD_CYLINDER && ph.fpar[1] > 0.0) {
+    // stream brought to rest at the wall r = fpar[0] over the length fpar[1]
+    const double r = sqrt(x[0] * x[0] + x[1] * x[1]);
+    vel[0] = 1.0 - exp(-fmax(r - ph.fpar[0], 0.0) / ph.fpar[1]);
   } else {  // uniform / cylinder free stream
     vel[0] = 1.0;
   }

@@ -75,6 +75,7 @@ CASES = {
     "cylinder_far_far": lambda: w.small_cylinder_case(2, 6, 1, P=2,
                                                       bc=(w.BC_FARFIELD, w.BC_FARFIELD)),
     "channel_ff_adiabatic": channel_with_new_bcs,
+    "cylinder_wall_layer": lambda: w.small_cylinder_case(3, 8, 2, P=2, wall_layer=0.1),
 }
 
 
@@ -99,7 +100,7 @@ def test_residual_parity_general(dgl, name):
     assert rel(L, L_ref) < max(R_TOL, 64.0 * rounding_floor(dg, u, R_ref, weak=True)), rel(L, L_ref)
 
 
-@pytest.mark.parametrize("name", ["wavy_P3", "cylinder_P2", "rotated_2d_P3"])
+@pytest.mark.parametrize("name", ["wavy_P3", "cylinder_P2", "rotated_2d_P3", "cylinder_wall_layer"])
 def test_projection_parity_general(dgl, name):
     c = case(name)
     dg = DG(c.mesh, c.P, c.Q, c.phys)

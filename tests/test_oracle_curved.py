@@ -247,3 +247,20 @@ def test_adiabatic_wall_carries_no_mass_or_energy_discretely():
         assert np.abs(Hh[..., 0]).max() < 1e-13 * scale
         assert np.abs(Hh[..., -1]).max() < 1e-13 * scale
         assert np.abs(S[..., -1]).max() == 0.0
+
+
+def test_cylinder_wall_layer_field():
+    """The cylinder's initial stream with a wall layer: at rest on the wall,
+    the undisturbed stream far away, monotone in between."""
+    ph = Physics(Ma=0.2, Re=3900.0, fid=phy.FIELD_CYLINDER, fpar=(0.5, 0.1))
+    th = np.linspace(0, 2 * np.pi, 7)
+    for r, expect in ((0.5, 0.0), (20.0, 1.0)):
+        x = np.stack([r * np.cos(th), r * np.sin(th), np.zeros_like(th)], -1)
+        U = phy.exact_state(ph, x, 0.0)
+        assert np.allclose(U[:, 1] / U[:, 0], expect, atol=1e-15) and np.all(U[:, 2:4] == 0)
+    r = np.linspace(0.5, 2.0, 50)
+    x = np.stack([r, np.zeros_like(r), np.zeros_like(r)], -1)
+    u = phy.exact_state(ph, x, 0.0)[:, 1]
+    assert np.all(np.diff(u) > 0)
+    assert np.allclose(u, 1 - np.exp(-(r - 0.5) / 0.1), atol=1e-15)
+

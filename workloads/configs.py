@@ -113,12 +113,15 @@ def small_tgv_case(shape=(4, 3, 2), P=2, Q=None, Re=1600.0, Ma=0.1, riemann=RIEM
     return Case(f"box{shape}_P{P}", m, P, Q, ph)
 
 
-def cylinder_case(n_r=64, n_theta=96, n_z=12, P=3, Q=None, Re=3900.0, Ma=0.2):
+def cylinder_case(n_r=64, n_theta=96, n_z=12, P=3, Q=None, Re=3900.0, Ma=0.2, wall_layer=0.0):
     """Curved O-grid around a unit-diameter cylinder (radius 0.5), outer
-    radius 20, radial growth 1.08, span pi: adiabatic wall and far field."""
+    radius 20, radial growth 1.08, span pi: adiabatic wall and far field.
+    wall_layer > 0 brings the initial stream to rest at the wall over that
+    length (the far-field state is the undisturbed stream)."""
     Q = int(np.ceil(3 * (P + 1) / 2)) if Q is None else Q
     m = ogrid_mesh(n_r, n_theta, n_z, 0.5, 20.0, 1.08, np.pi)
-    ph = Physics(Ma=Ma, Re=Re, fid=FIELD_CYLINDER, bc=[BC_ADIA_WALL, BC_FARFIELD])
+    ph = Physics(Ma=Ma, Re=Re, fid=FIELD_CYLINDER, bc=[BC_ADIA_WALL, BC_FARFIELD],
+                 fpar=(0.5, wall_layer))
     return Case(f"cylinder{n_r}x{n_theta}x{n_z}_P{P}", m, P, Q, ph)
 
 
@@ -168,11 +171,11 @@ def rotated_box_case(shape=(3, 2, 2), P=2, Q=None, order=1, Re=1600.0, Ma=0.1,
 
 
 def small_cylinder_case(n_r=3, n_theta=8, n_z=2, P=2, Q=None, Re=3900.0, Ma=0.2,
-                        r_out=3.0, bc=(BC_ADIA_WALL, BC_FARFIELD)):
+                        r_out=3.0, bc=(BC_ADIA_WALL, BC_FARFIELD), wall_layer=0.0):
     """A coarse O-grid (radius 0.5 to r_out) with the cylinder workload's
     boundary conditions, for parity cases."""
     Q = int(np.ceil(3 * (P + 1) / 2)) if Q is None else Q
     m = ogrid_mesh(n_r, n_theta, n_z, 0.5, r_out, 1.08, np.pi)
-    ph = Physics(Ma=Ma, Re=Re, fid=FIELD_CYLINDER, bc=list(bc))
+    ph = Physics(Ma=Ma, Re=Re, fid=FIELD_CYLINDER, bc=list(bc), fpar=(0.5, wall_layer))
     return Case(f"cylinder{n_r}x{n_theta}x{n_z}_P{P}", m, P, Q, ph)
 
