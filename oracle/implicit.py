@@ -152,8 +152,13 @@ class BRJ:
     terms with the trace-gradient and symmetric-flux Jacobians are neglected.
     """
 
-    def __init__(self, dg, u, t, dt_a, J=7, omega=1.0):
+    assembly_dtype = np.float64
+
+    def __init__(self, dg, u, t, dt_a, J=7, omega=1.0, assembly_dtype=np.float64):
+        """assembly_dtype: precision of the two volume-term contractions (float32
+        measures the rounding floor of a single-precision block assembly)."""
         self.dg, self.J, self.omega, self.dt_a = dg, J, omega, dt_a
+        self.assembly_dtype = assembly_dtype
         d, nv, nm, E = dg.dim, dg.nv, dg.nm, dg.E
         self.nb = nv * nm
         dLdu = self._volume_jacobian(u)                            # [E][v m][l n]
@@ -204,9 +209,10 @@ class BRJ:
         DB = np.einsum("eqrj,rqm->ejqm", dg.ginv, dg.D)
         wJ = dg.wJ
         # volume terms 1 and 2 of Eq. Jacobian-matrix-form2
-        T = np.einsum("eq,ejqm,eqjkl,qn->ekmln", wJ, DB, A0, dg.B, optimize=True)
-        T += np.einsum("eq,ejqm,eqjikl,eiqn->ekmln", wJ, DB, A1, DB, optimize=True)
-        return T.reshape(E, nv * nm, nv * nm)
+        c = lambda a: np.asarray(a, dtype=self.assembly_dtype)
+        T = np.einsum("eq,ejqm,eqjkl,qn->ekmln", c(wJ), c(DB), c(A0), c(dg.B), optimize=True)
+        T += np.einsum("eq,ejqm,eqjikl,eiqn->ekmln", c(wJ), c(DB), c(A1), c(DB), optimize=True)
+        return T.astype(np.float64).reshape(E, nv * nm, nv * nm)
 
     def _flux_only(self, g, QL, QR, dQa, t):
         """H^n on group g as a function of the two traces at fixed gradients;

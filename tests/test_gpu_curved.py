@@ -168,6 +168,12 @@ def test_precond_apply_parity_general(dgl, name, precision, tol):
     dt_a = 0.02
     ref_pc = im.BRJ(dg, u, 0.0, dt_a, J=7)
     q = w.random_direction(u, 3)
+    if precision == "fp32":
+        # the device assembles FP32 blocks: at high order its rounding, after
+        # cancellation in the volume sums, exceeds 1e-4; bound by 4x the
+        # oracle's own float32-assembly difference
+        ref32 = im.BRJ(dg, u, 0.0, dt_a, J=7, assembly_dtype=np.float32).apply(q)
+        tol = max(tol, 4 * rel(ref32, ref_pc.apply(q)))
     pc = dgl.Precond(m).build(to_dev(u), 0.0, dt_a, J=7, precision=precision)
     assert rel(pc.apply(to_dev(q)).cpu().numpy(), ref_pc.apply(q)) < tol
     ref_pc.J = 1

@@ -30,12 +30,15 @@ def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-def test_guess_loss_and_gradients_match_oracle(dgl):
-    c = w.small_tgv_case((3, 2, 2), P=1)
+@pytest.mark.parametrize("P,hidden,shape", [(1, 32, (3, 2, 2)), (3, 256, (6, 5, 5)), (2, 96, (5, 4, 7))])
+def test_guess_loss_and_gradients_match_oracle(dgl, P, hidden, shape):
+    """Tensor-core GEMM tiles of 64/128/256 columns, several row tiles (150
+    and 140 elements > 128), ragged N (40, 135, 320) and split-K weight
+    gradients, all against the oracle MLP with the same BF16 rounding points."""
+    c = w.small_tgv_case(shape, P=P)
     m = dgl.Mesh.from_case(c)
     E, nv, nm = m.shape
     nb = nv * nm
-    hidden = 32
     params = w.mlp_params(3 * nb, hidden, nb, seed=3) + w.mlp_params(3 * nb, hidden, nb, seed=4)
     g = dgl.Guess(m, params, stages=2, hidden=hidden)
     h1, h0, S, u1, u = fields((E, nv, nm), 5, 5)
