@@ -424,6 +424,16 @@ __device__ __forceinline__ void mode_coords(int m, int* mc) {
   mc[2] = DIM == 3 ? m / (N * N) : 0;
 }
 
+// Element block of (k, l) by sum factorisation.  With the per-point weights
+// W_ja(q) (test derivative direction j, trial slot a: value or derivative a-1)
+// and the 1-D tables b (value) and d (derivative) of the modified basis,
+//   X[n][m] = sum_{j,a} sum_q W_ja(q) prod_r f_r(q_r, m_r) g_r(q_r, n_r),
+//   f_r = d if r = j else b,  g_r = d if r = a-1 else b,
+// contracted one Gauss direction at a time: 3-D: q0 (per (j,a)), q1 (per (j,a),
+// accumulated by the factor types of direction 2), q2 (once per type); 2-D:
+// q0 per (j,a) accumulated by the types of direction 1, then q1.  The own-side
+// trace term adds, on each face, the face-slice modes (vertex mode across the
+// face) contracted over the two (one) tangential face-point directions.
 template <int DIM, int P, int Q, typename T, bool CV>
 __global__ void __launch_bounds__(256) brj_block_kernel(
     const __grid_constant__ Tables tab, const ElemGeo* __restrict__ geo,
@@ -432,14 +442,19 @@ __global__ void __launch_bounds__(256) brj_block_kernel(
   using C = Cfg<DIM, P, Q>;
   constexpr int N = C::N, NV = C::NV, NM = C::NM, NQ = C::NQ, NF = C::NF;
   constexpr int NW = DIM * (DIM + 1) * NV * NV;
-  constexpr int TM = 4;                         // output tile TM x TM per thread
-  constexpr int NTILE = (NM + TM - 1) / TM;
+  constexpr int JA = DIM * (DIM + 1);
+  constexpr int N2 = N * N;
+  // 3-D: T1 [N2][Q*Q] per (j,a), T2 [N2*N2][Q] per type; 2-D: T1 [4][N2][Q]
+  constexpr int T1SZ = DIM == 3 ? N2 * Q * Q : 4 * N2 * Q;
+  constexpr int T2SZ = DIM == 3 ? N2 * N2 * Q : 0;
   __shared__ T sB1[Q * N], sD1[Q * N];
   __shared__ double sMi[N * N];
   extern __shared__ unsigned char smraw[];
-  T* X = reinterpret_cast<T*>(smraw);           // [NM (col)][NM (row)]
+  T* X = reinterpret_cast<T*>(smraw);           // [NM (col n)][NM (row m)]
   T* Y = X + NM * NM;
-  T* sW = Y + NM * NM;                          // [NQ][DIM][DIM+1]
+  T* sW = Y + NM * NM;                          // [JA][NQ]; later the dense M^-1
+  T* T1 = sW + (CV && NM * NM > JA * NQ ? NM * NM : JA * NQ);
+  T* T2 = T1 + T1SZ;
   const int el = blockIdx.x, e = e_begin + el;
   const int k = blockIdx.y / NV, l = blockIdx.y % NV;
   for (int i = threadIdx.x; i < Q * N; i += blockDim.x) {
@@ -451,115 +466,153 @@ __global__ void __launch_bounds__(256) brj_block_kernel(
   }
   for (int i = threadIdx.x; i < N * N; i += blockDim.x) sMi[i] = tab.Minv[i];
   const T* We = W + (long long)el * NQ * NW;
-  for (int i = threadIdx.x; i < NQ * DIM * (DIM + 1); i += blockDim.x) {
-    const int q = i / (DIM * (DIM + 1)), ja = i % (DIM * (DIM + 1));
+  for (int i = threadIdx.x; i < NQ * JA; i += blockDim.x) {
+    const int ja = i / NQ, q = i % NQ;
     sW[i] = We[(long long)q * NW + (ja * NV + k) * NV + l];
   }
+  for (int i = threadIdx.x; i < T1SZ + T2SZ; i += blockDim.x) T1[i] = (T)0;
   __syncthreads();
-  for (int tile = threadIdx.x; tile < NTILE * NTILE; tile += blockDim.x) {
-    const int tm = tile / NTILE, tn = tile % NTILE;
-    int mi[TM][3], ni[TM][3];
-    bool mv[TM], nvld[TM];
+  // factor of direction r for test (F) / trial (G) side of combination (j, a)
+  auto ftab = [&](int j, int r) -> const T* { return r == j ? sD1 : sB1; };
+  auto gtab = [&](int a, int r) -> const T* { return r == a - 1 ? sD1 : sB1; };
+  if constexpr (DIM == 3) {
+    // one pass per factor type of direction 2 (f2, g2 in {b, d}): the (j, a)
+    // of that type are contracted over q0 and q1 into T2, then q2 into X
+    for (int i = threadIdx.x; i < NM * NM; i += blockDim.x) X[i] = (T)0;
+    for (int type = 0; type < 4; ++type) {
+      for (int i = threadIdx.x; i < N2 * N2 * Q; i += blockDim.x) T2[i] = (T)0;
+      __syncthreads();
+      for (int ja = 0; ja < JA; ++ja) {
+        const int j = ja / (DIM + 1), a = ja % (DIM + 1);
+        if ((j == 2 ? 2 : 0) + (a == 3 ? 1 : 0) != type) continue;
+        const T* f0 = ftab(j, 0); const T* g0 = gtab(a, 0);
+        const T* f1 = ftab(j, 1); const T* g1 = gtab(a, 1);
+        const T* w = sW + ja * NQ;
+        // contract q0: T1[(m0 + N n0)][q1 + Q q2]
+        for (int i = threadIdx.x; i < N2 * Q * Q; i += blockDim.x) {
+          const int mn = i / (Q * Q), qq = i % (Q * Q);
+          const int m0 = mn % N, n0 = mn / N;
+          T acc = (T)0;
 #pragma unroll
-    for (int a = 0; a < TM; ++a) {
-      const int m = tm * TM + a, n = tn * TM + a;
-      mv[a] = m < NM;
-      nvld[a] = n < NM;
-      mode_coords<DIM, N>(mv[a] ? m : 0, mi[a]);
-      mode_coords<DIM, N>(nvld[a] ? n : 0, ni[a]);
-    }
-    T acc[TM][TM];
-#pragma unroll
-    for (int a = 0; a < TM; ++a)
-#pragma unroll
-      for (int b = 0; b < TM; ++b) acc[a][b] = (T)0;
-    for (int q = 0; q < NQ; ++q) {
-      int c[3];
-      grid_coords<DIM, Q>(q, c);
-      // trial functions (value and reference derivatives) of the tile columns
-      T tr[TM][DIM + 1];
-#pragma unroll
-      for (int b = 0; b < TM; ++b) {
-        T bv[3], dv[3];
-#pragma unroll
-        for (int r = 0; r < DIM; ++r) {
-          bv[r] = sB1[c[r] * N + ni[b][r]];
-          dv[r] = sD1[c[r] * N + ni[b][r]];
+          for (int q0 = 0; q0 < Q; ++q0) acc += f0[q0 * N + m0] * g0[q0 * N + n0] * w[q0 + Q * qq];
+          T1[i] = acc;
         }
-        T prod = bv[0] * bv[1] * (DIM == 3 ? bv[2] : (T)1);
-        tr[b][0] = prod;
-        tr[b][1] = dv[0] * bv[1] * (DIM == 3 ? bv[2] : (T)1);
-        tr[b][2] = bv[0] * dv[1] * (DIM == 3 ? bv[2] : (T)1);
-        if (DIM == 3) tr[b][DIM] = bv[0] * bv[1] * dv[DIM - 1];
+        __syncthreads();
+        // contract q1: T2[((m0 + N n0) N2 + m1 + N n1) Q + q2] +=
+        for (int i = threadIdx.x; i < N2 * N2 * Q; i += blockDim.x) {
+          const int q2 = i % Q, r = i / Q;
+          const int m1 = r % N, n1 = (r / N) % N, mn0 = r / N2;
+          T acc = (T)0;
+#pragma unroll
+          for (int q1 = 0; q1 < Q; ++q1)
+            acc += f1[q1 * N + m1] * g1[q1 * N + n1] * T1[mn0 * Q * Q + q1 + Q * q2];
+          T2[i] += acc;
+        }
+        __syncthreads();
       }
-      // inner sums S_j(n) = sum_a W_ja T_a(n)
-      const T* w = sW + q * DIM * (DIM + 1);
-      T sj[TM][DIM];
+      // contract q2 into X[n][m]
+      const T* f2 = (type & 2) ? sD1 : sB1;
+      const T* g2 = (type & 1) ? sD1 : sB1;
+      for (int i = threadIdx.x; i < NM * NM; i += blockDim.x) {
+        const int n = i / NM, m = i % NM;
+        const int m0 = m % N, m1 = (m / N) % N, m2 = m / N2;
+        const int n0 = n % N, n1 = (n / N) % N, n2 = n / N2;
+        const T* t2 = T2 + ((m0 + N * n0) * N2 + m1 + N * n1) * Q;
+        T acc = (T)0;
 #pragma unroll
-      for (int b = 0; b < TM; ++b)
-#pragma unroll
-        for (int j = 0; j < DIM; ++j) {
-          T s = (T)0;
-#pragma unroll
-          for (int a = 0; a < DIM + 1; ++a) s += w[j * (DIM + 1) + a] * tr[b][a];
-          sj[b][j] = s;
-        }
-      // test-function derivatives of the tile rows
-#pragma unroll
-      for (int a = 0; a < TM; ++a) {
-        T bv[3], dv[3];
-#pragma unroll
-        for (int r = 0; r < DIM; ++r) {
-          bv[r] = sB1[c[r] * N + mi[a][r]];
-          dv[r] = sD1[c[r] * N + mi[a][r]];
-        }
-        T te[DIM];
-        te[0] = dv[0] * bv[1] * (DIM == 3 ? bv[2] : (T)1);
-        te[1] = bv[0] * dv[1] * (DIM == 3 ? bv[2] : (T)1);
-        if (DIM == 3) te[2] = bv[0] * bv[1] * dv[2];
-#pragma unroll
-        for (int b = 0; b < TM; ++b)
-#pragma unroll
-          for (int j = 0; j < DIM; ++j) acc[a][b] += te[j] * sj[b][j];
+        for (int q2 = 0; q2 < Q; ++q2) acc += f2[q2 * N + m2] * g2[q2 * N + n2] * t2[q2];
+        X[i] += acc;
       }
+      __syncthreads();
     }
-    // own-side trace term: sum_faces sum_p Bf(p,m) Jd(p) Bf(p,n)
-    for (int lf = 0; lf < 2 * DIM; ++lf) {
-      const int r = lf >> 1;
-      const int vert = (lf & 1) ? P : 0;
-      const T* jd = Jd + (((long long)e * 2 * DIM + lf) * NF) * NV * NV + k * NV + l;
-      for (int p = 0; p < NF; ++p) {
-        int pc[2] = {p % Q, DIM == 3 ? p / Q : 0};
-        const T jv = jd[(long long)p * NV * NV];
-        T fm[TM], fn[TM];
+  } else {
+    for (int ja = 0; ja < JA; ++ja) {
+      const int j = ja / (DIM + 1), a = ja % (DIM + 1);
+      const T* f0 = ftab(j, 0); const T* g0 = gtab(a, 0);
+      const int type = (j == 1 ? 2 : 0) + (a == 2 ? 1 : 0);
+      const T* w = sW + ja * NQ;
+      // contract q0: T1[type][(m0 + N n0)][q1] +=
+      T* t1 = T1 + type * N2 * Q;
+      for (int i = threadIdx.x; i < N2 * Q; i += blockDim.x) {
+        const int mn = i / Q, q1 = i % Q;
+        const int m0 = mn % N, n0 = mn / N;
+        T acc = (T)0;
 #pragma unroll
-        for (int a = 0; a < TM; ++a) {
-          T vm = mi[a][r] == vert ? (T)1 : (T)0, vn = ni[a][r] == vert ? (T)1 : (T)0;
-          int t = 0;
-#pragma unroll
-          for (int s = 0; s < DIM; ++s) {
-            if (s == r) continue;
-            vm *= sB1[pc[t] * N + mi[a][s]];
-            vn *= sB1[pc[t] * N + ni[a][s]];
-            ++t;
-          }
-          fm[a] = vm;
-          fn[a] = vn * jv;
-        }
-#pragma unroll
-        for (int a = 0; a < TM; ++a)
-#pragma unroll
-          for (int b = 0; b < TM; ++b) acc[a][b] += fm[a] * fn[b];
+        for (int q0 = 0; q0 < Q; ++q0) acc += f0[q0 * N + m0] * g0[q0 * N + n0] * w[q0 + Q * q1];
+        t1[i] += acc;
       }
+      __syncthreads();
     }
-    // X stored column-major per trial mode n: X[n][m]
+    for (int i = threadIdx.x; i < NM * NM; i += blockDim.x) {
+      const int n = i / NM, m = i % NM;
+      const int m0 = m % N, m1 = m / N, n0 = n % N, n1 = n / N;
+      T acc = (T)0;
 #pragma unroll
-    for (int a = 0; a < TM; ++a)
+      for (int type = 0; type < 4; ++type) {
+        const T* f1 = (type & 2) ? sD1 : sB1;
+        const T* g1 = (type & 1) ? sD1 : sB1;
+        const T* t1 = T1 + type * N2 * Q + (m0 + N * n0) * Q;
 #pragma unroll
-      for (int b = 0; b < TM; ++b)
-        if (mv[a] && nvld[b]) X[(tn * TM + b) * NM + tm * TM + a] = acc[a][b];
+        for (int q1 = 0; q1 < Q; ++q1) acc += f1[q1 * N + m1] * g1[q1 * N + n1] * t1[q1];
+      }
+      X[i] = acc;
+    }
   }
   __syncthreads();
+  // own-side trace term, face by face (face-slice modes only)
+  for (int lf = 0; lf < 2 * DIM; ++lf) {
+    const int r = lf >> 1;
+    const int vert = (lf & 1) ? P : 0;
+    const T* jd = Jd + (((long long)e * 2 * DIM + lf) * NF) * NV * NV + k * NV + l;
+    T* sJ = T1;  // [NF] face values, then [N2][Q] partial contraction
+    T* S1 = T1 + NF;
+    for (int p = threadIdx.x; p < NF; p += blockDim.x) sJ[p] = jd[(long long)p * NV * NV];
+    __syncthreads();
+    if constexpr (DIM == 3) {
+      const int t0 = r == 0 ? 1 : 0, t1 = r == 2 ? 1 : 2;
+      // S1[(a0 + N b0)][p1] = sum_p0 b(p0, a0) b(p0, b0) J(p0 + Q p1)
+      for (int i = threadIdx.x; i < N2 * Q; i += blockDim.x) {
+        const int ab = i / Q, p1 = i % Q;
+        const int a0 = ab % N, b0 = ab / N;
+        T acc = (T)0;
+#pragma unroll
+        for (int p0 = 0; p0 < Q; ++p0) acc += sB1[p0 * N + a0] * sB1[p0 * N + b0] * sJ[p0 + Q * p1];
+        S1[i] = acc;
+      }
+      __syncthreads();
+      for (int i = threadIdx.x; i < N2 * N2; i += blockDim.x) {
+        const int a0 = i % N, b0 = (i / N) % N, a1 = (i / N2) % N, b1 = i / (N2 * N);
+        T acc = (T)0;
+#pragma unroll
+        for (int p1 = 0; p1 < Q; ++p1)
+          acc += sB1[p1 * N + a1] * sB1[p1 * N + b1] * S1[(a0 + N * b0) * Q + p1];
+        int mc[3], nc[3];
+        mc[r] = vert;
+        nc[r] = vert;
+        mc[t0] = a0;
+        mc[t1] = a1;
+        nc[t0] = b0;
+        nc[t1] = b1;
+        const int m = mc[0] + N * (mc[1] + N * mc[2]), n = nc[0] + N * (nc[1] + N * nc[2]);
+        X[n * NM + m] += acc;
+      }
+    } else {
+      const int t0 = 1 - r;
+      for (int i = threadIdx.x; i < N2; i += blockDim.x) {
+        const int a0 = i % N, b0 = i / N;
+        T acc = (T)0;
+#pragma unroll
+        for (int p = 0; p < Q; ++p) acc += sB1[p * N + a0] * sB1[p * N + b0] * sJ[p];
+        int mc[2], nc[2];
+        mc[r] = vert;
+        nc[r] = vert;
+        mc[t0] = a0;
+        nc[t0] = b0;
+        X[(nc[0] + N * nc[1]) * NM + mc[0] + N * mc[1]] += acc;
+      }
+    }
+    __syncthreads();
+  }
   T* src = X;
   T* dst = Y;
   if constexpr (CV) {
@@ -1162,7 +1215,9 @@ struct BRJImpl {
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsm));
     // general elements stage the dense M^-1 beside the weights
     const int wsz = NQ * DIM * (DIM + 1);
-    const size_t bsm = sizeof(T) * (2 * NM * NM + (CV && NM * NM > wsz ? NM * NM : wsz));
+    constexpr int N2 = C::N * C::N;
+    constexpr int TSZ = DIM == 3 ? N2 * Q * Q + N2 * N2 * Q : 4 * N2 * Q;
+    const size_t bsm = sizeof(T) * (2 * NM * NM + (CV && NM * NM > wsz ? NM * NM : wsz) + TSZ);
     DG_CUDA(cudaFuncSetAttribute(brj_block_kernel<DIM, P, Q, T, CV>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm));
     const int CH = pc->wchunk;
