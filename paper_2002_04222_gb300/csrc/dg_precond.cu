@@ -9,15 +9,17 @@
 //                       the numerical flux in each trace variable (boundary
 //                       states re-evaluated), chi_k = sqrt(eps)||u_k||;
 //   brj_block_kernel    one block per (element, variable pair): the volume
-//                       terms sum_q (D_j B)^T W (B; D_i B) plus the own-side
-//                       trace term B_f^T J B_f, then D = I - dt_a M^-1 X;
-//   brj_invert_kernel   in-place Gauss-Jordan inversion with partial pivoting
-//                       of every diagonal block.
+//                       terms sum_q (D_j B)^T W (B; D_i B) by sum factorisation
+//                       plus the own-side trace term B_f^T J B_f, then
+//                       D = I - dt_a M^-1 X, stored transposed;
+//   brj_invert_blocked_kernel  blocked in-place Gauss-Jordan inversion with
+//                       partial pivoting of every diagonal block.
 // Apply (Eq. precond-Jacobi): q^1 = D^-1 q; q^j = D^-1 (q - (L+U) q^(j-1)), the
 // off-diagonal product formed on the fly from the neighbour traces and the
 // stored neighbour trace Jacobians (brj_offdiag_kernel, which also evaluates the
 // neighbour traces),
-// the block product by brj_diag_kernel (HBM-bound batched GEMV).
+// the block product by brj_diag_cm_kernel (HBM-bound batched GEMV streaming the
+// transposed blocks column by column).
 #include <cmath>
 #include <cstring>
 #include <cuda_bf16.h>
@@ -670,89 +672,6 @@ __global__ void __launch_bounds__(256) brj_block_kernel(
 }
 
 // ------------------------------------------------------------ inversion
-// In-place Gauss-Jordan inversion with partial pivoting of the nb x nb block
-// of each element (row stride ld); singular blocks set *fail.
-template <typename T>
-__global__ void __launch_bounds__(512) brj_invert_kernel(T* __restrict__ blocks, int nb, int ld,
-                                                         int* __restrict__ fail) {
-  extern __shared__ unsigned char smraw[];
-  T* col = reinterpret_cast<T*>(smraw);   // [nb] pivot column
-  T* row = col + nb;                      // [nb] pivot row
-  int* perm = reinterpret_cast<int*>(row + nb);
-  __shared__ T redv[512];
-  __shared__ int redi[512];
-  T* A = blocks + (long long)blockIdx.x * nb * ld;
-  for (int kk = 0; kk < nb; ++kk) {
-    // pivot search (largest magnitude, smallest index on ties)
-    T best = (T)-1;
-    int bi = kk;
-    for (int i = kk + threadIdx.x; i < nb; i += blockDim.x) {
-      T v = fabs(A[(long long)i * ld + kk]);
-      if (v > best) {
-        best = v;
-        bi = i;
-      }
-    }
-    redv[threadIdx.x] = best;
-    redi[threadIdx.x] = bi;
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-      if (threadIdx.x < s) {
-        T o = redv[threadIdx.x + s];
-        int oi = redi[threadIdx.x + s];
-        if (o > redv[threadIdx.x] || (o == redv[threadIdx.x] && oi < redi[threadIdx.x])) {
-          redv[threadIdx.x] = o;
-          redi[threadIdx.x] = oi;
-        }
-      }
-      __syncthreads();
-    }
-    const int pr = redi[0];
-    const T pmag = redv[0];
-    __syncthreads();
-    if (threadIdx.x == 0) perm[kk] = pr;
-    if (!(pmag > (T)0)) {
-      if (threadIdx.x == 0) atomicExch(fail, 1);
-      return;
-    }
-    if (pr != kk)
-      for (int j = threadIdx.x; j < nb; j += blockDim.x) {
-        T a = A[(long long)kk * ld + j];
-        A[(long long)kk * ld + j] = A[(long long)pr * ld + j];
-        A[(long long)pr * ld + j] = a;
-      }
-    __syncthreads();
-    const T piv = A[(long long)kk * ld + kk];
-    const T ipiv = (T)1 / piv;
-    for (int j = threadIdx.x; j < nb; j += blockDim.x) {
-      T a = j == kk ? ipiv : A[(long long)kk * ld + j] * ipiv;
-      row[j] = a;
-      col[j] = A[(long long)j * ld + kk];
-    }
-    __syncthreads();
-    for (int j = threadIdx.x; j < nb; j += blockDim.x) A[(long long)kk * ld + j] = row[j];
-    for (int i2 = threadIdx.x; i2 < (nb - 1) * nb; i2 += blockDim.x) {
-      int i = i2 / nb, j = i2 % nb;
-      if (i >= kk) ++i;  // skip the pivot row
-      const T f = col[i];
-      T a = j == kk ? (T)0 : A[(long long)i * ld + j];
-      A[(long long)i * ld + j] = a - f * row[j];
-    }
-    __syncthreads();
-  }
-  // undo the row interchanges by column swaps in reverse order
-  for (int kk = nb - 1; kk >= 0; --kk) {
-    const int pr = perm[kk];
-    if (pr != kk)
-      for (int i = threadIdx.x; i < nb; i += blockDim.x) {
-        T a = A[(long long)i * ld + kk];
-        A[(long long)i * ld + kk] = A[(long long)i * ld + pr];
-        A[(long long)i * ld + pr] = a;
-      }
-    __syncthreads();
-  }
-}
-
 // Blocked in-place Gauss-Jordan inversion with partial pivoting, one block per
 // element.  Pivot columns K = [k0, k0+B) are processed as a panel held in
 // shared memory (row interchanges applied to whole rows at once); afterwards
@@ -761,7 +680,7 @@ __global__ void __launch_bounds__(512) brj_invert_kernel(T* __restrict__ blocks,
 // rank-B update, so the block is read and written once per panel instead of
 // once per pivot.  The inverse's columns are un-permuted at the end.
 template <typename T, int B>
-__global__ void __launch_bounds__(256) brj_invert_blocked_kernel(T* __restrict__ blocks, int nb,
+__global__ void __launch_bounds__(512) brj_invert_blocked_kernel(T* __restrict__ blocks, int nb,
                                                                  int ld, int* __restrict__ fail) {
   extern __shared__ unsigned char smraw[];
   T* P = reinterpret_cast<T*>(smraw);     // [nb][B] panel
@@ -769,8 +688,9 @@ __global__ void __launch_bounds__(256) brj_invert_blocked_kernel(T* __restrict__
   T* prow = Ak + (size_t)B * nb;          // [B] scaled pivot row of the panel
   T* fcol = prow + B;                     // [nb] multipliers
   int* perm = reinterpret_cast<int*>(fcol + nb);
-  __shared__ T redv[256];
-  __shared__ int redi[256];
+  __shared__ T redv[32];
+  __shared__ int redi[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   T* A = blocks + (long long)blockIdx.x * nb * ld;
   for (int k0 = 0; k0 < nb; k0 += B) {
     const int bw = nb - k0 < B ? nb - k0 : B;
@@ -781,6 +701,8 @@ __global__ void __launch_bounds__(256) brj_invert_blocked_kernel(T* __restrict__
     __syncthreads();
     for (int j = 0; j < bw; ++j) {
       const int k = k0 + j;
+      // pivot: largest |P[i][j]|, i >= k (lowest index on ties): warp shuffles,
+      // then one exchange through shared memory
       T best = (T)-1;
       int bi = k;
       for (int i = k + threadIdx.x; i < nb; i += blockDim.x) {
@@ -790,23 +712,30 @@ __global__ void __launch_bounds__(256) brj_invert_blocked_kernel(T* __restrict__
           bi = i;
         }
       }
-      redv[threadIdx.x] = best;
-      redi[threadIdx.x] = bi;
-      __syncthreads();
-      for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) {
-          const T o = redv[threadIdx.x + s];
-          const int oi = redi[threadIdx.x + s];
-          if (o > redv[threadIdx.x] || (o == redv[threadIdx.x] && oi < redi[threadIdx.x])) {
-            redv[threadIdx.x] = o;
-            redi[threadIdx.x] = oi;
-          }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const T ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > best || (ov == best && oi < bi)) {
+          best = ov;
+          bi = oi;
         }
-        __syncthreads();
       }
-      const int pr = redi[0];
-      const T pmag = redv[0];
+      if (lane == 0) {
+        redv[warp] = best;
+        redi[warp] = bi;
+      }
       __syncthreads();
+      T pmag = redv[0];
+      int pr = redi[0];
+      for (int w = 1; w < nwarp; ++w) {
+        const T ov = redv[w];
+        const int oi = redi[w];
+        if (ov > pmag || (ov == pmag && oi < pr)) {
+          pmag = ov;
+          pr = oi;
+        }
+      }
       if (!(pmag > (T)0)) {
         if (threadIdx.x == 0) atomicExch(fail, 1);
         return;
@@ -848,19 +777,31 @@ __global__ void __launch_bounds__(256) brj_invert_blocked_kernel(T* __restrict__
       Ak[i] = (j < bw && (c < k0 || c >= k0 + bw)) ? A[(long long)(k0 + j) * ld + c] : (T)0;
     }
     __syncthreads();
-    // A[:, c] += (T_K - E_K) A[K, c] for c outside the panel; panel columns <- T_K
+    // A[:, c] += (T_K - E_K) A[K, c] for c outside the panel, eight rows per
+    // batch of independent loads; panel columns <- T_K
     for (int c = threadIdx.x; c < nb; c += blockDim.x) {
       if (c >= k0 && c < k0 + bw) continue;
       T ak[B];
 #pragma unroll
       for (int j = 0; j < B; ++j) ak[j] = Ak[j * nb + c];
-      for (int i = 0; i < nb; ++i) {
-        const T* u = P + i * B;
-        T acc = A[(long long)i * ld + c];
-        const int dj = i - k0;
+      for (int i0 = 0; i0 < nb; i0 += 8) {
+        T acc[8];
 #pragma unroll
-        for (int j = 0; j < B; ++j) acc += (u[j] - (j == dj ? (T)1 : (T)0)) * ak[j];
-        A[(long long)i * ld + c] = acc;
+        for (int t = 0; t < 8; ++t) acc[t] = i0 + t < nb ? A[(long long)(i0 + t) * ld + c] : (T)0;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          const int i = i0 + t;
+          if (i >= nb) break;
+          const T* u = P + i * B;
+          const int dj = i - k0;
+          T a = acc[t];
+#pragma unroll
+          for (int j = 0; j < B; ++j) a += (u[j] - (j == dj ? (T)1 : (T)0)) * ak[j];
+          acc[t] = a;
+        }
+#pragma unroll
+        for (int t = 0; t < 8; ++t)
+          if (i0 + t < nb) A[(long long)(i0 + t) * ld + c] = acc[t];
       }
     }
     for (int i = threadIdx.x; i < nb * B; i += blockDim.x) {
@@ -912,101 +853,6 @@ __global__ void __launch_bounds__(256) var_norm_kernel(const double* __restrict_
 }
 
 // ------------------------------------------------------------ apply
-// out = omega * D^-1 y + (1 - omega) * qprev  (one warp per row group)
-template <typename TB, typename TA>
-__global__ void __launch_bounds__(256) brj_diag_kernel(const TB* __restrict__ blocks, int nb,
-                                                       int ld, const double* __restrict__ y,
-                                                       const double* __restrict__ qprev,
-                                                       double omega, double* __restrict__ out) {
-  extern __shared__ unsigned char smraw[];
-  TA* sy = reinterpret_cast<TA*>(smraw);
-  const int e = blockIdx.x;
-  for (int i = threadIdx.x; i < nb; i += blockDim.x) sy[i] = (TA)y[(long long)e * nb + i];
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  const TB* A = blocks + (long long)e * nb * ld;
-  for (int rrow = warp; rrow < nb; rrow += nw) {
-    const TB* ar = A + (long long)rrow * ld;
-    TA acc = (TA)0;
-    for (int c = lane; c < nb; c += 32) acc += (TA)ar[c] * sy[c];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) {
-      double v = (double)acc;
-      const long long gi = (long long)e * nb + rrow;
-      out[gi] = omega == 1.0 ? v : omega * v + (1.0 - omega) * qprev[gi];
-    }
-  }
-}
-
-// FP32 blocks and arithmetic, 4 elements per 16-byte load (rows padded to ld)
-__global__ void __launch_bounds__(256) brj_diag_f32_kernel(const float* __restrict__ blocks, int nb,
-                                                           int ld, const double* __restrict__ y,
-                                                           const double* __restrict__ qprev,
-                                                           double omega, double* __restrict__ out) {
-  extern __shared__ unsigned char smraw[];
-  float* sy = reinterpret_cast<float*>(smraw);
-  const int e = blockIdx.x;
-  for (int i = threadIdx.x; i < ld; i += blockDim.x)
-    sy[i] = i < nb ? (float)y[(long long)e * nb + i] : 0.0f;
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  const float* A = blocks + (long long)e * nb * ld;
-  const float4* sy4 = reinterpret_cast<const float4*>(sy);
-  for (int rrow = warp; rrow < nb; rrow += nw) {
-    const float4* ar = reinterpret_cast<const float4*>(A + (long long)rrow * ld);
-    float acc = 0.0f;
-    for (int c4 = lane; c4 < ld / 4; c4 += 32) {
-      const float4 a = __ldcs(ar + c4);
-      const float4 b = sy4[c4];
-      acc = fmaf(a.x, b.x, acc);
-      acc = fmaf(a.y, b.y, acc);
-      acc = fmaf(a.z, b.z, acc);
-      acc = fmaf(a.w, b.w, acc);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) {
-      const long long gi = (long long)e * nb + rrow;
-      out[gi] = omega == 1.0 ? (double)acc : omega * (double)acc + (1.0 - omega) * qprev[gi];
-    }
-  }
-}
-
-// bf16 blocks, FP32 arithmetic, 8 elements per 16-byte load
-__global__ void __launch_bounds__(256) brj_diag_bf16_kernel(
-    const __nv_bfloat16* __restrict__ blocks, int nb, int ld, const double* __restrict__ y,
-    const double* __restrict__ qprev, double omega, double* __restrict__ out) {
-  extern __shared__ unsigned char smraw[];
-  float* sy = reinterpret_cast<float*>(smraw);
-  const int e = blockIdx.x;
-  for (int i = threadIdx.x; i < ld; i += blockDim.x)
-    sy[i] = i < nb ? (float)y[(long long)e * nb + i] : 0.0f;
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  const __nv_bfloat16* A = blocks + (long long)e * nb * ld;
-  for (int rrow = warp; rrow < nb; rrow += nw) {
-    const uint4* ar = reinterpret_cast<const uint4*>(A + (long long)rrow * ld);
-    float acc = 0.0f;
-    for (int c8 = lane; c8 < ld / 8; c8 += 32) {
-      uint4 pk = __ldcs(ar + c8);
-      const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&pk);
-#pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        float2 f = __bfloat1622float2(h2[t]);
-        acc = fmaf(f.x, sy[c8 * 8 + 2 * t], acc);
-        acc = fmaf(f.y, sy[c8 * 8 + 2 * t + 1], acc);
-      }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) {
-      const long long gi = (long long)e * nb + rrow;
-      out[gi] = omega == 1.0 ? (double)acc : omega * (double)acc + (1.0 - omega) * qprev[gi];
-    }
-  }
-}
-
 // y = q - (L+U) qh = q + dt_a M^-1 sum_faces B_f^T (Jo . trace of the neighbour's qh)
 // One block per element: the neighbour face values are evaluated from the
 // neighbour's face-mode coefficients (2-D sum factorisation), multiplied by
@@ -1236,7 +1082,9 @@ struct BRJImpl {
     const size_t ism = sizeof(T) * ((size_t)2 * nb * IB + IB + nb) + sizeof(int) * nb;
     DG_CUDA(cudaFuncSetAttribute(brj_invert_blocked_kernel<T, IB>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism));
-    DG_PROF(K_BRJ_INVERT, s, brj_invert_blocked_kernel<T, IB><<<E, 256, ism, s>>>(blk, nb, ld, fail));
+    // one thread per column of the block (the trailing update's unit of work)
+    const int ith = nb <= 512 ? (nb + 31) / 32 * 32 : 512;
+    DG_PROF(K_BRJ_INVERT, s, brj_invert_blocked_kernel<T, IB><<<E, ith, ism, s>>>(blk, nb, ld, fail));
     DG_LAUNCHED(1);
     if (pc->precision == DG_PREC_BF16) {
       const long long n = (long long)E * nb * ld;
