@@ -46,7 +46,8 @@ struct Prec<float> {
 __host__ __device__ constexpr int round_up8(int x) { return (x + 7) & ~7; }
 
 // ------------------------------------------------------------ weights
-// W[e][q][j][a][k][l], a = 0: w|J| (2/h_j) dH_jk/dQ_l;
+// W[e][k][l][j][a][q] (q fastest: one contiguous slice per variable pair),
+//                       a = 0: w|J| (2/h_j) dH_jk/dQ_l;
 //                       a = 1+i: w|J| (2/h_j)(2/h_i) dH_jk/d(d_i Q_l)
 // General elements (CV): with G[r][j] = d xi_r / d x_j at the point,
 //   a = 0:   w|J| sum_j G[r][j] dH_jk/dQ_l                      (row index r)
@@ -62,6 +63,7 @@ __global__ void __launch_bounds__(256) brj_weights_kernel(const __grid_constant_
   using C = Cfg<DIM, P, Q>;
   constexpr int N = C::N, NV = C::NV, NM = C::NM, NQ = C::NQ, Q2 = C::Q2, N2 = C::N2;
   constexpr int NW = DIM * (DIM + 1) * NV * NV;
+  constexpr int JA = DIM * (DIM + 1);
   extern __shared__ double sm[];
   double* sB = sm;
   double* sD = sB + Q * N;
@@ -112,7 +114,7 @@ __global__ void __launch_bounds__(256) brj_weights_kernel(const __grid_constant_
           dU[j][v] = a;
         }
       }
-      TW* Wq = W + ((long long)el * NQ + q) * NW;
+      TW* Wq = W + (long long)el * NQ * NW + q;  // [(k NV + l) JA + ja][NQ]
       for (int l = 0; l < NV; ++l) {
         Dual Ud[NV];
 #pragma unroll
@@ -134,7 +136,7 @@ __global__ void __launch_bounds__(256) brj_weights_kernel(const __grid_constant_
             double a = 0.0;
 #pragma unroll
             for (int j = 0; j < DIM; ++j) a = fma(gi[r][j], F[j][k].d, a);
-            Wq[((r * (DIM + 1) + 0) * NV + k) * NV + l] = (TW)(wJ * a);
+            Wq[((k * NV + l) * JA + r * (DIM + 1) + 0) * NQ] = (TW)(wJ * a);
           }
         double acc[DIM][DIM][NV];
 #pragma unroll
@@ -169,7 +171,7 @@ __global__ void __launch_bounds__(256) brj_weights_kernel(const __grid_constant_
           for (int s2 = 0; s2 < DIM; ++s2)
 #pragma unroll
             for (int k = 0; k < NV; ++k)
-              Wq[((r * (DIM + 1) + 1 + s2) * NV + k) * NV + l] = (TW)(wJ * acc[r][s2][k]);
+              Wq[((k * NV + l) * JA + r * (DIM + 1) + 1 + s2) * NQ] = (TW)(wJ * acc[r][s2][k]);
       }
     }
     return;
@@ -192,7 +194,7 @@ __global__ void __launch_bounds__(256) brj_weights_kernel(const __grid_constant_
 #pragma unroll
       for (int r = 0; r < DIM; ++r) dU[r][v] = sG[(r * NV + v) * NQ + q] * rh[r];
     }
-    TW* Wq = W + ((long long)el * NQ + q) * NW;
+    TW* Wq = W + (long long)el * NQ * NW + q;  // [(k NV + l) JA + ja][NQ]
     for (int l = 0; l < NV; ++l) {
       Dual Ud[NV];
 #pragma unroll
@@ -211,7 +213,7 @@ __global__ void __launch_bounds__(256) brj_weights_kernel(const __grid_constant_
       for (int j = 0; j < DIM; ++j)
 #pragma unroll
         for (int k = 0; k < NV; ++k)
-          Wq[((j * (DIM + 1) + 0) * NV + k) * NV + l] = (TW)(wJ * rh[j] * F[j][k].d);
+          Wq[((k * NV + l) * JA + j * (DIM + 1) + 0) * NQ] = (TW)(wJ * rh[j] * F[j][k].d);
     }
     for (int i = 0; i < DIM; ++i)
       for (int l = 0; l < NV; ++l) {
@@ -233,7 +235,7 @@ __global__ void __launch_bounds__(256) brj_weights_kernel(const __grid_constant_
         for (int j = 0; j < DIM; ++j)
 #pragma unroll
           for (int k = 0; k < NV; ++k)
-            Wq[((j * (DIM + 1) + 1 + i) * NV + k) * NV + l] = (TW)(-wJ * rh[j] * rh[i] * G[j][k]);
+            Wq[((k * NV + l) * JA + j * (DIM + 1) + 1 + i) * NQ] = (TW)(-wJ * rh[j] * rh[i] * G[j][k]);
       }
   }
 }
@@ -468,10 +470,8 @@ __global__ void __launch_bounds__(256) brj_block_kernel(
   }
   for (int i = threadIdx.x; i < N * N; i += blockDim.x) sMi[i] = tab.Minv[i];
   const T* We = W + (long long)el * NQ * NW;
-  for (int i = threadIdx.x; i < NQ * JA; i += blockDim.x) {
-    const int ja = i / NQ, q = i % NQ;
-    sW[i] = We[(long long)q * NW + (ja * NV + k) * NV + l];
-  }
+  for (int i = threadIdx.x; i < NQ * JA; i += blockDim.x)
+    sW[i] = We[(long long)(k * NV + l) * JA * NQ + i];  // contiguous slice of (k, l)
   for (int i = threadIdx.x; i < T1SZ + T2SZ; i += blockDim.x) T1[i] = (T)0;
   __syncthreads();
   // factor of direction r for test (F) / trial (G) side of combination (j, a)
@@ -982,13 +982,22 @@ __global__ void __launch_bounds__(128) brj_offdiag_kernel(
   __syncthreads();
   if constexpr (CV) {
     // dense inverse mass matrix of the element (symmetric)
+    // (one thread per mode m: each entry of M^-1 is read once for all variables)
     const double* Me = minv + (long long)e * NM * NM;
-    for (int i = threadIdx.x; i < NV * NM; i += blockDim.x) {
-      const int v = i / NM, m = i % NM;
-      TA s2 = (TA)0;
-      for (int kk = 0; kk < NM; ++kk) s2 += (TA)Me[kk * NM + m] * L0[v * NM + kk];
-      const long long gi = (long long)e * NV * NM + i;
-      y[gi] = q[gi] + dta * (double)s2;
+    for (int m = threadIdx.x; m < NM; m += blockDim.x) {
+      TA s2[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) s2[v] = (TA)0;
+      for (int kk = 0; kk < NM; ++kk) {
+        const TA mk = (TA)Me[kk * NM + m];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) s2[v] += mk * L0[v * NM + kk];
+      }
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const long long gi = ((long long)e * NV + v) * NM + m;
+        y[gi] = q[gi] + dta * (double)s2[v];
+      }
     }
     return;
   }
@@ -1154,7 +1163,7 @@ struct Vec16<__nv_bfloat16> {
 };
 
 template <typename TB>
-__global__ void __launch_bounds__(256) brj_diag_cm_kernel(const TB* __restrict__ blocks, int nb,
+__global__ void __launch_bounds__(512) brj_diag_cm_kernel(const TB* __restrict__ blocks, int nb,
                                                           int ld, int split,
                                                           const double* __restrict__ y,
                                                           const double* __restrict__ qprev,
@@ -1202,10 +1211,13 @@ static dg_status diag_launch(const void* blocks, int E, int nb, int ld, const do
                              const double* qprev, double omega, double* out, cudaStream_t s) {
   using V = Vec16<TB>;
   const int nrq = ld / V::W;
-  int split = 256 / nrq;
+  // BF16 columns carry half the bytes of FP32 ones: twice the column groups
+  // keep the same number of loads in flight
+  const int budget = sizeof(TB) == 2 ? 512 : 256;
+  int split = budget / nrq;
   if (split < 1) split = 1;
   const int threads = ((nrq * split + 31) / 32) * 32;
-  if (threads > 256 && split == 1) return DG_ERR_UNSUPPORTED;  // ld > 256 W: not built
+  if (threads > 512) return DG_ERR_UNSUPPORTED;  // ld > 512 W: not built
   const size_t sm = sizeof(typename V::TA) * ((size_t)nb + (size_t)split * ld);
   DG_PROF(K_BRJ_DIAG, s, brj_diag_cm_kernel<TB><<<E, threads, sm, s>>>(
       (const TB*)blocks, nb, ld, split, y, qprev, omega, out));
