@@ -40,6 +40,8 @@ WORKLOAD = {"n": 16, "P": 3, "Q": 6, "Re": 1600.0, "Ma": 0.1, "cfl": 0.10, "dt_f
 # synthetic start-up field
 CYLINDER = {"n_r": 64, "n_theta": 96, "n_z": 12, "P": 3, "Q": 6, "Re": 3900.0, "Ma": 0.2,
             "cfl_c": 1.7, "seed": 5, "wall_layer": 0.1, "ramp": (0.25, 0.5)}
+# the same flow at P = 4 on 24^3 hexes (over-integration Q = 8)
+TGV24 = {"n": 24, "P": 4, "Q": 8, "Re": 1600.0, "Ma": 0.1, "cfl": 0.10, "dt_factor": 10.0}
 SAMPLE_N = 3          # CPU sample: the same case on 3^3 elements (same P, Q, CFL)
 FREEZE = 10
 # DRAM bytes (read + write) per element and launch from one ncu capture of the
@@ -172,7 +174,7 @@ def run_ours(args, rank, world):
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
     cyl = args.workload == "cylinder"
-    wl = CYLINDER if cyl else WORKLOAD
+    wl = CYLINDER if cyl else (TGV24 if args.workload == "tgv24" else WORKLOAD)
     if cyl:
         case = w.cylinder_case(wl["n_r"], wl["n_theta"], wl["n_z"], P=wl["P"], Q=wl["Q"],
                                Re=wl["Re"], Ma=wl["Ma"], wall_layer=wl["wall_layer"])
@@ -334,7 +336,7 @@ def run_ours(args, rank, world):
                 "perturbation; start-up ramp dt/4, dt/2 before the warm-up)")
     else:
         metric = ("SDIRK2 step throughput at fixed Newton tolerance (DOF-steps/s); "
-                  "TGV 16^3 hexes P=3, 10x explicit dt")
+                  f"TGV {wl['n']}^3 hexes P={wl['P']}, 10x explicit dt")
         wname = f"tgv{wl['n']}^3_P{wl['P']}_Q{wl['Q']}_sdirk2_dt{wl['dt_factor']:g}xexplicit"
         data = "synthetic (analytic Taylor-Green initial field)"
     out = {
@@ -461,15 +463,17 @@ def main():
                     help="Newton initial guess: S_m, S_m + previous stage increment, or that plus "
                          "the learned MLP correction")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="tgv", choices=["tgv", "cylinder"],
-                    help="tgv: the Taylor-Green benchmark (default); cylinder: the curved O-grid "
-                         "workload (SDIRK3, BF16 blocks, learned guess unless overridden)")
+    ap.add_argument("--workload", default="tgv", choices=["tgv", "tgv24", "cylinder"],
+                    help="tgv: the Taylor-Green benchmark (default, 16^3 P=3); tgv24: 24^3 P=4 "
+                         "Q=8; cylinder: the curved O-grid workload (SDIRK3, BF16 blocks, learned "
+                         "guess unless overridden)")
     ap.add_argument("--elems", type=int, default=WORKLOAD["n"],
                     help="elements per direction (16 = the benchmark; smaller only for profiler captures)")
     args = ap.parse_args()
     WORKLOAD["n"] = args.elems
+    if args.workload != "tgv":
+        args.no_cpu_baseline = True    # the oracle sample is the 16^3 P=3 Taylor-Green case
     if args.workload == "cylinder":
-        args.no_cpu_baseline = True    # the oracle sample is the Taylor-Green case
         if "--precision" not in sys.argv:
             args.precision = "bf16"
         if "--guess" not in sys.argv:

@@ -170,6 +170,10 @@ typedef struct {
   int precision;
   double omega;
   int graphs;
+  int tc_invert; /* FP32 / BF16 modes: run the rank-32 trailing updates of the
+                    block inversion on the tensor cores (TF32 head + tail
+                    products, FP32 accumulation; same result to FP32 rounding;
+                    slower than the default SIMT kernel at P = 3, 4) */
 } dg_prec_cfg;
 
 /* Build (or rebuild in place, when *inout is not NULL and was built for the

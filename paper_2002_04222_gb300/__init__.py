@@ -151,8 +151,8 @@ class Precond:
         self._lib = lib()
 
     def build(self, u, t=0.0, dt_a=0.0, J=7, precision="fp64", omega=1.0, graphs=False,
-              stream=None):
-        cfg = _lib.PrecCfg(J, _lib.PREC[precision], omega, int(graphs))
+              tc_invert=False, stream=None):
+        cfg = _lib.PrecCfg(J, _lib.PREC[precision], omega, int(graphs), int(tc_invert))
         _check("dg_precond_build", self._lib.dg_precond_build(
             self.mesh.handle, _ptr(u), t, dt_a, ctypes.byref(cfg), ctypes.byref(self.handle),
             _stream(stream)))

@@ -24,11 +24,13 @@
 #include <cstring>
 #include <cuda_bf16.h>
 #include <new>
+#include <type_traits>
 #include <vector>
 #include "dg_internal.h"
 #include "dg_physics.cuh"
 #include "dg_precond.h"
 #include "dg_sumfact.cuh"
+#include "dg_tc.cuh"
 
 namespace dg {
 
@@ -852,6 +854,227 @@ __global__ void __launch_bounds__(256) var_norm_kernel(const double* __restrict_
   }
 }
 
+// The same blocked Gauss-Jordan inversion (FP32 blocks) with the trailing
+// rank-32 update A[:, c] += (T_K - E_K) A[K, c] on the tensor cores: tcgen05
+// kind::tf32 products with FP32 accumulation in tensor memory, each operand
+// split into a TF32 head and a TF32 tail (x = hi + lo, hi = x with its 13 low
+// mantissa bits cleared) and the three products hi*hi + hi*lo + lo*hi summed,
+// which keeps the update to FP32 accuracy.  Row tiles of 128 (M) by column
+// chunks of up to 256 (N), K = the 32 panel columns; operands staged by the
+// CTA's threads in the K-major core-matrix layout; the accumulator is read
+// back one row per thread (warps w and w + 4 share the rows of lane quarter
+// w and split the columns) and added to A in global memory.  The panel
+// factorisation is the SIMT code of brj_invert_blocked_kernel.
+constexpr int TCI_B = 32, TCI_N = 256, TCI_WAIT = 1 << 20;
+
+__device__ __forceinline__ void tf32_split(float x, float& hi, float& lo) {
+  hi = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
+  lo = x - hi;
+}
+
+__global__ void __launch_bounds__(256) brj_invert_tc_kernel(float* __restrict__ blocks, int nb,
+                                                            int ld, int* __restrict__ fail) {
+  constexpr int B = TCI_B;
+  constexpr int SBO = (B / 4) * 128;              // TF32 tiles: 8 core matrices along K
+  constexpr int UT = 128 * B * 4, VT = TCI_N * B * 4;
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  uint8_t* Uh = smraw;
+  uint8_t* Ul = Uh + UT;
+  uint8_t* Vh = Ul + UT;
+  uint8_t* Vl = Vh + VT;
+  float* P = reinterpret_cast<float*>(Vl + VT);   // [nb][B] panel
+  float* prow = P + (size_t)nb * B;               // [B]
+  float* fcol = prow + B;                         // [nb]
+  int* perm = reinterpret_cast<int*>(fcol + nb);
+  __shared__ float redv[32];
+  __shared__ int redi[32];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_slot;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+  if (warp == 0) tc::tmem_alloc(&tmem_slot, TCI_N);
+  if (tid == 0) tc::mbar_init(&mbar, 1);
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = tmem_slot;
+  uint32_t phase = 0;
+  bool ok = true;
+  float* A = blocks + (long long)blockIdx.x * nb * ld;
+  for (int k0 = 0; k0 < nb && ok; k0 += B) {
+    const int bw = nb - k0 < B ? nb - k0 : B;
+    for (int i = tid; i < nb * B; i += blockDim.x) {
+      const int r = i / B, j = i % B;
+      P[i] = j < bw ? A[(long long)r * ld + k0 + j] : 0.f;
+    }
+    __syncthreads();
+    for (int j = 0; j < bw; ++j) {
+      const int k = k0 + j;
+      float best = -1.f;
+      int bi = k;
+      for (int i = k + tid; i < nb; i += blockDim.x) {
+        const float v = fabsf(P[i * B + j]);
+        if (v > best) {
+          best = v;
+          bi = i;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > best || (ov == best && oi < bi)) {
+          best = ov;
+          bi = oi;
+        }
+      }
+      if (lane == 0) {
+        redv[warp] = best;
+        redi[warp] = bi;
+      }
+      __syncthreads();
+      float pmag = redv[0];
+      int pr = redi[0];
+      for (int w = 1; w < nwarp; ++w) {
+        const float ov = redv[w];
+        const int oi = redi[w];
+        if (ov > pmag || (ov == pmag && oi < pr)) {
+          pmag = ov;
+          pr = oi;
+        }
+      }
+      if (!(pmag > 0.f)) {  // singular block: leave (uniformly) through the common exit
+        if (tid == 0) atomicExch(fail, 1);
+        ok = false;
+        break;
+      }
+      if (tid == 0) perm[k] = pr;
+      if (pr != k) {
+        for (int jj = tid; jj < B; jj += blockDim.x) {
+          const float a = P[k * B + jj];
+          P[k * B + jj] = P[pr * B + jj];
+          P[pr * B + jj] = a;
+        }
+        for (int c = tid; c < nb; c += blockDim.x) {
+          if (c >= k0 && c < k0 + bw) continue;
+          const float a = A[(long long)k * ld + c];
+          A[(long long)k * ld + c] = A[(long long)pr * ld + c];
+          A[(long long)pr * ld + c] = a;
+        }
+      }
+      __syncthreads();
+      const float ipiv = 1.f / P[k * B + j];
+      for (int jj = tid; jj < B; jj += blockDim.x) prow[jj] = jj == j ? ipiv : P[k * B + jj] * ipiv;
+      for (int i = tid; i < nb; i += blockDim.x) fcol[i] = P[i * B + j];
+      __syncthreads();
+      for (int i2 = tid; i2 < nb * B; i2 += blockDim.x) {
+        const int i = i2 / B, jj = i2 % B;
+        if (i == k) {
+          P[i2] = prow[jj];
+        } else {
+          const float a = jj == j ? 0.f : P[i2];
+          P[i2] = a - fcol[i] * prow[jj];
+        }
+      }
+      __syncthreads();
+    }
+    if (!ok) break;
+    // trailing update on the tensor cores, column chunk by row tile
+    for (int nc0 = 0; nc0 < nb && ok; nc0 += TCI_N) {
+      const int ncols = nb - nc0 < TCI_N ? nb - nc0 : TCI_N;
+      const int nmma = (ncols + 15) / 16 * 16;
+      // V: rows c (outside the panel) x K = old pivot rows A[k0 + j][c]
+      for (int i = tid; i < nmma * B; i += blockDim.x) {
+        const int r = i / B, j = i % B, c = nc0 + r;
+        float x = 0.f;
+        if (c < nb && j < bw && (c < k0 || c >= k0 + bw)) x = A[(long long)(k0 + j) * ld + c];
+        float hi, lo;
+        tf32_split(x, hi, lo);
+        const int off = (r >> 3) * SBO + (j >> 2) * 128 + (r & 7) * 16 + (j & 3) * 4;
+        *reinterpret_cast<float*>(Vh + off) = hi;
+        *reinterpret_cast<float*>(Vl + off) = lo;
+      }
+      for (int rt = 0; rt < nb && ok; rt += 128) {
+        // U: rows i x K = (T_K - E_K)[i][j]
+        for (int i2 = tid; i2 < 128 * B; i2 += blockDim.x) {
+          const int r = i2 / B, j = i2 % B, i = rt + r;
+          float x = 0.f;
+          if (i < nb && j < bw) x = P[i * B + j] - (i == k0 + j ? 1.f : 0.f);
+          float hi, lo;
+          tf32_split(x, hi, lo);
+          const int off = (r >> 3) * SBO + (j >> 2) * 128 + (r & 7) * 16 + (j & 3) * 4;
+          *reinterpret_cast<float*>(Uh + off) = hi;
+          *reinterpret_cast<float*>(Ul + off) = lo;
+        }
+        tc::fence_async_smem();
+        tc::fence_before();
+        __syncthreads();
+        tc::fence_after();
+        if (tid == 0) {
+          const uint32_t id = tc::idesc(2, 128, nmma);
+#pragma unroll
+          for (int ks = 0; ks < B / 8; ++ks) {
+            const uint64_t uh = tc::desc(tc::smem_addr(Uh) + ks * 256, 128, SBO);
+            const uint64_t ul = tc::desc(tc::smem_addr(Ul) + ks * 256, 128, SBO);
+            const uint64_t vh = tc::desc(tc::smem_addr(Vh) + ks * 256, 128, SBO);
+            const uint64_t vl = tc::desc(tc::smem_addr(Vl) + ks * 256, 128, SBO);
+            tc::mma_tf32(tmem, uh, vh, id, ks > 0 ? 1u : 0u);
+            tc::mma_tf32(tmem, uh, vl, id, 1u);
+            tc::mma_tf32(tmem, ul, vh, id, 1u);
+          }
+          tc::commit(&mbar);
+        }
+        const bool w = tc::mbar_wait(&mbar, phase, TCI_WAIT);
+        phase ^= 1u;
+        if (!__syncthreads_and(w)) {
+          if (tid == 0) atomicExch(fail, 2);
+          ok = false;
+          break;
+        }
+        tc::fence_after();
+        // A[i][c] += accumulator, one row per thread; the two warp groups
+        // split the 16-column chunks
+        const int q = warp & 3, grp = warp >> 2, ngrp = nwarp >> 2;
+        const int i = rt + q * 32 + lane;
+        const uint32_t lanes = (uint32_t)(q * 32) << 16;
+        for (int cc = grp * 16; cc < nmma; cc += 16 * ngrp) {
+          float v[16];
+          tc::ld16(tmem + lanes + cc, v);
+          if (i < nb) {
+#pragma unroll
+            for (int t = 0; t < 16; ++t) {
+              const int c = nc0 + cc + t;
+              if (c < nb && (c < k0 || c >= k0 + bw)) A[(long long)i * ld + c] += v[t];
+            }
+          }
+        }
+        tc::fence_before();
+        __syncthreads();  // tiles and accumulator are reused by the next product
+      }
+    }
+    if (!ok) break;
+    for (int i = tid; i < nb * B; i += blockDim.x) {
+      const int r = i / B, j = i % B;
+      if (j < bw) A[(long long)r * ld + k0 + j] = P[i];
+    }
+    __syncthreads();
+  }
+  if (ok) {
+    for (int k = nb - 1; k >= 0; --k) {
+      const int pr = perm[k];
+      if (pr != k)
+        for (int i = tid; i < nb; i += blockDim.x) {
+          const float a = A[(long long)i * ld + k];
+          A[(long long)i * ld + k] = A[(long long)i * ld + pr];
+          A[(long long)i * ld + pr] = a;
+        }
+      __syncthreads();
+    }
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, TCI_N);
+}
+
 // ------------------------------------------------------------ apply
 // y = q - (L+U) qh = q + dt_a M^-1 sum_faces B_f^T (Jo . trace of the neighbour's qh)
 // One block per element: the neighbour face values are evaluated from the
@@ -1088,12 +1311,26 @@ struct BRJImpl {
     int* fail = (int*)(m->scratch + 16);
     DG_CUDA(cudaMemsetAsync(fail, 0, sizeof(int), s));
     constexpr int IB = 32;  // panel width of the blocked inversion
-    const size_t ism = sizeof(T) * ((size_t)2 * nb * IB + IB + nb) + sizeof(int) * nb;
-    DG_CUDA(cudaFuncSetAttribute(brj_invert_blocked_kernel<T, IB>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism));
-    // one thread per column of the block (the trailing update's unit of work)
-    const int ith = nb <= 512 ? (nb + 31) / 32 * 32 : 512;
-    DG_PROF(K_BRJ_INVERT, s, brj_invert_blocked_kernel<T, IB><<<E, ith, ism, s>>>(blk, nb, ld, fail));
+    bool tc_done = false;
+    if constexpr (std::is_same<T, float>::value) {
+      if (pc->tc_invert) {
+      // FP32 blocks (FP32 and BF16 modes): trailing updates on the tensor cores
+      const size_t ism = 2 * (size_t)(128 + TCI_N) * TCI_B * 4 +
+                         sizeof(float) * ((size_t)nb * TCI_B + TCI_B + nb) + sizeof(int) * nb;
+      DG_CUDA(cudaFuncSetAttribute(brj_invert_tc_kernel,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism));
+      DG_PROF(K_BRJ_INVERT, s, brj_invert_tc_kernel<<<E, 256, ism, s>>>(blk, nb, ld, fail));
+      tc_done = true;
+      }
+    }
+    if (!tc_done) {
+      const size_t ism = sizeof(T) * ((size_t)2 * nb * IB + IB + nb) + sizeof(int) * nb;
+      DG_CUDA(cudaFuncSetAttribute(brj_invert_blocked_kernel<T, IB>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism));
+      // one thread per column of the block (the trailing update's unit of work)
+      const int ith = nb <= 512 ? (nb + 31) / 32 * 32 : 512;
+      DG_PROF(K_BRJ_INVERT, s, brj_invert_blocked_kernel<T, IB><<<E, ith, ism, s>>>(blk, nb, ld, fail));
+    }
     DG_LAUNCHED(1);
     if (pc->precision == DG_PREC_BF16) {
       const long long n = (long long)E * nb * ld;
@@ -1464,6 +1701,7 @@ dg_status dg_precond_build(dg_mesh_t m, const double* u, double t, double dt_a,
   // the captured sweeps hold J, omega and the launch shapes: a rebuild re-captures
   precond_drop_graphs(p);
   p->use_graphs = cfg->graphs;
+  p->tc_invert = cfg->tc_invert;
   p->J = cfg->J;
   p->omega = cfg->omega;
   p->dt_a = dt_a;

@@ -27,6 +27,7 @@ struct dg_precond_s {
     long long kernels;     // kernel launches the graph holds
   };
   int use_graphs = 0;
+  int tc_invert = 0;      // FP32 blocks: trailing updates of the inversion on the tensor cores
   std::vector<Graph> graphs;
   cudaStream_t cs = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;

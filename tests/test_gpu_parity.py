@@ -159,7 +159,9 @@ def test_free_stream_and_conservation_on_gpu(dgl):
                                                 ("box_P2_Q4", "fp64", 1e-6),
                                                 ("box_P2_Q4", "fp32", 1e-4),
                                                 ("box_P3_Q6", "bf16", 3e-2),
-                                                ("box_P4_Q8", "fp32", 1e-4)])
+                                                ("box_P4_Q8", "fp32", 1e-4),
+                                                ("box_P3_Q6", "fp32-tc", 1e-4),
+                                                ("box_P4_Q8", "fp32-tc", 1e-4)])
 def test_precond_apply_parity(dgl, name, precision, tol):
     c = CASES[name]()
     dg = DG(c.mesh, c.P, c.Q, c.phys)
@@ -168,6 +170,9 @@ def test_precond_apply_parity(dgl, name, precision, tol):
     dt_a = 0.02
     ref_pc = im.BRJ(dg, u, 0.0, dt_a, J=7)
     q = w.random_direction(u, 3)
+    # "fp32-tc": FP32 blocks inverted with the tensor-core trailing updates
+    tc = precision.endswith("-tc")
+    precision = precision.replace("-tc", "")
     if precision == "fp32":
         # the device assembles FP32 blocks: at high order its rounding, after
         # cancellation in the volume sums, exceeds 1e-4; bound by 4x the
@@ -175,12 +180,12 @@ def test_precond_apply_parity(dgl, name, precision, tol):
         ref32 = im.BRJ(dg, u, 0.0, dt_a, J=7, assembly_dtype=np.float32).apply(q)
         tol = max(tol, 4 * rel(ref32, ref_pc.apply(q)))
     ref = ref_pc.apply(q)
-    pc = dgl.Precond(m).build(to_dev(u), 0.0, dt_a, J=7, precision=precision)
+    pc = dgl.Precond(m).build(to_dev(u), 0.0, dt_a, J=7, precision=precision, tc_invert=tc)
     got = pc.apply(to_dev(q)).cpu().numpy()
     assert rel(got, ref) < tol
     # J = 1 is plain block Jacobi
     ref_pc.J = 1
-    pc1 = dgl.Precond(m).build(to_dev(u), 0.0, dt_a, J=1, precision=precision)
+    pc1 = dgl.Precond(m).build(to_dev(u), 0.0, dt_a, J=1, precision=precision, tc_invert=tc)
     assert rel(pc1.apply(to_dev(q)).cpu().numpy(), ref_pc.apply(q)) < tol
 
 
