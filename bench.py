@@ -368,6 +368,13 @@ def run_ours(args, rank, world):
         "gmres_per_step": sum(gm) / len(gm),
         "residual_gdofs": ndof / (res_ms / 1e3) / 1e9,
         "residual_ms": res_ms,
+        # the preconditioner build inside the profiled steps (one per FREEZE steps):
+        # its kernels' time, and the step time with the build taken out
+        "rebuild_kernels_ms": round(sum(prof[k][1] for k in ("brj_weights", "brj_tracejac",
+                                                             "brj_block", "brj_invert") if k in prof), 3),
+        "ms_per_step_frozen": ms / args.steps - sum(prof[k][1] for k in ("brj_weights", "brj_tracejac",
+                                                                         "brj_block", "brj_invert")
+                                                    if k in prof) / args.steps,
         "gpu_launches": launches,
         "clocks": clk,
         "roofline": roof,
