@@ -198,11 +198,20 @@ dg_status dg_precond_destroy(dg_precond_t p);
  * x0 = 0, Arnoldi by classical Gram-Schmidt applied twice with fixed-order
  * FP64 reductions, Givens rotations, stop when the residual estimate is
  * <= rtol*||b||, at most max_cycles restarts of length restart
- * (1 <= restart <= 64).  p may be NULL (no preconditioner). */
+ * (1 <= restart <= 64).  p may be NULL (no preconditioner).
+ * graphs != 0 launches each Arnoldi step (preconditioner apply, Jacobian-free
+ * product, both Gram-Schmidt passes, the norm and the normalisation) as one
+ * CUDA graph, captured the first time a (step index, restart, u, r_u,
+ * preconditioner) set is seen and replayed afterwards; the results are bitwise
+ * those of graphs = 0.  The mesh handle keeps up to 128 such graphs (the
+ * oldest is dropped), and drops them all when its launch tuning changes or
+ * its Krylov basis is reallocated.  Per-kernel profiling launches plainly.
+ * dg_gmres_noalloc ignores graphs. */
 typedef struct {
   int restart;
   int max_cycles;
   double rtol;
+  int graphs;
 } dg_gmres_cfg;
 typedef struct {
   int iters, cycles, converged;

@@ -96,9 +96,10 @@ class Mesh:
         return out
 
     def gmres(self, u, r_u, b, t=0.0, dt_a=0.0, precond=None, restart=30, max_cycles=10,
-              rtol=5e-2, out=None, stream=None):
+              rtol=5e-2, graphs=False, out=None, stream=None):
+        """dg_gmres; graphs=True replays each Arnoldi step as one CUDA graph."""
         out = self.empty() if out is None else out
-        cfg = _lib.GmresCfg(restart, max_cycles, rtol)
+        cfg = _lib.GmresCfg(restart, max_cycles, rtol, int(graphs))
         st = _lib.GmresStats()
         code = self._lib.dg_gmres(self.handle, precond.handle if precond else None, _ptr(u),
                                   _ptr(r_u), t, dt_a, _ptr(b), _ptr(out), ctypes.byref(cfg),
@@ -125,9 +126,11 @@ class Mesh:
                    guess_train_iters=4, graphs=False, stream=None):
         """One SDIRK step in place on u; `precond` is a Precond holder whose
         handle is built (or reused, frozen) by the library; `guess` an optional
-        Guess (learned initial guess, trained on the converged stages)."""
+        Guess (learned initial guess, trained on the converged stages);
+        graphs=True replays the BRJ applies and the GMRES Arnoldi steps as
+        CUDA graphs."""
         cfg = _lib.SdirkCfg(tableau, alpha, abs_tol, max_newton, int(rebuild), int(use_precond),
-                            _lib.GmresCfg(restart, max_cycles, rtol),
+                            _lib.GmresCfg(restart, max_cycles, rtol, int(graphs)),
                             _lib.PrecCfg(J, _lib.PREC[precision], omega, int(graphs)),
                             guess.handle if guess is not None else None, guess_train_iters)
         st = _lib.StepStats()

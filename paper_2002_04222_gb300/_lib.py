@@ -53,7 +53,8 @@ class PrecCfg(ctypes.Structure):
 
 
 class GmresCfg(ctypes.Structure):
-    _fields_ = [("restart", ctypes.c_int), ("max_cycles", ctypes.c_int), ("rtol", ctypes.c_double)]
+    _fields_ = [("restart", ctypes.c_int), ("max_cycles", ctypes.c_int), ("rtol", ctypes.c_double),
+                ("graphs", ctypes.c_int)]
 
 
 class GmresStats(ctypes.Structure):

@@ -200,4 +200,31 @@ dg_status newton_resid(double* N, const double* u, const double* S, const double
   return DG_OK;
 }
 
+__global__ void set_scalars_kernel(double* __restrict__ d, double a, double b) {
+  d[0] = a;
+  d[1] = b;
+}
+dg_status set_scalars(double* d, double a, double b, cudaStream_t s) {
+  DG_PROF(K_VEC, s, set_scalars_kernel<<<1, 1, 0, s>>>(d, a, b));
+  DG_LAUNCHED(1);
+  return DG_OK;
+}
+
+// the Arnoldi normalisation with the norm read on the device: h = sqrt(*hsq),
+// w = (1/h) w + 0 w as axpby_kernel forms it, skipped when h is 0 or not finite
+__global__ void normalize_dev_kernel(double* __restrict__ w, const double* __restrict__ hsq,
+                                     long long n) {
+  const double h = sqrt(hsq[0]);
+  if (!(h > 0.0) || !isfinite(h)) return;
+  const double a = 1.0 / h;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    w[i] = fma(a, w[i], 0.0 * w[i]);
+}
+dg_status normalize_dev(double* w, const double* hsq, long long n, cudaStream_t s) {
+  DG_PROF(K_VEC, s, normalize_dev_kernel<<<grid_for(n), 256, 0, s>>>(w, hsq, n));
+  DG_LAUNCHED(1);
+  return DG_OK;
+}
+
 }  // namespace dg

@@ -217,6 +217,11 @@ static void build_tables(int P, int Q, Tables& t) {
   for (int k = 0; k < n; ++k) t.dpp[k] = dphi[k];
 }
 
+void drop_arnoldi_graphs(dg_mesh_s* m) {
+  for (auto& g : m->agraphs) cudaGraphExecDestroy(g.exec);
+  m->agraphs.clear();
+}
+
 }  // namespace dg
 
 using namespace dg;
@@ -294,6 +299,8 @@ static void free_mesh(dg_mesh_s* m) {
   cudaFree(m->hdev);
   cudaFree(m->stage);
   if (m->hhost) cudaFreeHost(m->hhost);
+  drop_arnoldi_graphs(m);
+  if (m->gs) cudaStreamDestroy(m->gs);
   delete m;
 }
 
@@ -471,6 +478,7 @@ dg_status dg_autotune(dg_mesh_t m, int reps, dg_tune_result* result, void* strea
   if (!m || !result || reps < 1) return DG_ERR_ARG;
   dg_tune_result r{};
   DG_TRY(autotune(m, reps, &r, (cudaStream_t)stream));
+  drop_arnoldi_graphs(m);  // captured with the previous launch shapes
   *result = r;
   return DG_OK;
 }
@@ -482,6 +490,7 @@ dg_status dg_set_tune(dg_mesh_t m, const dg_tune_result* t) {
   m->tune.vol_threads = t->vol_threads;
   m->tune.lift_epb = t->lift_epb;
   m->tune.lift_threads = t->lift_threads;
+  drop_arnoldi_graphs(m);
   return DG_OK;
 }
 
@@ -520,6 +529,7 @@ dg_status dg_jvp(dg_mesh_t m, const double* u, const double* r_u, double t, cons
 // ---------------------------------------------------------------- GMRES
 static dg_status ensure_krylov(dg_mesh_s* m, int restart) {
   if (m->krylov && m->krylov_m >= restart) return DG_OK;
+  drop_arnoldi_graphs(m);  // they hold the old basis
   cudaFree(m->krylov);  // implicitly synchronises the device
   m->krylov = nullptr;
   const size_t nd = (size_t)m->ndof;
@@ -541,6 +551,85 @@ static dg_status host_norm(dg_mesh_s* m, const double* a, double* out, cudaStrea
 static dg_status apply_A(dg_mesh_s* m, const double* u, const double* r_u, double t, double dta,
                          const double* z, double* out, cudaStream_t s) {
   return dg_jvp(m, u, r_u, t, z, 1.0, -dta, out, s);
+}
+
+// The device work of Arnoldi step k: z_k = P^-1 v_k, w = A z_k by the
+// Jacobian-free product, two classical Gram-Schmidt passes, ||w||^2, the
+// Hessenberg column copied to the pinned host mirror and w normalised with
+// the norm read on the device.  t and -dt_a come from the device scalars
+// dscal, so one captured sequence serves every stage and step.
+static dg_status arnoldi_step_ops(dg_mesh_s* m, dg_precond_s* p, const double* u,
+                                  const double* r_u, const double* dscal, double* V, int k,
+                                  int mr, cudaStream_t s) {
+  const long long n = m->ndof;
+  double* hd = m->hdev;
+  const double* vk = V + (size_t)k * n;
+  const double* zk = vk;
+  if (p) {
+    double* zz = V + (size_t)(mr + 1) * n + (size_t)k * n;
+    DG_TRY(precond_sweeps(p, vk, zz, s));
+    zk = zz;
+  }
+  double* w = V + (size_t)(k + 1) * n;
+  DG_TRY(jvp_eps(u, zk, n, m->red, m->scratch, s));
+  EvalArgs a{};
+  a.u = u;
+  a.v = zk;
+  a.r_u = r_u;
+  a.eps = m->scratch;
+  a.alpha = 1.0;
+  a.dscal = dscal;
+  a.out = w;
+  DG_TRY(launch_residual(m, a, s));
+  DG_TRY(multi_dot(V, k + 1, w, n, m->red, hd, s));
+  DG_TRY(multi_axpy(w, V, k + 1, hd, n, s));
+  DG_TRY(multi_dot(V, k + 1, w, n, m->red, hd + (mr + 2), s));
+  DG_TRY(multi_axpy(w, V, k + 1, hd + (mr + 2), n, s));
+  DG_TRY(dot(w, w, n, m->red, hd + 2 * (mr + 2), s));
+  DG_CUDA(cudaMemcpyAsync(m->hhost, hd, sizeof(double) * 3 * (mr + 2), cudaMemcpyDeviceToHost, s));
+  return normalize_dev(w, hd + 2 * (mr + 2), n, s);
+}
+
+static constexpr size_t kMaxArnoldiGraphs = 2 * MAX_RESTART;
+
+// Launch Arnoldi step k as one graph on s: captured on the mesh's own stream
+// the first time its (k, restart, u, r_u, basis, preconditioner) set is seen,
+// then replayed.  The graph bakes in pointers and launch shapes, which is why
+// they form the key and why a new preconditioner sequence or launch tuning
+// leads to a new capture.
+static dg_status arnoldi_step_graph(dg_mesh_s* m, dg_precond_s* p, const double* u,
+                                    const double* r_u, const double* dscal, double* V, int k,
+                                    int mr, cudaStream_t s) {
+  const unsigned long long pgen = p ? p->gen : 0;
+  for (auto& g : m->agraphs)
+    if (g.k == k && g.mr == mr && g.u == u && g.r_u == r_u && g.V == V && g.p == p && g.pgen == pgen) {
+      __atomic_fetch_add(&g_launches, g.kernels, __ATOMIC_RELAXED);
+      DG_CUDA(cudaGraphLaunch(g.exec, s));
+      return DG_OK;
+    }
+  if (!m->gs) DG_CUDA(cudaStreamCreateWithFlags(&m->gs, cudaStreamNonBlocking));
+  cudaGraph_t graph = nullptr;
+  const long long before = dg_kernel_launches();
+  DG_CUDA(cudaStreamBeginCapture(m->gs, cudaStreamCaptureModeThreadLocal));
+  const dg_status st = arnoldi_step_ops(m, p, u, r_u, dscal, V, k, mr, m->gs);
+  const long long kernels = dg_kernel_launches() - before;  // counted once, by the capture
+  const cudaError_t ce = cudaStreamEndCapture(m->gs, &graph);
+  if (st != DG_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  DG_CUDA(ce);
+  cudaGraphExec_t exec = nullptr;
+  const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  DG_CUDA(ie);
+  if (m->agraphs.size() >= kMaxArnoldiGraphs) {
+    cudaGraphExecDestroy(m->agraphs.front().exec);
+    m->agraphs.erase(m->agraphs.begin());
+  }
+  m->agraphs.push_back({k, mr, u, r_u, V, p, pgen, exec, kernels});
+  DG_CUDA(cudaGraphLaunch(exec, s));
+  return DG_OK;
 }
 
 static dg_status gmres_impl(dg_mesh_s* m, dg_precond_s* p, const double* u, const double* r_u,
@@ -565,6 +654,10 @@ static dg_status gmres_impl(dg_mesh_s* m, dg_precond_s* p, const double* u, cons
   std::vector<double> H((size_t)(mr + 1) * mr), cs(mr), sn(mr), g(mr + 1), y(mr);
   double* hd = m->hdev;
   double* hh = m->hhost;
+  // graph replay of the Arnoldi steps; per-kernel profiling launches plainly
+  const bool use_graph = cfg->graphs && !profiling_on();
+  double* dscal = m->scratch + 8;
+  if (use_graph) DG_TRY(set_scalars(dscal, t, -dta, s));
   for (int cyc = 0; cyc < cfg->max_cycles; ++cyc) {
     double beta;
     if (cyc == 0) {
@@ -587,29 +680,34 @@ static dg_status gmres_impl(dg_mesh_s* m, dg_precond_s* p, const double* u, cons
     int kused = 0;
     bool done = false;
     for (int k = 0; k < mr; ++k) {
-      const double* vk = V + (size_t)k * n;
-      const double* zk = vk;
-      if (p) {
-        double* zz = Z + (size_t)k * n;
-        DG_TRY(precond_apply_impl(p, vk, zz, s));
-        zk = zz;
-      }
       double* w = V + (size_t)(k + 1) * n;
-      DG_TRY(apply_A(m, u, r_u, t, dta, zk, w, s));
+      if (use_graph) {
+        DG_TRY(arnoldi_step_graph(m, p, u, r_u, dscal, V, k, mr, s));
+      } else {
+        const double* vk = V + (size_t)k * n;
+        const double* zk = vk;
+        if (p) {
+          double* zz = Z + (size_t)k * n;
+          DG_TRY(precond_apply_impl(p, vk, zz, s));
+          zk = zz;
+        }
+        DG_TRY(apply_A(m, u, r_u, t, dta, zk, w, s));
+        // classical Gram-Schmidt, applied twice
+        DG_TRY(multi_dot(V, k + 1, w, n, m->red, hd, s));
+        DG_TRY(multi_axpy(w, V, k + 1, hd, n, s));
+        DG_TRY(multi_dot(V, k + 1, w, n, m->red, hd + (mr + 2), s));
+        DG_TRY(multi_axpy(w, V, k + 1, hd + (mr + 2), n, s));
+        DG_TRY(dot(w, w, n, m->red, hd + 2 * (mr + 2), s));
+        DG_CUDA(cudaMemcpyAsync(hh, hd, sizeof(double) * 3 * (mr + 2), cudaMemcpyDeviceToHost, s));
+      }
       S.iters++;
-      // classical Gram-Schmidt, applied twice
-      DG_TRY(multi_dot(V, k + 1, w, n, m->red, hd, s));
-      DG_TRY(multi_axpy(w, V, k + 1, hd, n, s));
-      DG_TRY(multi_dot(V, k + 1, w, n, m->red, hd + (mr + 2), s));
-      DG_TRY(multi_axpy(w, V, k + 1, hd + (mr + 2), n, s));
-      DG_TRY(dot(w, w, n, m->red, hd + 2 * (mr + 2), s));
-      DG_CUDA(cudaMemcpyAsync(hh, hd, sizeof(double) * 3 * (mr + 2), cudaMemcpyDeviceToHost, s));
       DG_CUDA(cudaStreamSynchronize(s));
       const double hn = std::sqrt(hh[2 * (mr + 2)]);
       if (!std::isfinite(hn)) return DG_ERR_NONFINITE;
       for (int i = 0; i <= k; ++i) H[(size_t)i * mr + k] = hh[i] + hh[(mr + 2) + i];
       H[(size_t)(k + 1) * mr + k] = hn;
-      if (hn > 0.0) DG_TRY(axpby(w, 1.0 / hn, w, 0.0, n, s));
+      // (the graph normalised w on the device)
+      if (!use_graph && hn > 0.0) DG_TRY(axpby(w, 1.0 / hn, w, 0.0, n, s));
       for (int i = 0; i < k; ++i) {
         double t0 = cs[i] * H[(size_t)i * mr + k] + sn[i] * H[(size_t)(i + 1) * mr + k];
         H[(size_t)(i + 1) * mr + k] = -sn[i] * H[(size_t)i * mr + k] + cs[i] * H[(size_t)(i + 1) * mr + k];

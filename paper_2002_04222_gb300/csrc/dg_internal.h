@@ -95,8 +95,19 @@ struct dg_mesh_s {
   // SDIRK workspace
   double* stage = nullptr;      // [4 + 3][ndof]: E^0..E^3, S, R, N
   std::vector<std::vector<int>> elem_faces;  // host: face id of (e, lf)
-  // cached norms of the JFNK base point
-  const double* jvp_u = nullptr;
+  // graph replay of GMRES Arnoldi steps (one instantiated graph per step index
+  // and operand set; see gmres_impl)
+  struct ArnoldiGraph {
+    int k, mr;
+    const double *u, *r_u;
+    double* V;
+    const void* p;
+    unsigned long long pgen;
+    cudaGraphExec_t exec;
+    long long kernels;
+  };
+  std::vector<ArnoldiGraph> agraphs;
+  cudaStream_t gs = nullptr;  // capture stream
 };
 
 namespace dg {
@@ -147,6 +158,9 @@ struct EvalArgs {
   double alpha, beta;  // JVP combination
   double t;
   double* out;
+  // optional device scalars {t, beta} read by the kernels in place of t and
+  // beta, so that a captured graph serves every time level and step size
+  const double* dscal = nullptr;
   bool skip_vol = false, skip_lift = false;  // autotuning times the kernels separately
 };
 dg_status launch_residual(dg_mesh_s* m, const EvalArgs& a, cudaStream_t s);
@@ -183,5 +197,9 @@ dg_status jvp_eps(const double* u, const double* v, long long n, double* partial
                   cudaStream_t s);
 dg_status newton_resid(double* N, const double* u, const double* S, const double* R, double dta,
                        long long n, cudaStream_t s);
+dg_status set_scalars(double* d, double a, double b, cudaStream_t s);  // d[0] = a, d[1] = b
+// w = w / sqrt(*hsq) when sqrt(*hsq) > 0 (the same arithmetic as axpby(w, 1/h, w, 0))
+dg_status normalize_dev(double* w, const double* hsq, long long n, cudaStream_t s);
+void drop_arnoldi_graphs(dg_mesh_s* m);
 
 }  // namespace dg

@@ -1523,7 +1523,7 @@ static dg_status dispatch_offdiag(dg_precond_s* pc, const double* qh, const doub
 }
 
 // the J sweeps of Eq. precond-Jacobi as kernel launches on stream s
-static dg_status precond_sweeps(dg_precond_s* pc, const double* q, double* out, cudaStream_t s) {
+dg_status precond_sweeps(dg_precond_s* pc, const double* q, double* out, cudaStream_t s) {
   // sweep 1 from qh = 0: D^-1 q (the relaxation term vanishes)
   double* cur = pc->J == 1 ? out : pc->qh;
   DG_TRY(diag_apply(pc, 1.0, q, nullptr, cur, s));
@@ -1700,6 +1700,9 @@ dg_status dg_precond_build(dg_mesh_t m, const double* u, double t, double dt_a,
   }
   // the captured sweeps hold J, omega and the launch shapes: a rebuild re-captures
   precond_drop_graphs(p);
+  static unsigned long long g_gen = 0;
+  if (p->gen == 0 || p->J != cfg->J || p->omega != cfg->omega)
+    p->gen = __atomic_add_fetch(&g_gen, 1ULL, __ATOMIC_RELAXED);
   p->use_graphs = cfg->graphs;
   p->tc_invert = cfg->tc_invert;
   p->J = cfg->J;

@@ -9,6 +9,9 @@ struct dg_precond_s {
   double omega = 1.0;
   double dt_a = 0.0;
   int nb = 0;             // block size n_var * n_mode
+  // identity of the apply's launch sequence (handle, J, omega): new whenever
+  // they change, so graphs that captured the sweeps know when to re-capture
+  unsigned long long gen = 0;
   void* blocks = nullptr; // [E][nb][nb] inverse diagonal blocks (double, float or bf16)
   void* jd = nullptr;     // [E][2d][nf][nv][nv] own-side trace Jacobians (double or float)
   void* jo = nullptr;     // [E][2d][nf][nv][nv] neighbour trace Jacobians
@@ -35,6 +38,8 @@ struct dg_precond_s {
 
 namespace dg {
 dg_status precond_apply_impl(dg_precond_s* p, const double* q, double* out, cudaStream_t s);
+// the apply as plain kernel launches on s (for capture inside a larger graph)
+dg_status precond_sweeps(dg_precond_s* p, const double* q, double* out, cudaStream_t s);
 void precond_drop_graphs(dg_precond_s* p);
 inline dg_mesh_s* precond_mesh(dg_precond_s* p) { return p->mesh; }
 }  // namespace dg

@@ -239,13 +239,15 @@ __global__ void __launch_bounds__(128) face_kernel(const __grid_constant__ Table
                                                    const __grid_constant__ Phys ph,
                                                    const ElemGeo* __restrict__ geo,
                                                    const int32_t* __restrict__ faces, int F,
-                                                   double t, const double* __restrict__ tbuf,
+                                                   double t, const double* __restrict__ dscal,
+                                                   const double* __restrict__ tbuf,
                                                    double* __restrict__ fbuf) {
   using C = Cfg<DIM, P, Q>;
   constexpr int NV = C::NV, NF = C::NF;
   constexpr int NTR = 2 * DIM * (1 + DIM) * NV * NF;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= F * NF) return;
+  if (dscal) t = dscal[0];
   const int f = idx / NF, p = idx - f * NF;
   const int eL = faces[f * 6 + 0], fL = faces[f * 6 + 1];
   const int eR = faces[f * 6 + 2], fR = faces[f * 6 + 3], bc = faces[f * 6 + 5];
@@ -342,13 +344,15 @@ template <int DIM, int P, int Q>
 __global__ void __launch_bounds__(128) face_kernel_gen(const __grid_constant__ Phys ph,
                                                        const __grid_constant__ GenGeo gg,
                                                        const int32_t* __restrict__ faces, int F,
-                                                       double t, const double* __restrict__ tbuf,
+                                                       double t, const double* __restrict__ dscal,
+                                                       const double* __restrict__ tbuf,
                                                        double* __restrict__ fbuf) {
   using C = Cfg<DIM, P, Q>;
   constexpr int NV = C::NV, NF = C::NF;
   constexpr int NTR = 2 * DIM * (1 + DIM) * NV * NF;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= F * NF) return;
+  if (dscal) t = dscal[0];
   const int f = idx / NF, p = idx - f * NF;
   const int eL = faces[f * 6 + 0], fL = faces[f * 6 + 1];
   const int eR = faces[f * 6 + 2], fR = faces[f * 6 + 3], bc = faces[f * 6 + 5];
@@ -484,8 +488,9 @@ __global__ void __launch_bounds__(256) lift_kernel(const __grid_constant__ Table
                                                    const double* __restrict__ v,
                                                    const double* __restrict__ r_u,
                                                    const double* __restrict__ epsp, double alpha,
-                                                   double beta, double* __restrict__ out,
-                                                   const int EPB) {
+                                                   double beta, const double* __restrict__ dscal,
+                                                   double* __restrict__ out, const int EPB) {
+  if (dscal) beta = dscal[1];
   using C = Cfg<DIM, P, Q>;
   constexpr int N = C::N, NV = C::NV, NM = C::NM, NQ = C::NQ, NF = C::NF;
   constexpr int Q2 = C::Q2;
@@ -667,17 +672,17 @@ static dg_status run_residual_g(dg_mesh_s* m, const EvalArgs& a, cudaStream_t s)
     const int nfp = m->F * C::NF;
     if constexpr (CV) {
       DG_PROF(K_FACE, s, face_kernel_gen<DIM, P, Q><<<(nfp + 127) / 128, 128, 0, s>>>(
-          m->phys, gg, m->faces, m->F, a.t, m->tbuf, m->fbuf));
+          m->phys, gg, m->faces, m->F, a.t, a.dscal, m->tbuf, m->fbuf));
     } else {
       DG_PROF(K_FACE, s, face_kernel<DIM, P, Q><<<(nfp + 127) / 128, 128, 0, s>>>(
-          m->tab, m->phys, m->geo, m->faces, m->F, a.t, m->tbuf, m->fbuf));
+          m->tab, m->phys, m->geo, m->faces, m->F, a.t, a.dscal, m->tbuf, m->fbuf));
     }
     DG_LAUNCHED(1);
   }
   if (!a.skip_lift) {
     DG_PROF(K_LIFT, s, lift_kernel<DIM, P, Q, CV><<<(m->E + lepb - 1) / lepb, lnt, lsm, s>>>(
         m->tab, m->geo, gg, m->E, m->hbuf, m->fbuf, m->force, a.v, a.r_u, a.eps, a.alpha, a.beta,
-        a.out, lepb));
+        a.dscal, a.out, lepb));
     DG_LAUNCHED(1);
   }
   return DG_OK;

@@ -1,8 +1,9 @@
 """Runtime features with no counterpart in the paper, through the C ABI:
-CUDA-graph replay of the BRJ apply and autotuned launch shapes of the
-sum-factorisation kernels.  Both change how the same kernels are launched,
-never their arithmetic, so results must match the plain launches bit for bit
-(and the plain launches match the oracle in test_gpu_parity)."""
+CUDA-graph replay of the BRJ apply and of the GMRES Arnoldi steps, and
+autotuned launch shapes of the sum-factorisation kernels.  They change how the
+same kernels are launched, never their arithmetic, so results must match the
+plain launches bit for bit (and the plain launches match the oracle in
+test_gpu_parity)."""
 import ctypes
 
 import numpy as np
@@ -23,6 +24,18 @@ def dgl():
 
 def to_dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def dirichlet_vortex_case(n=6, P=2):
+    """The advected isentropic vortex on the unit square with weak Dirichlet
+    data from the exact solution on all four sides: the boundary fluxes depend
+    on t, so a graph that kept the t of its capture would be caught."""
+    from workloads.configs import Case
+    lines = [np.linspace(0.0, 1.0, n + 1)] * 2
+    mesh = w.box_mesh(lines, (False, False), side_bc=[0, 0, 0, 0])
+    ph = w.Physics(Re=100.0, fid=w.FIELD_VORTEX, fpar=(1.0, 0.5, 5.0, 0.5, 0.5, 10.0),
+                   bc=[w.BC_DIRICHLET])
+    return Case(f"vortex_dirichlet{n}_P{P}", mesh, P, P + 2, ph)
 
 
 def perturbed(c, seed=0, amp=0.01):
@@ -59,10 +72,59 @@ def test_graph_apply_bitwise(dgl, precision):
         assert torch.equal(o, plain.apply(q))
 
 
-def test_graph_sdirk_bitwise(dgl):
-    """Three SDIRK2 steps of the 8x8 P=2 vortex with the preconditioner frozen
-    after the first: the graph-replayed BRJ gives the same iterates and counts."""
-    c = w.vortex_case(n=8, P=2)
+@pytest.mark.parametrize("precision", [None, "fp32", "bf16"])
+def test_gmres_graph_bitwise(dgl, precision):
+    """GMRES with every Arnoldi step replayed as one graph: the same iterate and
+    statistics as the plain launches, bit for bit, across calls at other t and
+    dt_a (read by the graph from device scalars), with restarts, and with the
+    replayed kernels counted."""
+    c = dirichlet_vortex_case()
+    m = dgl.Mesh.from_case(c)
+    u = to_dev(perturbed(c))
+    b = to_dev(w.random_direction(u.cpu().numpy(), 3))
+    pc = None
+    if precision:
+        pc = dgl.Precond(m).build(u, 0.0, 0.03, J=4, precision=precision)
+    kw = dict(precond=pc, restart=4, max_cycles=12, rtol=1e-6)
+    for t, dta in [(0.0, 0.03), (0.37, 0.05), (0.0, 0.03), (0.37, 0.05)]:
+        r_u = m.residual(u, t)
+        n0 = dgl.kernel_launches()
+        x_plain, st_plain = m.gmres(u, r_u, b, t, dta, graphs=False, **kw)
+        n_plain = dgl.kernel_launches() - n0
+        n0 = dgl.kernel_launches()
+        x_graph, st_graph = m.gmres(u, r_u, b, t, dta, graphs=True, **kw)
+        n_graph = dgl.kernel_launches() - n0
+        torch.cuda.synchronize()
+        assert st_plain["cycles"] > 1, st_plain    # restarts exercised
+        assert st_graph == st_plain, (t, dta)
+        assert torch.equal(x_graph, x_plain), (t, dta, precision)
+        # the graph path adds one launch per solve (the device scalars)
+        assert n_graph == n_plain + 1, (n_graph, n_plain)
+
+
+def test_gmres_graph_follows_a_new_preconditioner(dgl):
+    """A rebuild with another J gives the apply another launch sequence: the
+    Arnoldi graphs captured with the old one are not replayed."""
+    c = dirichlet_vortex_case(n=4)
+    m = dgl.Mesh.from_case(c)
+    u = to_dev(perturbed(c))
+    b = to_dev(w.random_direction(u.cpu().numpy(), 5))
+    r_u = m.residual(u, 0.1)
+    pc = dgl.Precond(m).build(u, 0.1, 0.04, J=2, precision="fp32")
+    for J in (2, 5, 2):
+        pc.build(u, 0.1, 0.04, J=J, precision="fp32")
+        x_plain, st_plain = m.gmres(u, r_u, b, 0.1, 0.04, precond=pc, restart=10, rtol=1e-6)
+        x_graph, st_graph = m.gmres(u, r_u, b, 0.1, 0.04, precond=pc, restart=10, rtol=1e-6,
+                                    graphs=True)
+        assert st_graph == st_plain and torch.equal(x_graph, x_plain), J
+
+
+@pytest.mark.parametrize("case", ["vortex", "vortex_dirichlet"])
+def test_graph_sdirk_bitwise(dgl, case):
+    """Three SDIRK2 steps with the preconditioner frozen after the first: the
+    graph-replayed BRJ applies and Arnoldi steps give the same iterates and
+    counts (on the Dirichlet vortex every stage has another t)."""
+    c = w.vortex_case(n=8, P=2) if case == "vortex" else dirichlet_vortex_case(n=6)
     m = dgl.Mesh.from_case(c)
     u0 = m.project()
     res = []
@@ -95,6 +157,18 @@ def test_graph_bypassed_while_profiling(dgl):
         dgl.profile_enable(False)
     assert "brj_diag" in names and "brj_offdiag" in names
     assert torch.equal(out, pc.apply(q))
+    # GMRES with graphs requested launches plainly while profiling
+    r_u = m.residual(u)
+    dgl.profile_enable(True)
+    try:
+        dgl.profile_read()
+        x, _ = m.gmres(u, r_u, q, 0.0, 0.02, precond=pc, restart=4, max_cycles=1, graphs=True)
+        names = set(dgl.profile_read())
+    finally:
+        dgl.profile_enable(False)
+    assert {"dg_vol", "dg_face", "dg_lift", "multi_dot"} <= names
+    x2, _ = m.gmres(u, r_u, q, 0.0, 0.02, precond=pc, restart=4, max_cycles=1, graphs=True)
+    assert torch.equal(x, x2)
 
 
 @pytest.mark.parametrize("case", ["vortex", "box_P3"])
