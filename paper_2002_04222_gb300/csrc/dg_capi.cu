@@ -656,7 +656,7 @@ static dg_status gmres_impl(dg_mesh_s* m, dg_precond_s* p, const double* u, cons
   double* hh = m->hhost;
   // graph replay of the Arnoldi steps; per-kernel profiling launches plainly
   const bool use_graph = cfg->graphs && !profiling_on();
-  double* dscal = m->scratch + 8;
+  double* dscal = m->scratch + 24;
   if (use_graph) DG_TRY(set_scalars(dscal, t, -dta, s));
   for (int cyc = 0; cyc < cfg->max_cycles; ++cyc) {
     double beta;

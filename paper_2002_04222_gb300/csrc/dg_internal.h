@@ -83,7 +83,8 @@ struct dg_mesh_s {
   double* tbuf = nullptr;       // [E][2dim][(1+dim)nv][nf] face traces
   double* fbuf = nullptr;       // [E][2dim][(1+dim)nv][nf] face fluxes to lift
   double* force = nullptr;      // [ndof] M^-1 B^T wJ f (nullptr when no forcing)
-  double* scratch = nullptr;    // [4] eps, 1/eps, ...
+  double* scratch = nullptr;    // [64]: [0,4) JFNK eps, 1/eps, norms; [8,13) BRJ chi;
+                                //   [16] inversion failure flag; [24,26) GMRES {t, -dt_a}
   double* red = nullptr;        // reduction partials
   double* w1 = nullptr;         // work vectors of ndof
   double* w2 = nullptr;

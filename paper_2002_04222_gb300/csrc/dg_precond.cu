@@ -243,8 +243,9 @@ __global__ void __launch_bounds__(256) brj_weights_kernel(const __grid_constant_
 }
 
 // ------------------------------------------------------------ trace Jacobians
-// Jd[e][lf][p][k][l] = s wJf dH_k/dQ_own,l ; Jo = s wJf dH_k/dQ_nbr,l with
-// s = -1 on the owner (left) side and +1 on the right side.
+// Jd[e][lf][p][k][l] = s wJf dH_k/dQ_own,l ; Jo[e][lf][k][l][p] = s wJf dH_k/dQ_nbr,l
+// with s = -1 on the owner (left) side and +1 on the right side (Jo with the
+// face point fastest, so that the apply's product reads it coalesced).
 template <int DIM, int P, int Q, typename TJ>
 __global__ void __launch_bounds__(128) brj_tracejac_kernel(
     const __grid_constant__ Tables tab, const __grid_constant__ Phys ph,
@@ -306,9 +307,9 @@ __global__ void __launch_bounds__(128) brj_tracejac_kernel(
   double H0[NV], H1[NV], S[DIM][NV];
   numerical_flux<DIM>(QL, QR, bctype, x, t, dQa, r, sgn, beta, ph, H0, S);
   TJ* jdl = Jd + (((long long)eL * 2 * DIM + fL) * NF + p) * NV * NV;
-  TJ* jol = Jo + (((long long)eL * 2 * DIM + fL) * NF + p) * NV * NV;
+  TJ* jol = Jo + ((long long)eL * 2 * DIM + fL) * NV * NV * NF + p;
   TJ* jdr = eR >= 0 ? Jd + (((long long)eR * 2 * DIM + fR) * NF + p) * NV * NV : nullptr;
-  TJ* jor = eR >= 0 ? Jo + (((long long)eR * 2 * DIM + fR) * NF + p) * NV * NV : nullptr;
+  TJ* jor = eR >= 0 ? Jo + ((long long)eR * 2 * DIM + fR) * NV * NV * NF + p : nullptr;
   for (int l = 0; l < NV; ++l) {
     const double h = chi[l];
     const double ih = 1.0 / h;
@@ -320,7 +321,7 @@ __global__ void __launch_bounds__(128) brj_tracejac_kernel(
     for (int k = 0; k < NV; ++k) {
       const double dHdL = (H1[k] - H0[k]) * ih;
       jdl[k * NV + l] = (TJ)(-wJf * dHdL);
-      if (eR >= 0) jor[k * NV + l] = (TJ)(wJf * dHdL);
+      if (eR >= 0) jor[(k * NV + l) * NF] = (TJ)(wJf * dHdL);
     }
     if (eR >= 0) {
 #pragma unroll
@@ -329,12 +330,12 @@ __global__ void __launch_bounds__(128) brj_tracejac_kernel(
 #pragma unroll
       for (int k = 0; k < NV; ++k) {
         const double dHdR = (H1[k] - H0[k]) * ih;
-        jol[k * NV + l] = (TJ)(-wJf * dHdR);
+        jol[(k * NV + l) * NF] = (TJ)(-wJf * dHdR);
         jdr[k * NV + l] = (TJ)(wJf * dHdR);
       }
     } else {
 #pragma unroll
-      for (int k = 0; k < NV; ++k) jol[k * NV + l] = (TJ)0;
+      for (int k = 0; k < NV; ++k) jol[(k * NV + l) * NF] = (TJ)0;
     }
   }
 }
@@ -388,9 +389,9 @@ __global__ void __launch_bounds__(128) brj_tracejac_gen_kernel(
   double H0[NV], H1[NV], S[DIM][NV];
   numerical_flux_n<DIM>(QL, QR, bctype, x, t, dQa, n, beta, ph, H0, S);
   TJ* jdl = Jd + (((long long)eL * 2 * DIM + fL) * NF + p) * NV * NV;
-  TJ* jol = Jo + (((long long)eL * 2 * DIM + fL) * NF + p) * NV * NV;
+  TJ* jol = Jo + ((long long)eL * 2 * DIM + fL) * NV * NV * NF + p;
   TJ* jdr = eR >= 0 ? Jd + (((long long)eR * 2 * DIM + fR) * NF + p) * NV * NV : nullptr;
-  TJ* jor = eR >= 0 ? Jo + (((long long)eR * 2 * DIM + fR) * NF + p) * NV * NV : nullptr;
+  TJ* jor = eR >= 0 ? Jo + ((long long)eR * 2 * DIM + fR) * NV * NV * NF + p : nullptr;
   for (int l = 0; l < NV; ++l) {
     const double h = chi[l];
     const double ih = 1.0 / h;
@@ -402,7 +403,7 @@ __global__ void __launch_bounds__(128) brj_tracejac_gen_kernel(
     for (int k = 0; k < NV; ++k) {
       const double dHdL = (H1[k] - H0[k]) * ih;
       jdl[k * NV + l] = (TJ)(-wJf * dHdL);
-      if (eR >= 0) jor[k * NV + l] = (TJ)(wJf * dHdL);
+      if (eR >= 0) jor[(k * NV + l) * NF] = (TJ)(wJf * dHdL);
     }
     if (eR >= 0) {
 #pragma unroll
@@ -411,12 +412,12 @@ __global__ void __launch_bounds__(128) brj_tracejac_gen_kernel(
 #pragma unroll
       for (int k = 0; k < NV; ++k) {
         const double dHdR = (H1[k] - H0[k]) * ih;
-        jol[k * NV + l] = (TJ)(-wJf * dHdR);
+        jol[(k * NV + l) * NF] = (TJ)(-wJf * dHdR);
         jdr[k * NV + l] = (TJ)(wJf * dHdR);
       }
     } else {
 #pragma unroll
-      for (int k = 0; k < NV; ++k) jol[k * NV + l] = (TJ)0;
+      for (int k = 0; k < NV; ++k) jol[(k * NV + l) * NF] = (TJ)0;
     }
   }
 }
@@ -1077,6 +1078,16 @@ __global__ void __launch_bounds__(256) brj_invert_tc_kernel(float* __restrict__ 
 
 // ------------------------------------------------------------ apply
 // y = q - (L+U) qh = q + dt_a M^-1 sum_faces B_f^T (Jo . trace of the neighbour's qh)
+// Hint that brings the 16-byte-aligned interior of [p, p + bytes) of global
+// memory toward L2 (bulk prefetch: no registers, no shared memory, no wait).
+__device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes) {
+  const size_t g = __cvta_generic_to_global(p);
+  const size_t a = (g + 15) & ~(size_t)15, b = (g + bytes) & ~(size_t)15;
+  if (b > a)
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"((uint32_t)(b - a))
+                 : "memory");
+}
+
 // One block per element: the neighbour face values are evaluated from the
 // neighbour's face-mode coefficients (2-D sum factorisation), multiplied by
 // the stored neighbour trace Jacobians, lifted onto the face modes and
@@ -1097,6 +1108,12 @@ __global__ void __launch_bounds__(128) brj_offdiag_kernel(
   __shared__ TA tr[2 * DIM * NV * NF];            // neighbour face values, then Jo . values
   __shared__ TA L0[NV * NM], L1[NV * NM];
   const int e = blockIdx.x;
+  // the element's neighbour trace Jacobians (one face per thread) and q are
+  // read late; start their way from DRAM now
+  if (threadIdx.x < 2 * DIM)
+    prefetch_l2(Jo + ((long long)e * 2 * DIM + threadIdx.x) * NV * NV * NF, sizeof(TJ) * NV * NV * NF);
+  else if (threadIdx.x == 2 * DIM)
+    prefetch_l2(q + (long long)e * NV * NM, sizeof(double) * NV * NM);
   for (int i = threadIdx.x; i < Q * N; i += blockDim.x) sB[i] = (TA)tab.B[i];
   for (int i = threadIdx.x; i < N * N; i += blockDim.x) sMi[i] = (TA)tab.Minv[i];
   // gather the neighbour's face slice (modes with m_r = vertex of its face)
@@ -1158,10 +1175,10 @@ __global__ void __launch_bounds__(128) brj_offdiag_kernel(
     if (i < 2 * DIM * NV * NF) {
       const int p = i % NF, k = (i / NF) % NV, lf = i / (NF * NV);
       if (nbr[e * 2 * DIM + lf] >= 0) {
-        const TJ* j = Jo + (((long long)e * 2 * DIM + lf) * NF + p) * NV * NV + k * NV;
+        const TJ* j = Jo + (((long long)e * 2 * DIM + lf) * NV + k) * NV * NF + p;
         const TA* t0 = tr + lf * NV * NF + p;
 #pragma unroll
-        for (int l = 0; l < NV; ++l) s2 += (TA)j[l] * t0[l * NF];
+        for (int l = 0; l < NV; ++l) s2 += (TA)j[l * NF] * t0[l * NF];
       }
     }
     prod[t] = s2;
@@ -1173,7 +1190,19 @@ __global__ void __launch_bounds__(128) brj_offdiag_kernel(
     if (i < 2 * DIM * NV * NF) tr[i] = prod[t];
   }
   __syncthreads();
-  // lift onto the face modes of this element
+  if (DIM == 3) {
+    // lift, first tangential direction: ct[lf][v][a][p1] = sum_p0 B[p0][a] tr[lf][v][p0 + Q p1]
+    for (int i = threadIdx.x; i < 2 * DIM * NV * NT; i += blockDim.x) {
+      const int p1 = i % Q, a = (i / Q) % N, fv = i / NT;
+      const TA* c = tr + fv * NF + Q * p1;
+      TA acc = (TA)0;
+#pragma unroll
+      for (int p0 = 0; p0 < Q; ++p0) acc += sB[p0 * N + a] * c[p0];
+      ct[i] = acc;
+    }
+    __syncthreads();
+  }
+  // lift onto the face modes of this element (second tangential direction in 3-D)
   for (int i = threadIdx.x; i < NV * NM; i += blockDim.x) {
     const int v = i / NM, m = i % NM;
     int mc[3];
@@ -1183,21 +1212,17 @@ __global__ void __launch_bounds__(128) brj_offdiag_kernel(
     for (int lf = 0; lf < 2 * DIM; ++lf) {
       const int r = lf >> 1, vert = (lf & 1) ? P : 0;
       if (mc[r] != vert) continue;
-      const TA* c = tr + (lf * NV + v) * NF;
       if (DIM == 2) {
+        const TA* c = tr + (lf * NV + v) * NF;
         const int a = mc[1 - r];
 #pragma unroll
         for (int p = 0; p < Q; ++p) s2 += sB[p * N + a] * c[p];
       } else {
         const int t0 = r == 0 ? 1 : 0, t1 = r == 2 ? 1 : 2;
         const int a = mc[t0], b = mc[t1];
+        const TA* c = ct + (lf * NV + v) * NT + a * Q;
 #pragma unroll
-        for (int p1 = 0; p1 < Q; ++p1) {
-          TA s3 = (TA)0;
-#pragma unroll
-          for (int p0 = 0; p0 < Q; ++p0) s3 += sB[p0 * N + a] * c[p0 + Q * p1];
-          s2 += sB[p1 * N + b] * s3;
-        }
+        for (int p1 = 0; p1 < Q; ++p1) s2 += sB[p1 * N + b] * c[p1];
       }
     }
     L0[i] = s2;

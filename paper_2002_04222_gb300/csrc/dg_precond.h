@@ -14,7 +14,7 @@ struct dg_precond_s {
   unsigned long long gen = 0;
   void* blocks = nullptr; // [E][nb][nb] inverse diagonal blocks (double, float or bf16)
   void* jd = nullptr;     // [E][2d][nf][nv][nv] own-side trace Jacobians (double or float)
-  void* jo = nullptr;     // [E][2d][nf][nv][nv] neighbour trace Jacobians
+  void* jo = nullptr;     // [E][2d][nv][nv][nf] neighbour trace Jacobians (point fastest)
   int32_t* nbr = nullptr; // [E][2d] neighbour (element * 2d + local face) or -1
   double* tr = nullptr;   // [E][2d][nv][nf] face values of the current iterate
   double* qh = nullptr;   // [ndof] iterate
