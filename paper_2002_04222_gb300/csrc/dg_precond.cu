@@ -1390,8 +1390,9 @@ template <>
 struct Vec16<double> {
   static constexpr int W = 2;
   using TA = double;
-  __device__ static void load(const double* p, double* o) {
-    const double2 v = __ldcs(reinterpret_cast<const double2*>(p));
+  using R = double2;  // one 16-byte load
+  __device__ static R ld(const double* p) { return __ldcs(reinterpret_cast<const double2*>(p)); }
+  __device__ static void cvt(const R& v, double* o) {
     o[0] = v.x;
     o[1] = v.y;
   }
@@ -1400,8 +1401,9 @@ template <>
 struct Vec16<float> {
   static constexpr int W = 4;
   using TA = float;
-  __device__ static void load(const float* p, float* o) {
-    const float4 v = __ldcs(reinterpret_cast<const float4*>(p));
+  using R = float4;
+  __device__ static R ld(const float* p) { return __ldcs(reinterpret_cast<const float4*>(p)); }
+  __device__ static void cvt(const R& v, float* o) {
     o[0] = v.x;
     o[1] = v.y;
     o[2] = v.z;
@@ -1412,8 +1414,9 @@ template <>
 struct Vec16<__nv_bfloat16> {
   static constexpr int W = 8;
   using TA = float;
-  __device__ static void load(const __nv_bfloat16* p, float* o) {
-    const uint4 v = __ldcs(reinterpret_cast<const uint4*>(p));
+  using R = uint4;
+  __device__ static R ld(const __nv_bfloat16* p) { return __ldcs(reinterpret_cast<const uint4*>(p)); }
+  __device__ static void cvt(const R& v, float* o) {
     const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
@@ -1424,8 +1427,12 @@ struct Vec16<__nv_bfloat16> {
   }
 };
 
+// FP32/FP64 blocks launch at most 256 threads, BF16 blocks up to 512 (twice the
+// column groups, half the bytes each); registers capped so that 6 and 2 CTAs
+// fit an SM
 template <typename TB>
-__global__ void __launch_bounds__(512) brj_diag_cm_kernel(const TB* __restrict__ blocks, int nb,
+__global__ void __launch_bounds__(sizeof(TB) == 2 ? 512 : 256, sizeof(TB) == 2 ? 2 : 6)
+    brj_diag_cm_kernel(const TB* __restrict__ blocks, int nb,
                                                           int ld, int split,
                                                           const double* __restrict__ y,
                                                           const double* __restrict__ qprev,
@@ -1448,13 +1455,24 @@ __global__ void __launch_bounds__(512) brj_diag_cm_kernel(const TB* __restrict__
   for (int t = 0; t < W; ++t) acc[t] = (TA)0;
   if (sp < split) {
     const TB* A = blocks + (long long)e * nb * ld + rq * W;
-#pragma unroll 4
-    for (int c = c0; c < c1; ++c) {
-      TA a[W];
-      V::load(A + (long long)c * ld, a);
-      const TA yc = sy[c];
+    // U columns per step, their loads issued together; the ragged last step
+    // predicates its loads instead of running a one-load-at-a-time remainder
+    constexpr int U = sizeof(TB) == 2 ? 8 : 4;
+    for (int c = c0; c < c1; c += U) {
+      typename V::R r[U];  // raw 16-byte loads, widened when used
 #pragma unroll
-      for (int t = 0; t < W; ++t) acc[t] += a[t] * yc;
+      for (int u = 0; u < U; ++u)
+        if (c + u < c1) r[u] = V::ld(A + (long long)(c + u) * ld);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (c + u < c1) {
+          TA a[W];
+          V::cvt(r[u], a);
+          const TA yc = sy[c + u];
+#pragma unroll
+          for (int t = 0; t < W; ++t) acc[t] += a[t] * yc;
+        }
+      }
     }
 #pragma unroll
     for (int t = 0; t < W; ++t) part[sp * ld + rq * W + t] = acc[t];
@@ -1479,7 +1497,7 @@ static dg_status diag_launch(const void* blocks, int E, int nb, int ld, const do
   int split = budget / nrq;
   if (split < 1) split = 1;
   const int threads = ((nrq * split + 31) / 32) * 32;
-  if (threads > 512) return DG_ERR_UNSUPPORTED;  // ld > 512 W: not built
+  if (threads > budget) return DG_ERR_UNSUPPORTED;  // ld > budget W: not built
   const size_t sm = sizeof(typename V::TA) * ((size_t)nb + (size_t)split * ld);
   DG_PROF(K_BRJ_DIAG, s, brj_diag_cm_kernel<TB><<<E, threads, sm, s>>>(
       (const TB*)blocks, nb, ld, split, y, qprev, omega, out));
