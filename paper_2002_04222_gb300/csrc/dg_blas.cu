@@ -141,10 +141,14 @@ dg_status lincomb(double* y, const double* x, double a, const double* z, double 
   return DG_OK;
 }
 
-// y = x * s or x / s with s a device scalar
+// y = x * s or x / s with s a device scalar (the reciprocal formed once per
+// block: an FP64 division per thread would cost more than the stream)
 __global__ void scale_dev_kernel(double* __restrict__ y, const double* __restrict__ x,
                                  const double* __restrict__ sdev, int inv, long long n) {
-  const double s = inv ? 1.0 / sdev[0] : sdev[0];
+  __shared__ double ss;
+  if (threadIdx.x == 0) ss = inv ? 1.0 / sdev[0] : sdev[0];
+  __syncthreads();
+  const double s = ss;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
     y[i] = x[i] * s;
@@ -214,9 +218,14 @@ dg_status set_scalars(double* d, double a, double b, cudaStream_t s) {
 // w = (1/h) w + 0 w as axpby_kernel forms it, skipped when h is 0 or not finite
 __global__ void normalize_dev_kernel(double* __restrict__ w, const double* __restrict__ hsq,
                                      long long n) {
-  const double h = sqrt(hsq[0]);
-  if (!(h > 0.0) || !isfinite(h)) return;
-  const double a = 1.0 / h;
+  __shared__ double sa;  // 1/h once per block (FP64 sqrt and division are long sequences)
+  if (threadIdx.x == 0) {
+    const double h = sqrt(hsq[0]);
+    sa = (h > 0.0 && isfinite(h)) ? 1.0 / h : 0.0;
+  }
+  __syncthreads();
+  const double a = sa;
+  if (a == 0.0) return;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
     w[i] = fma(a, w[i], 0.0 * w[i]);
