@@ -1744,7 +1744,9 @@ dg_status dg_precond_build(dg_mesh_t m, const double* u, double t, double dt_a,
   // the captured sweeps hold J, omega and the launch shapes: a rebuild re-captures
   precond_drop_graphs(p);
   static unsigned long long g_gen = 0;
-  if (p->gen == 0 || p->J != cfg->J || p->omega != cfg->omega)
+  // (the sweeps pass J, omega and dt_a by value; everything else by pointer
+  // into buffers that a rebuild refills in place)
+  if (p->gen == 0 || p->J != cfg->J || p->omega != cfg->omega || p->dt_a != dt_a)
     p->gen = __atomic_add_fetch(&g_gen, 1ULL, __ATOMIC_RELAXED);
   p->use_graphs = cfg->graphs;
   p->tc_invert = cfg->tc_invert;

@@ -9,8 +9,8 @@ struct dg_precond_s {
   double omega = 1.0;
   double dt_a = 0.0;
   int nb = 0;             // block size n_var * n_mode
-  // identity of the apply's launch sequence (handle, J, omega): new whenever
-  // they change, so graphs that captured the sweeps know when to re-capture
+  // identity of the apply's launch sequence (handle, J, omega, dt_a): new
+  // whenever one changes, so graphs that captured the sweeps re-capture
   unsigned long long gen = 0;
   void* blocks = nullptr; // [E][nb][nb] inverse diagonal blocks (double, float or bf16)
   void* jd = nullptr;     // [E][2d][nf][nv][nv] own-side trace Jacobians (double or float)

@@ -103,28 +103,35 @@ def test_gmres_graph_bitwise(dgl, precision):
 
 
 def test_gmres_graph_follows_a_new_preconditioner(dgl):
-    """A rebuild with another J gives the apply another launch sequence: the
-    Arnoldi graphs captured with the old one are not replayed."""
+    """A rebuild with another J, omega or dt_a gives the apply another launch
+    sequence (they are kernel arguments): the Arnoldi graphs captured with the
+    old one are not replayed.  A rebuild at the same (J, omega, dt_a) refills
+    the blocks in place and the graphs stay valid."""
     c = dirichlet_vortex_case(n=4)
     m = dgl.Mesh.from_case(c)
     u = to_dev(perturbed(c))
     b = to_dev(w.random_direction(u.cpu().numpy(), 5))
     r_u = m.residual(u, 0.1)
     pc = dgl.Precond(m).build(u, 0.1, 0.04, J=2, precision="fp32")
-    for J in (2, 5, 2):
-        pc.build(u, 0.1, 0.04, J=J, precision="fp32")
-        x_plain, st_plain = m.gmres(u, r_u, b, 0.1, 0.04, precond=pc, restart=10, rtol=1e-6)
-        x_graph, st_graph = m.gmres(u, r_u, b, 0.1, 0.04, precond=pc, restart=10, rtol=1e-6,
+    u2 = to_dev(perturbed(c, seed=7))
+    for J, omega, dta, state in [(2, 1.0, 0.04, u), (5, 1.0, 0.04, u), (5, 1.0, 0.01, u),
+                                 (5, 0.8, 0.01, u), (5, 0.8, 0.01, u2), (2, 1.0, 0.04, u)]:
+        pc.build(state, 0.1, dta, J=J, omega=omega, precision="fp32")
+        x_plain, st_plain = m.gmres(u, r_u, b, 0.1, dta, precond=pc, restart=10, rtol=1e-6)
+        x_graph, st_graph = m.gmres(u, r_u, b, 0.1, dta, precond=pc, restart=10, rtol=1e-6,
                                     graphs=True)
-        assert st_graph == st_plain and torch.equal(x_graph, x_plain), J
+        assert st_graph == st_plain and torch.equal(x_graph, x_plain), (J, omega, dta)
 
 
-@pytest.mark.parametrize("case", ["vortex", "vortex_dirichlet"])
+@pytest.mark.parametrize("case", ["vortex", "vortex_dirichlet", "vortex_ramp"])
 def test_graph_sdirk_bitwise(dgl, case):
-    """Three SDIRK2 steps with the preconditioner frozen after the first: the
+    """Three SDIRK2 steps with the preconditioner frozen after the first (or,
+    for vortex_ramp, rebuilt every step at a growing step size): the
     graph-replayed BRJ applies and Arnoldi steps give the same iterates and
     counts (on the Dirichlet vortex every stage has another t)."""
-    c = w.vortex_case(n=8, P=2) if case == "vortex" else dirichlet_vortex_case(n=6)
+    c = dirichlet_vortex_case(n=6) if case == "vortex_dirichlet" else w.vortex_case(n=8, P=2)
+    ramp = case == "vortex_ramp"
+    dts = [0.005, 0.01, 0.02] if ramp else [0.02] * 3
     m = dgl.Mesh.from_case(c)
     u0 = m.project()
     res = []
@@ -133,8 +140,8 @@ def test_graph_sdirk_bitwise(dgl, case):
         pc = dgl.Precond(m)
         stats = []
         for k in range(3):
-            st = m.sdirk_step(u, 0.02 * k, 0.02, precond=pc, rebuild=(k == 0), restart=20, J=7,
-                              graphs=graphs)
+            st = m.sdirk_step(u, sum(dts[:k]), dts[k], precond=pc, rebuild=(k == 0 or ramp),
+                              restart=20, J=7, graphs=graphs)
             assert st["converged"]
             stats.append((st["stage_newton"], st["stage_gmres"]))
         res.append((u, stats))
