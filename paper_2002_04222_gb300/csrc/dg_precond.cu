@@ -781,7 +781,9 @@ __global__ void __launch_bounds__(512) brj_invert_blocked_kernel(T* __restrict__
     }
     __syncthreads();
     // A[:, c] += (T_K - E_K) A[K, c] for c outside the panel, eight rows per
-    // batch of independent loads; panel columns <- T_K
+    // batch of independent loads: the T_K A[K, c] product in the inner loop,
+    // the E_K A[K, c] term (row K_j loses A[K_j, c]) once per row of the
+    // panel's rows; panel columns <- T_K
     for (int c = threadIdx.x; c < nb; c += blockDim.x) {
       if (c >= k0 && c < k0 + bw) continue;
       T ak[B];
@@ -796,10 +798,11 @@ __global__ void __launch_bounds__(512) brj_invert_blocked_kernel(T* __restrict__
           const int i = i0 + t;
           if (i >= nb) break;
           const T* u = P + i * B;
-          const int dj = i - k0;
           T a = acc[t];
 #pragma unroll
-          for (int j = 0; j < B; ++j) a += (u[j] - (j == dj ? (T)1 : (T)0)) * ak[j];
+          for (int j = 0; j < B; ++j) a += u[j] * ak[j];
+          const int dj = i - k0;
+          if (dj >= 0 && dj < B) a -= Ak[dj * nb + c];
           acc[t] = a;
         }
 #pragma unroll
