@@ -49,6 +49,31 @@ FREEZE = 10
 TRAFFIC_PER_ELEM = {("brj_diag", "fp32", 3, 6): 418_400.0, ("brj_diag", "bf16", 3, 6): 209_770.0}
 
 
+def max_over_ranks(x, world, device="cuda"):
+    """The largest of the ranks' values of x (a duration): the job lasts as long
+    as its slowest replica.  world = 1 returns x without a process group."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier_all(world):
+    """Barrier over the ranks (none for one process)."""
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def job_throughput(units_per_rank, world, seconds):
+    """Whole-job throughput of `world` replicas that each processed
+    units_per_rank units in `seconds` (the max over ranks)."""
+    return world * units_per_rank / seconds
+
+
 def tgv_dt(n, P, Ma, cfl=0.10, factor=10.0):
     """dt = factor x the explicit step of Eq. CFL (c_lambda = 0.2, d_RK = 2) with
     c + |u| = 1/Ma + 1 (T = 1, |u| <= 1 for the Taylor-Green field)."""
@@ -167,7 +192,6 @@ def kernel_work(name, launches, E, nb, prec_bytes, P, Q):
 # ------------------------------------------------------------------ our arm
 def run_ours(args, rank, world):
     import torch
-    import torch.distributed as dist
     import workloads as w
     import paper_2002_04222_gb300 as dgl
 
@@ -226,8 +250,7 @@ def run_ours(args, rank, world):
         state["k"] = 0
 
     def barrier():
-        if world > 1:
-            dist.barrier()
+        barrier_all(world)
 
     for _ in range(args.warmup):
         step(u)
@@ -250,11 +273,8 @@ def run_ours(args, rank, world):
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
     timed_stats = list(stats)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * ndof * args.steps / (ms / 1e3)
+    ms = max_over_ranks(ms, world)
+    value = job_throughput(ndof * args.steps, world, ms / 1e3)
 
     # per-kernel device time over the same number of further steps (CUDA events
     # on the launch stream, recorded by the library)
@@ -316,13 +336,9 @@ def run_ours(args, rank, world):
             step(dev_u)
             host.copy_(dev_u, non_blocking=True)
             torch.cuda.synchronize()
-        el = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([el], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
+        el = max_over_ranks(time.perf_counter() - t0, world)
         nbytes = ndof * 8
-        e2e = {"value": world * ndof * args.steps / el, "unit": "DOF*step/s",
+        e2e = {"value": job_throughput(ndof * args.steps, world, el), "unit": "DOF*step/s",
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
 
     newton = [s["newton_iters"] for s in timed_stats]
