@@ -184,6 +184,14 @@ def kernel_work(name, launches, E, nb, prec_bytes, P, Q):
         return "alu", f[name] * E, "flop"
     if name == "brj_diag":
         return "hbm", E * (nb * nb * prec_bytes + 2 * nb * 8), "byte"
+    if name == "brj_sweep":
+        # the block, the element's 6 neighbour trace Jacobians (5x5 per face
+        # point), q, the own previous iterate and the output, the neighbours'
+        # face-slice coefficients (3-D workloads)
+        sj = 8 if prec_bytes == 8 else 4
+        per = (nb * nb * prec_bytes + 6 * 25 * Q * Q * sj + 3 * nb * 8
+               + 6 * 5 * (P + 1) ** 2 * 8)
+        return "hbm", E * per, "byte"
     if name in ("multi_dot", "multi_axpy", "dot", "vector"):
         return "hbm", None, "byte"
     return None, None, None
@@ -216,7 +224,7 @@ def run_ours(args, rank, world):
     tableau = 3 if cyl else 2
     nstage = tableau
     kw = dict(restart=30, rtol=5e-2, alpha=1e-3, J=7, precision=args.precision, tableau=tableau,
-              graphs=True)
+              graphs=True, fused=args.fused)
     if args.guess != "plain":
         # initial guess S_m + previous stage increment (+ learned MLP correction, one
         # per stage, 2 x 256 hidden, seeded weights with a zero output layer,
@@ -370,7 +378,8 @@ def run_ours(args, rank, world):
         "data": data,
         "config": {"workload": wname,
                    "n_dof": ndof, "dt": dt, "newton_alpha": 1e-3, "gmres": "restart 30, rtol 5e-2",
-                   "precond": f"BRJ(7) {args.precision} blocks, rebuilt every {FREEZE} steps",
+                   "precond": f"BRJ(7) {args.precision} blocks, rebuilt every {FREEZE} steps"
+                              + (", fused sweeps" if args.fused else ""),
                    "initial_guess": {"plain": "S_m (plain)",
                                      "extrap": "S_m + previous stage increment",
                                      "learned": "S_m + previous stage increment + per-element "
@@ -486,6 +495,8 @@ def main():
                     help="Newton initial guess: S_m, S_m + previous stage increment, or that plus "
                          "the learned MLP correction")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fused", action="store_true",
+                    help="BRJ sweeps after the first as one off-diagonal + block kernel each")
     ap.add_argument("--workload", default="tgv", choices=["tgv", "tgv24", "cylinder"],
                     help="tgv: the Taylor-Green benchmark (default, 16^3 P=3); tgv24: 24^3 P=4 "
                          "Q=8; cylinder: the curved O-grid workload (SDIRK3, BF16 blocks, learned "

@@ -174,6 +174,12 @@ typedef struct {
                     block inversion on the tensor cores (TF32 head + tail
                     products, FP32 accumulation; same result to FP32 rounding;
                     slower than the default SIMT kernel at P = 3, 4) */
+  int fused;     /* != 0: each sweep after the first as one kernel that forms
+                    q - (L+U) q^(j-1) of an element in shared memory and
+                    multiplies it by the element's block in the same launch
+                    (J-1 fewer launches and no HBM round trip of the sweep's
+                    right-hand side; bitwise the same result; one more
+                    n_dof-vector of device memory) */
 } dg_prec_cfg;
 
 /* Build (or rebuild in place, when *inout is not NULL and was built for the

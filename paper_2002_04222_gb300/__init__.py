@@ -123,15 +123,17 @@ class Mesh:
     def sdirk_step(self, u, t, dt, precond=None, tableau=2, alpha=1e-3, abs_tol=0.0,
                    max_newton=20, rebuild=False, restart=30, max_cycles=10, rtol=5e-2,
                    J=7, precision="fp64", omega=1.0, use_precond=True, guess=None,
-                   guess_train_iters=4, graphs=False, stream=None):
+                   guess_train_iters=4, graphs=False, fused=False, stream=None):
         """One SDIRK step in place on u; `precond` is a Precond holder whose
         handle is built (or reused, frozen) by the library; `guess` an optional
         Guess (learned initial guess, trained on the converged stages);
         graphs=True replays the BRJ applies and the GMRES Arnoldi steps as
-        CUDA graphs."""
+        CUDA graphs; fused=True runs each BRJ sweep after the first as one
+        kernel."""
         cfg = _lib.SdirkCfg(tableau, alpha, abs_tol, max_newton, int(rebuild), int(use_precond),
                             _lib.GmresCfg(restart, max_cycles, rtol, int(graphs)),
-                            _lib.PrecCfg(J, _lib.PREC[precision], omega, int(graphs)),
+                            _lib.PrecCfg(J, _lib.PREC[precision], omega, int(graphs), 0,
+                                         int(fused)),
                             guess.handle if guess is not None else None, guess_train_iters)
         st = _lib.StepStats()
         holder = precond if precond is not None else Precond(self)
@@ -154,8 +156,8 @@ class Precond:
         self._lib = lib()
 
     def build(self, u, t=0.0, dt_a=0.0, J=7, precision="fp64", omega=1.0, graphs=False,
-              tc_invert=False, stream=None):
-        cfg = _lib.PrecCfg(J, _lib.PREC[precision], omega, int(graphs), int(tc_invert))
+              tc_invert=False, fused=False, stream=None):
+        cfg = _lib.PrecCfg(J, _lib.PREC[precision], omega, int(graphs), int(tc_invert), int(fused))
         _check("dg_precond_build", self._lib.dg_precond_build(
             self.mesh.handle, _ptr(u), t, dt_a, ctypes.byref(cfg), ctypes.byref(self.handle),
             _stream(stream)))

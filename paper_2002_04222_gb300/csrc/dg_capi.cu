@@ -18,7 +18,7 @@ long long g_launches = 0;
 static const char* kernel_names[K_COUNT] = {
     "dg_vol", "dg_face", "dg_lift", "dg_project", "dot", "multi_dot", "multi_axpy", "vector",
     "brj_weights", "brj_tracejac", "brj_block", "brj_invert", "brj_diag",
-    "brj_offdiag", "mlp_gemm"};
+    "brj_offdiag", "mlp_gemm", "brj_sweep"};
 struct ProfRec {
   int id;
   cudaEvent_t a, b;

@@ -132,7 +132,7 @@ extern long long g_launches;
 enum KernelId {
   K_VOL, K_FACE, K_LIFT, K_PROJECT, K_DOT, K_MULTIDOT, K_MULTIAXPY, K_VEC,
   K_BRJ_WEIGHTS, K_BRJ_TRACEJAC, K_BRJ_BLOCK, K_BRJ_INVERT, K_BRJ_DIAG,
-  K_BRJ_OFFDIAG, K_MLP, K_COUNT
+  K_BRJ_OFFDIAG, K_MLP, K_BRJ_SWEEP, K_COUNT
 };
 int prof_begin(int id, cudaStream_t s);
 void prof_end(int handle, cudaStream_t s);

@@ -31,6 +31,7 @@
 #include "dg_precond.h"
 #include "dg_sumfact.cuh"
 #include "dg_tc.cuh"
+#include "dg_brj_apply.cuh"
 
 namespace dg {
 
@@ -45,7 +46,6 @@ struct Prec<float> {
   static constexpr int code = DG_PREC_FP32;
 };
 
-__host__ __device__ constexpr int round_up8(int x) { return (x + 7) & ~7; }
 
 // ------------------------------------------------------------ weights
 // W[e][k][l][j][a][q] (q fastest: one contiguous slice per variable pair),
@@ -423,13 +423,6 @@ __global__ void __launch_bounds__(128) brj_tracejac_gen_kernel(
 }
 
 // ------------------------------------------------------------ block assembly
-// 1-D value/derivative factors of mode m at Gauss point q: B1[q][m_r] / D1[q][m_r]
-template <int DIM, int N>
-__device__ __forceinline__ void mode_coords(int m, int* mc) {
-  mc[0] = m % N;
-  mc[1] = (m / N) % N;
-  mc[2] = DIM == 3 ? m / (N * N) : 0;
-}
 
 // Element block of (k, l) by sum factorisation.  With the per-point weights
 // W_ja(q) (test derivative direction j, trial slot a: value or derivative a-1)
@@ -1081,204 +1074,17 @@ __global__ void __launch_bounds__(256) brj_invert_tc_kernel(float* __restrict__ 
 
 // ------------------------------------------------------------ apply
 // y = q - (L+U) qh = q + dt_a M^-1 sum_faces B_f^T (Jo . trace of the neighbour's qh)
-// Hint that brings the 16-byte-aligned interior of [p, p + bytes) of global
-// memory toward L2 (bulk prefetch: no registers, no shared memory, no wait).
-__device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes) {
-  const size_t g = __cvta_generic_to_global(p);
-  const size_t a = (g + 15) & ~(size_t)15, b = (g + bytes) & ~(size_t)15;
-  if (b > a)
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"((uint32_t)(b - a))
-                 : "memory");
-}
-
-// One block per element: the neighbour face values are evaluated from the
-// neighbour's face-mode coefficients (2-D sum factorisation), multiplied by
-// the stored neighbour trace Jacobians, lifted onto the face modes and
-// multiplied by the inverse mass matrix, all in the apply precision TA.
+// y = q - (L+U) qh, one block of 128 threads per element
 template <int DIM, int P, int Q, typename TA, typename TJ, bool CV>
 __global__ void __launch_bounds__(128) brj_offdiag_kernel(
     const __grid_constant__ Tables tab, const ElemGeo* __restrict__ geo,
     const double* __restrict__ minv, int E, const TJ* __restrict__ Jo,
     const int32_t* __restrict__ nbr, const double* __restrict__ qh,
     const double* __restrict__ q, double dta, double* __restrict__ y) {
-  using C = Cfg<DIM, P, Q>;
-  constexpr int N = C::N, NV = C::NV, NM = C::NM, NF = C::NF;
-  constexpr int NS = DIM == 2 ? N : N * N;        // face-slice modes
-  constexpr int NT = DIM == 2 ? 1 : Q * N;        // half-transformed slice per variable
-  __shared__ TA sB[Q * N], sMi[N * N];
-  __shared__ TA cs[2 * DIM * NV * NS];            // neighbour face-slice coefficients
-  __shared__ TA ct[2 * DIM * NV * NT];
-  __shared__ TA tr[2 * DIM * NV * NF];            // neighbour face values, then Jo . values
-  __shared__ TA L0[NV * NM], L1[NV * NM];
+  constexpr int NB = Cfg<DIM, P, Q>::NV * Cfg<DIM, P, Q>::NM;
   const int e = blockIdx.x;
-  // the element's neighbour trace Jacobians (one face per thread) and q are
-  // read late; start their way from DRAM now
-  if (threadIdx.x < 2 * DIM)
-    prefetch_l2(Jo + ((long long)e * 2 * DIM + threadIdx.x) * NV * NV * NF, sizeof(TJ) * NV * NV * NF);
-  else if (threadIdx.x == 2 * DIM)
-    prefetch_l2(q + (long long)e * NV * NM, sizeof(double) * NV * NM);
-  for (int i = threadIdx.x; i < Q * N; i += blockDim.x) sB[i] = (TA)tab.B[i];
-  for (int i = threadIdx.x; i < N * N; i += blockDim.x) sMi[i] = (TA)tab.Minv[i];
-  // gather the neighbour's face slice (modes with m_r = vertex of its face)
-  for (int i = threadIdx.x; i < 2 * DIM * NV * NS; i += blockDim.x) {
-    const int a = i % NS, v = (i / NS) % NV, lf = i / (NS * NV);
-    const int nb = nbr[e * 2 * DIM + lf];
-    TA val = (TA)0;
-    if (nb >= 0) {
-      const int en = nb / (2 * DIM), fn = nb % (2 * DIM);
-      const int r = fn >> 1, vert = (fn & 1) ? P : 0;
-      int mc[3] = {0, 0, 0};
-      mc[r] = vert;
-      if (DIM == 2) {
-        mc[1 - r] = a;
-      } else {
-        const int t0 = r == 0 ? 1 : 0, t1 = r == 2 ? 1 : 2;
-        mc[t0] = a % N;
-        mc[t1] = a / N;
-      }
-      val = (TA)qh[((long long)en * NV + v) * NM + mc[0] + N * (mc[1] + N * mc[2])];
-    }
-    cs[i] = val;
-  }
-  __syncthreads();
-  // face values: contract the first tangential mode index, then the second
-  if (DIM == 2) {
-    for (int i = threadIdx.x; i < 2 * DIM * NV * NF; i += blockDim.x) {
-      const int p = i % NF, fv = i / NF;
-      TA acc = (TA)0;
-#pragma unroll
-      for (int a = 0; a < N; ++a) acc += sB[p * N + a] * cs[fv * NS + a];
-      tr[i] = acc;
-    }
-  } else {
-    for (int i = threadIdx.x; i < 2 * DIM * NV * NT; i += blockDim.x) {
-      const int p0 = i % Q, b = (i / Q) % N, fv = i / NT;
-      TA acc = (TA)0;
-#pragma unroll
-      for (int a = 0; a < N; ++a) acc += sB[p0 * N + a] * cs[fv * NS + a + N * b];
-      ct[i] = acc;
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < 2 * DIM * NV * NF; i += blockDim.x) {
-      const int p = i % NF, fv = i / NF;
-      const int p0 = p % Q, p1 = p / Q;
-      TA acc = (TA)0;
-#pragma unroll
-      for (int b = 0; b < N; ++b) acc += sB[p1 * N + b] * ct[fv * NT + p0 + Q * b];
-      tr[i] = acc;
-    }
-  }
-  __syncthreads();
-  // Jo . values (in registers, then back to tr)
-  TA prod[(2 * DIM * NV * NF + 127) / 128];
-#pragma unroll
-  for (int t = 0; t < (2 * DIM * NV * NF + 127) / 128; ++t) {
-    const int i = threadIdx.x + 128 * t;
-    TA s2 = (TA)0;
-    if (i < 2 * DIM * NV * NF) {
-      const int p = i % NF, k = (i / NF) % NV, lf = i / (NF * NV);
-      if (nbr[e * 2 * DIM + lf] >= 0) {
-        const TJ* j = Jo + (((long long)e * 2 * DIM + lf) * NV + k) * NV * NF + p;
-        const TA* t0 = tr + lf * NV * NF + p;
-#pragma unroll
-        for (int l = 0; l < NV; ++l) s2 += (TA)j[l * NF] * t0[l * NF];
-      }
-    }
-    prod[t] = s2;
-  }
-  __syncthreads();
-#pragma unroll
-  for (int t = 0; t < (2 * DIM * NV * NF + 127) / 128; ++t) {
-    const int i = threadIdx.x + 128 * t;
-    if (i < 2 * DIM * NV * NF) tr[i] = prod[t];
-  }
-  __syncthreads();
-  if (DIM == 3) {
-    // lift, first tangential direction: ct[lf][v][a][p1] = sum_p0 B[p0][a] tr[lf][v][p0 + Q p1]
-    for (int i = threadIdx.x; i < 2 * DIM * NV * NT; i += blockDim.x) {
-      const int p1 = i % Q, a = (i / Q) % N, fv = i / NT;
-      const TA* c = tr + fv * NF + Q * p1;
-      TA acc = (TA)0;
-#pragma unroll
-      for (int p0 = 0; p0 < Q; ++p0) acc += sB[p0 * N + a] * c[p0];
-      ct[i] = acc;
-    }
-    __syncthreads();
-  }
-  // lift onto the face modes of this element (second tangential direction in 3-D)
-  for (int i = threadIdx.x; i < NV * NM; i += blockDim.x) {
-    const int v = i / NM, m = i % NM;
-    int mc[3];
-    mode_coords<DIM, N>(m, mc);
-    TA s2 = (TA)0;
-#pragma unroll
-    for (int lf = 0; lf < 2 * DIM; ++lf) {
-      const int r = lf >> 1, vert = (lf & 1) ? P : 0;
-      if (mc[r] != vert) continue;
-      if (DIM == 2) {
-        const TA* c = tr + (lf * NV + v) * NF;
-        const int a = mc[1 - r];
-#pragma unroll
-        for (int p = 0; p < Q; ++p) s2 += sB[p * N + a] * c[p];
-      } else {
-        const int t0 = r == 0 ? 1 : 0, t1 = r == 2 ? 1 : 2;
-        const int a = mc[t0], b = mc[t1];
-        const TA* c = ct + (lf * NV + v) * NT + a * Q;
-#pragma unroll
-        for (int p1 = 0; p1 < Q; ++p1) s2 += sB[p1 * N + b] * c[p1];
-      }
-    }
-    L0[i] = s2;
-  }
-  __syncthreads();
-  if constexpr (CV) {
-    // dense inverse mass matrix of the element (symmetric)
-    // (one thread per mode m: each entry of M^-1 is read once for all variables)
-    const double* Me = minv + (long long)e * NM * NM;
-    for (int m = threadIdx.x; m < NM; m += blockDim.x) {
-      TA s2[NV];
-#pragma unroll
-      for (int v = 0; v < NV; ++v) s2[v] = (TA)0;
-      for (int kk = 0; kk < NM; ++kk) {
-        const TA mk = (TA)Me[kk * NM + m];
-#pragma unroll
-        for (int v = 0; v < NV; ++v) s2[v] += mk * L0[v * NM + kk];
-      }
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        const long long gi = ((long long)e * NV + v) * NM + m;
-        y[gi] = q[gi] + dta * (double)s2[v];
-      }
-    }
-    return;
-  }
-  // inverse mass matrix, axis by axis
-  TA* src = L0;
-  TA* dst = L1;
-#pragma unroll
-  for (int ax = 0; ax < DIM; ++ax) {
-    for (int i = threadIdx.x; i < NV * NM; i += blockDim.x) {
-      const int m = i % NM;
-      int mc[3];
-      mode_coords<DIM, N>(m, mc);
-      const int str = ax == 0 ? 1 : (ax == 1 ? N : N * N);
-      const int base = i - mc[ax] * str;
-      TA s2 = (TA)0;
-#pragma unroll
-      for (int kk = 0; kk < N; ++kk) s2 += sMi[mc[ax] * N + kk] * src[base + kk * str];
-      dst[i] = s2;
-    }
-    __syncthreads();
-    TA* t = src;
-    src = dst;
-    dst = t;
-  }
-  const double idet = geo[e].idet;
-  const double sc = dta * idet;
-  for (int i = threadIdx.x; i < NV * NM; i += blockDim.x) {
-    const long long gi = (long long)e * NV * NM + i;
-    y[gi] = q[gi] + sc * (double)src[i];
-  }
+  offdiag_element<DIM, P, Q, TA, TJ, CV, 128>(tab, geo, minv, Jo, nbr, qh, q, dta, e,
+                                              [&](int i, double v) { y[(long long)e * NB + i] = v; });
 }
 
 // ------------------------------------------------------------ drivers
@@ -1381,112 +1187,19 @@ struct BRJImpl {
   }
 };
 
-// out = omega D^-1 y + (1-omega) qprev with the block stored transposed
-// (At[c][r] = (D^-1)[r][c], rows padded to ld): each thread owns VW
-// consecutive rows and streams the columns with one 16-byte load per column,
-// so a warp reads 512 contiguous bytes per column and needs no reduction;
-// SPLIT thread groups share the columns and add their partial sums in shared
-// memory.  Arithmetic in TA (FP64 for FP64 blocks, FP32 otherwise).
 template <typename TB>
-struct Vec16;
-template <>
-struct Vec16<double> {
-  static constexpr int W = 2;
-  using TA = double;
-  using R = double2;  // one 16-byte load
-  __device__ static R ld(const double* p) { return __ldcs(reinterpret_cast<const double2*>(p)); }
-  __device__ static void cvt(const R& v, double* o) {
-    o[0] = v.x;
-    o[1] = v.y;
-  }
-};
-template <>
-struct Vec16<float> {
-  static constexpr int W = 4;
-  using TA = float;
-  using R = float4;
-  __device__ static R ld(const float* p) { return __ldcs(reinterpret_cast<const float4*>(p)); }
-  __device__ static void cvt(const R& v, float* o) {
-    o[0] = v.x;
-    o[1] = v.y;
-    o[2] = v.z;
-    o[3] = v.w;
-  }
-};
-template <>
-struct Vec16<__nv_bfloat16> {
-  static constexpr int W = 8;
-  using TA = float;
-  using R = uint4;
-  __device__ static R ld(const __nv_bfloat16* p) { return __ldcs(reinterpret_cast<const uint4*>(p)); }
-  __device__ static void cvt(const R& v, float* o) {
-    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      const float2 f = __bfloat1622float2(h[t]);
-      o[2 * t] = f.x;
-      o[2 * t + 1] = f.y;
-    }
-  }
-};
-
-// FP32/FP64 blocks launch at most 256 threads, BF16 blocks up to 512 (twice the
-// column groups, half the bytes each); registers capped so that 6 and 2 CTAs
-// fit an SM
-template <typename TB>
-__global__ void __launch_bounds__(sizeof(TB) == 2 ? 512 : 256, sizeof(TB) == 2 ? 2 : 6)
-    brj_diag_cm_kernel(const TB* __restrict__ blocks, int nb,
-                                                          int ld, int split,
-                                                          const double* __restrict__ y,
-                                                          const double* __restrict__ qprev,
-                                                          double omega, double* __restrict__ out) {
-  using V = Vec16<TB>;
-  using TA = typename V::TA;
-  constexpr int W = V::W;
+__global__ void DG_DIAG_BOUNDS(TB)
+    brj_diag_cm_kernel(const TB* __restrict__ blocks, int nb, int ld, int split,
+                       const double* __restrict__ y, const double* __restrict__ qprev,
+                       double omega, double* __restrict__ out) {
+  using TA = typename Vec16<TB>::TA;
   extern __shared__ unsigned char smraw[];
   TA* sy = reinterpret_cast<TA*>(smraw);                 // [nb]
   TA* part = sy + nb;                                    // [split][ld]
   const int e = blockIdx.x;
   for (int i = threadIdx.x; i < nb; i += blockDim.x) sy[i] = (TA)y[(long long)e * nb + i];
   __syncthreads();
-  const int nrq = ld / W;                                // row groups
-  const int rq = threadIdx.x % nrq, sp = threadIdx.x / nrq;
-  const int chunk = (nb + split - 1) / split;
-  const int c0 = sp * chunk, c1 = min(nb, c0 + chunk);
-  TA acc[W];
-#pragma unroll
-  for (int t = 0; t < W; ++t) acc[t] = (TA)0;
-  if (sp < split) {
-    const TB* A = blocks + (long long)e * nb * ld + rq * W;
-    // U columns per step, their loads issued together; the ragged last step
-    // predicates its loads instead of running a one-load-at-a-time remainder
-    constexpr int U = sizeof(TB) == 2 ? 8 : 4;
-    for (int c = c0; c < c1; c += U) {
-      typename V::R r[U];  // raw 16-byte loads, widened when used
-#pragma unroll
-      for (int u = 0; u < U; ++u)
-        if (c + u < c1) r[u] = V::ld(A + (long long)(c + u) * ld);
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        if (c + u < c1) {
-          TA a[W];
-          V::cvt(r[u], a);
-          const TA yc = sy[c + u];
-#pragma unroll
-          for (int t = 0; t < W; ++t) acc[t] += a[t] * yc;
-        }
-      }
-    }
-#pragma unroll
-    for (int t = 0; t < W; ++t) part[sp * ld + rq * W + t] = acc[t];
-  }
-  __syncthreads();
-  for (int r = threadIdx.x; r < nb; r += blockDim.x) {
-    TA s2 = (TA)0;
-    for (int k = 0; k < split; ++k) s2 += part[k * ld + r];
-    const long long gi = (long long)e * nb + r;
-    out[gi] = omega == 1.0 ? (double)s2 : omega * (double)s2 + (1.0 - omega) * qprev[gi];
-  }
+  diag_element<TB>(blocks, nb, ld, split, sy, part, qprev, omega, out, e);
 }
 
 template <typename TB>
@@ -1518,9 +1231,7 @@ static dg_status diag_apply(dg_precond_s* pc, double omega, const double* y, con
   return diag_launch<__nv_bfloat16>(pc->blocks, E, nb, ld, y, qprev, omega, out, s);
 }
 
-#define DG_PREC_INSTANCES(X)                                                                  \
-  X(2, 1, 3) X(2, 2, 3) X(2, 2, 4) X(2, 3, 5) X(2, 4, 6) X(2, 5, 7) X(2, 6, 8) X(3, 1, 3) \
-  X(3, 2, 4) X(3, 2, 5) X(3, 3, 5) X(3, 3, 6) X(3, 4, 6) X(3, 4, 8)
+
 
 // geometry kind at run time; general-geometry kernels only where instantiated
 template <int D, int P, int Q, typename T>
@@ -1568,8 +1279,26 @@ static dg_status dispatch_offdiag(dg_precond_s* pc, const double* qh, const doub
   return DG_ERR_UNSUPPORTED;
 }
 
+// the fused form of the sweeps: sweep 1 as before, then each later sweep one
+// launch reading the previous iterate from one buffer and writing the next
+// into the other (the neighbours read the previous iterate while it is
+// replaced, so the two cannot share a buffer)
+static dg_status precond_sweeps_fused(dg_precond_s* pc, const double* q, double* out,
+                                      cudaStream_t s) {
+  double* cur = pc->J == 1 ? out : pc->qh;
+  DG_TRY(diag_apply(pc, 1.0, q, nullptr, cur, s));
+  if (pc->omega != 1.0) DG_TRY(axpby(cur, 0.0, cur, pc->omega, pc->mesh->ndof, s));
+  for (int j = 1; j < pc->J; ++j) {
+    double* nxt = j == pc->J - 1 ? out : (cur == pc->qh ? pc->qh2 : pc->qh);
+    DG_TRY(dispatch_sweep(pc, cur, q, nxt, s));
+    cur = nxt;
+  }
+  return DG_OK;
+}
+
 // the J sweeps of Eq. precond-Jacobi as kernel launches on stream s
 dg_status precond_sweeps(dg_precond_s* pc, const double* q, double* out, cudaStream_t s) {
+  if (pc->fused) return precond_sweeps_fused(pc, q, out, s);
   // sweep 1 from qh = 0: D^-1 q (the relaxation term vanishes)
   double* cur = pc->J == 1 ? out : pc->qh;
   DG_TRY(diag_apply(pc, 1.0, q, nullptr, cur, s));
@@ -1655,6 +1384,7 @@ static void free_precond(dg_precond_s* p) {
   cudaFree(p->nbr);
   cudaFree(p->tr);
   cudaFree(p->qh);
+  cudaFree(p->qh2);
   cudaFree(p->y);
   cudaFree(p->work);
   precond_drop_graphs(p);
@@ -1747,10 +1477,13 @@ dg_status dg_precond_build(dg_mesh_t m, const double* u, double t, double dt_a,
   // the captured sweeps hold J, omega and the launch shapes: a rebuild re-captures
   precond_drop_graphs(p);
   static unsigned long long g_gen = 0;
-  // (the sweeps pass J, omega and dt_a by value; everything else by pointer
+  // (the sweeps take J, omega, dt_a and their form by value; everything else by pointer
   // into buffers that a rebuild refills in place)
-  if (p->gen == 0 || p->J != cfg->J || p->omega != cfg->omega || p->dt_a != dt_a)
+  if (p->gen == 0 || p->J != cfg->J || p->omega != cfg->omega || p->dt_a != dt_a ||
+      p->fused != (cfg->fused != 0))
     p->gen = __atomic_add_fetch(&g_gen, 1ULL, __ATOMIC_RELAXED);
+  if (cfg->fused && !p->qh2) DG_CUDA(cudaMalloc((void**)&p->qh2, sizeof(double) * (size_t)m->ndof));
+  p->fused = cfg->fused != 0;
   p->use_graphs = cfg->graphs;
   p->tc_invert = cfg->tc_invert;
   p->J = cfg->J;

@@ -31,6 +31,8 @@ struct dg_precond_s {
   };
   int use_graphs = 0;
   int tc_invert = 0;      // FP32 blocks: trailing updates of the inversion on the tensor cores
+  int fused = 0;          // sweeps j >= 2 as one off-diagonal + block kernel
+  double* qh2 = nullptr;  // [ndof] second iterate buffer of the fused sweeps (lazily allocated)
   std::vector<Graph> graphs;
   cudaStream_t cs = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -38,6 +40,9 @@ struct dg_precond_s {
 
 namespace dg {
 dg_status precond_apply_impl(dg_precond_s* p, const double* q, double* out, cudaStream_t s);
+// one fused sweep: out = omega D^-1 (q - (L+U) qprev) + (1-omega) qprev (dg_sweep.cu)
+dg_status dispatch_sweep(dg_precond_s* p, const double* qprev, const double* q, double* out,
+                         cudaStream_t s);
 // the apply as plain kernel launches on s (for capture inside a larger graph)
 dg_status precond_sweeps(dg_precond_s* p, const double* q, double* out, cudaStream_t s);
 void precond_drop_graphs(dg_precond_s* p);

@@ -201,3 +201,68 @@ def test_set_tune_rejects_non_candidates(dgl):
     assert dgl.lib().dg_set_tune(m.handle, ctypes.byref(bad)) == DG_ERR_ARG
     bad = _lib.TuneResult(1, 7, 1, 64, 0.0, 0.0, 0.0, 0.0)
     assert dgl.lib().dg_set_tune(m.handle, ctypes.byref(bad)) == DG_ERR_ARG
+
+
+@pytest.mark.parametrize("case,precision", [("vortex", "fp64"), ("vortex", "bf16"),
+                                            ("box_P3", "fp32"), ("box_P3", "bf16"),
+                                            ("box_P3", "fp64"), ("wavy_P2", "fp32")])
+def test_fused_sweeps_bitwise(dgl, case, precision):
+    """The fused sweep (off-diagonal product and block product of an element in
+    one kernel) forms the same y_e in the same order and multiplies it by the
+    same block: BRJ(J) applies equal the separate kernels' bit for bit, for
+    several J and omega, with graphs and inside GMRES."""
+    if case == "vortex":
+        c = w.vortex_case(n=6, P=2)
+    elif case == "box_P3":
+        c = w.small_tgv_case((3, 3, 2), P=3, Q=6)
+    else:
+        c = w.wavy_box_case((3, 2, 2), P=2)
+    m = dgl.Mesh.from_case(c)
+    u = to_dev(perturbed(c))
+    qs = [to_dev(w.random_direction(u.cpu().numpy(), s)) for s in range(2)]
+    for J, omega in [(1, 1.0), (2, 1.0), (3, 0.8), (7, 1.0)]:
+        plain = dgl.Precond(m).build(u, 0.0, 0.03, J=J, precision=precision, omega=omega)
+        fused = dgl.Precond(m).build(u, 0.0, 0.03, J=J, precision=precision, omega=omega,
+                                     fused=True)
+        for q in qs:
+            n0 = dgl.kernel_launches()
+            ref = plain.apply(q)
+            n_plain = dgl.kernel_launches() - n0
+            n0 = dgl.kernel_launches()
+            out = fused.apply(q)
+            n_fused = dgl.kernel_launches() - n0
+            torch.cuda.synchronize()
+            assert torch.equal(out, ref), (J, omega)
+            assert n_fused == n_plain - (J - 1), (n_fused, n_plain)
+        graph = dgl.Precond(m).build(u, 0.0, 0.03, J=J, precision=precision, omega=omega,
+                                     fused=True, graphs=True)
+        o = m.empty()
+        for _ in range(2):
+            graph.apply(qs[0], o)
+            assert torch.equal(o, plain.apply(qs[0]))
+    # the plain handle switched to fused and back: GMRES (with Arnoldi graphs) agrees
+    r_u = m.residual(u)
+    pc = dgl.Precond(m).build(u, 0.0, 0.03, J=4, precision=precision)
+    x0, s0 = m.gmres(u, r_u, qs[1], 0.0, 0.03, precond=pc, restart=8, rtol=1e-6, graphs=True)
+    pc.build(u, 0.0, 0.03, J=4, precision=precision, fused=True)
+    x1, s1 = m.gmres(u, r_u, qs[1], 0.0, 0.03, precond=pc, restart=8, rtol=1e-6, graphs=True)
+    assert s0 == s1 and torch.equal(x0, x1)
+
+
+def test_fused_sweeps_sdirk_bitwise(dgl):
+    c = w.vortex_case(n=8, P=2)
+    m = dgl.Mesh.from_case(c)
+    u0 = m.project()
+    res = []
+    for fused in (False, True):
+        u = u0.clone()
+        pc = dgl.Precond(m)
+        stats = []
+        for k in range(2):
+            st = m.sdirk_step(u, 0.02 * k, 0.02, precond=pc, rebuild=(k == 0), restart=20, J=7,
+                              precision="fp32", graphs=True, fused=fused)
+            assert st["converged"]
+            stats.append((st["stage_newton"], st["stage_gmres"]))
+        res.append((u, stats))
+    assert res[0][1] == res[1][1]
+    assert torch.equal(res[0][0], res[1][0])
