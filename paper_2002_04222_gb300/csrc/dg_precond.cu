@@ -1096,7 +1096,6 @@ struct BRJImpl {
   static dg_status build(dg_mesh_s* m, dg_precond_s* pc, const double* u, double t, double dta,
                          cudaStream_t s) {
     constexpr int NV = C::NV, NM = C::NM, NQ = C::NQ, NF = C::NF;
-    constexpr int NW = DIM * (DIM + 1) * NV * NV;
     const int E = m->E, nb = pc->nb, ld = round_up8(nb);
     // traces of Q and grad Q at u (residual pass fills the trace buffer)
     EvalArgs a{};
