@@ -17,9 +17,10 @@
 // Apply (Eq. precond-Jacobi): q^1 = D^-1 q; q^j = D^-1 (q - (L+U) q^(j-1)), the
 // off-diagonal product formed on the fly from the neighbour traces and the
 // stored neighbour trace Jacobians (brj_offdiag_kernel, which also evaluates the
-// neighbour traces),
-// the block product by brj_diag_cm_kernel (HBM-bound batched GEMV streaming the
-// transposed blocks column by column).
+// neighbour traces), the block product by brj_diag_cm_kernel (HBM-bound batched
+// GEMV streaming the transposed blocks column by column); both on the
+// per-element device functions of dg_brj_apply.cuh, which the fused form of a
+// sweep (brj_sweep_kernel, dg_sweep.cu) runs back to back in one kernel.
 #include <cmath>
 #include <cstring>
 #include <cuda_bf16.h>
