@@ -129,7 +129,8 @@ dg_status dg_mesh_info(dg_mesh_t m, dg_mesh_info_t* info);
  * per CTA, threads per CTA) of the volume and lift kernels that fits one CTA's
  * shared memory, reps launches each, on the projected analytic field, and keeps
  * the fastest for this mesh; result receives the choice and its times (ms per
- * launch; *_default: the built-in shape).  dg_set_tune applies a shape taken
+ * launch; *_default: the shape in effect before the call, the built-in one on
+ * a fresh mesh, timed also when it is not a candidate).  dg_set_tune applies a shape taken
  * from a stored tuning table (DG_ERR_ARG if it is not a candidate for this
  * (dim, P, Q)).  Results do not depend on the shape. */
 typedef struct {

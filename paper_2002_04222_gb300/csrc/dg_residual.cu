@@ -806,8 +806,9 @@ static dg_status run_autotune(dg_mesh_s* m, int reps, dg_tune_result* res, cudaS
     cudaEventElapsedTime(&ms, e0, e1);
     return ms / reps;
   };
-  // volume + face kernels (the face kernel's launch is fixed and adds the same time to each)
-  double best = 1e30, dflt = 0.0;
+  // volume + face kernels (the face kernel's launch is fixed and adds the same time to each);
+  // the shape in effect before tuning is timed too when it is not a candidate
+  double best = 1e30, dflt = -1.0;
   Tune t = keep;
   for (const int2& c : vc) {
     m->tune.vol_epb = c.x;
@@ -820,12 +821,18 @@ static dg_status run_autotune(dg_mesh_s* m, int reps, dg_tune_result* res, cudaS
       t.vol_threads = c.y;
     }
   }
+  if (dflt < 0.0) {
+    m->tune.vol_epb = keep.vol_epb;
+    m->tune.vol_threads = keep.vol_threads;
+    dflt = time_it(true);
+  }
   res->vol_ms = best;
   res->vol_ms_default = dflt;
   m->tune.vol_epb = t.vol_epb;
   m->tune.vol_threads = t.vol_threads;
   run_residual<DIM, P, Q>(m, a, s);  // traces and fluxes for the lift timing
   best = 1e30;
+  dflt = -1.0;
   for (const int2& c : lc) {
     m->tune.lift_epb = c.x;
     m->tune.lift_threads = c.y;
@@ -836,6 +843,11 @@ static dg_status run_autotune(dg_mesh_s* m, int reps, dg_tune_result* res, cudaS
       t.lift_epb = c.x;
       t.lift_threads = c.y;
     }
+  }
+  if (dflt < 0.0) {
+    m->tune.lift_epb = keep.lift_epb;
+    m->tune.lift_threads = keep.lift_threads;
+    dflt = time_it(false);
   }
   res->lift_ms = best;
   res->lift_ms_default = dflt;
