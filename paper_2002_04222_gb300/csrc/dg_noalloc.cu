@@ -1,14 +1,17 @@
 // GMRES entry point for callers that must not allocate device memory.
 //
 // dg_gmres sizes its Krylov basis on its first call with cudaMalloc.  Some
-// callers cannot allocate at solve time: code that runs while a CUDA stream
-// is being captured into a graph (allocation is not a capturable, stream-
-// ordered operation), applications whose memory pool has reserved the whole
-// device up front, or real-time loops that forbid allocator calls.  For them
+// callers cannot allocate while they solve: applications whose memory pool
+// has reserved the whole device up front, or loops that forbid allocator
+// calls once they run (real-time or latency-bound drivers).  For them
 // dg_gmres_noalloc runs the same algorithm with its Krylov basis in one
 // file-scope static device array of fixed size, so the call performs no
 // cudaMalloc, cudaFree or other allocating routine (host side included: its
-// small Hessenberg arrays live on the stack).
+// small Hessenberg arrays live on the stack).  The preconditioner's sweeps
+// run as plain kernel launches whatever its graph setting, because
+// capturing and instantiating a graph allocates.  Like dg_gmres, the call
+// reads the Hessenberg column back to the host and synchronises the stream
+// after every Arnoldi step.
 #include <cmath>
 #include <cuda_runtime.h>
 #include "dg_internal.h"
@@ -107,7 +110,9 @@ extern "C" dg_status dg_gmres_noalloc(dg_mesh_t m, dg_precond_t p, const double*
       const double* zk = vk;
       if (p) {
         double* zz = Z + (size_t)k * n;
-        DG_TRY(precond_apply_impl(p, vk, zz, s));
+        // plain launches, never the graph replay: capturing and instantiating
+        // a graph allocates (precond_sweeps is what the replay runs)
+        DG_TRY(precond_sweeps(p, vk, zz, s));
         zk = zz;
       }
       double* w = V + (size_t)(k + 1) * n;

@@ -67,3 +67,10 @@ def test_struct_layouts_match_header():
         assert int(got[cname]) == ctypes.sizeof(cls), cname
         for f, _ in cls._fields_:
             assert int(got[f"{cname}.{f}"]) == getattr(cls, f).offset, (cname, f)
+
+
+def test_noalloc_limit_matches_header():
+    from paper_2002_04222_gb300 import _lib
+    text = open(HEADER).read()
+    val = int(re.search(r"#define DG_GMRES_NOALLOC_MAX_DOUBLES (\d+)", text).group(1))
+    assert _lib.NOALLOC_MAX_DOUBLES == val
