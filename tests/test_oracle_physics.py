@@ -224,3 +224,52 @@ def test_tgv_velocity_divergence_free():
     assert np.abs(np.einsum("kjj->k", dv)).max() < 1e-9
     _, _, _, T = phy.primitives(phy.exact_state(ph, x, 0.0), ph)
     assert np.allclose(T, 1.0)
+
+
+# ------------------------------------------------------------------ Sutherland's law
+
+def sutherland_dimensional(T_kelvin, mu0=1.716e-5, T0=273.15, S=110.0):
+    """Sutherland's law in kelvin, mu = mu0 (T/T0)^(3/2) (T0 + S)/(T + S)
+    (the textbook dimensional form; mu0 and T0 cancel in any ratio)."""
+    return mu0 * (T_kelvin / T0) ** 1.5 * (T0 + S) / (T_kelvin + S)
+
+
+@pytest.mark.parametrize("T_inf", [288.15, 120.0, 1000.0])
+def test_sutherland_viscosity_pins(T_inf):
+    """Sec. 2.1 non-dimensionalises mu by its free-stream value, mu = 1/Re at
+    T = 1.  With Sutherland's law the non-dimensional mu(T) is the dimensional
+    law's ratio mu(T T_inf) / mu(T_inf) over Re; it grows like T^(1/2) for
+    T >> S/T_inf and like T^(3/2) for T << S/T_inf."""
+    ph = Physics(Re=250.0, mu_law=1, T_inf_K=T_inf)
+    assert phy.viscosity(np.array([1.0]), ph)[0] == pytest.approx(1.0 / ph.Re, rel=1e-15)
+    T = np.array([0.3, 0.8, 1.7, 4.0])
+    ref = sutherland_dimensional(T * T_inf) / sutherland_dimensional(T_inf) / ph.Re
+    assert np.allclose(phy.viscosity(T, ph), ref, rtol=1e-13, atol=0)
+    # the same ratio for another reference pair (mu0, T0): they cancel
+    ref2 = sutherland_dimensional(T * T_inf, 3.0, 100.0) / sutherland_dimensional(T_inf, 3.0, 100.0)
+    assert np.allclose(phy.viscosity(T, ph) * ph.Re, ref2, rtol=1e-13)
+    s = 110.0 / T_inf
+    big, small = np.array([1e8]), np.array([1e-8])
+    assert phy.viscosity(big, ph)[0] / np.sqrt(big[0]) == pytest.approx((1 + s) / ph.Re, rel=1e-6)
+    assert phy.viscosity(small, ph)[0] / small[0] ** 1.5 == pytest.approx((1 + s) / (s * ph.Re),
+                                                                         rel=1e-6)
+    # constant law: 1/Re at every temperature
+    assert np.all(phy.viscosity(T, Physics(Re=250.0)) == 1.0 / 250.0)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_viscous_flux_scales_with_sutherland_viscosity(d):
+    """The diffusion flux is linear in mu (stress and heat flux both carry it,
+    kappa = mu/(Ma^2 Pr (gamma-1))), so the Sutherland flux equals the
+    constant-mu flux times mu(T) Re, point by point."""
+    rng = np.random.default_rng(17 + d)
+    ph0 = Physics(Ma=0.3, Re=50.0)
+    ph1 = Physics(Ma=0.3, Re=50.0, mu_law=1, T_inf_K=200.0)
+    U = random_state(rng, d, n=7, ph=ph0)
+    dU = rng.standard_normal((7, d, d + 2))
+    _, _, _, T = phy.primitives(U, ph0)
+    G0 = phy.viscous_flux(U, dU, ph0)
+    G1 = phy.viscous_flux(U, dU, ph1)
+    scale = (phy.viscosity(T, ph1) * ph1.Re)[:, None, None]
+    assert np.allclose(G1, G0 * scale, rtol=1e-13, atol=1e-13 * np.abs(G0).max())
+    assert not np.allclose(G1, G0, rtol=1e-3)     # temperatures differ from 1
