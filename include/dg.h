@@ -213,7 +213,7 @@ dg_status dg_precond_destroy(dg_precond_t p);
  * those of graphs = 0.  The mesh handle keeps up to 128 such graphs (the
  * oldest is dropped), and drops them all when its launch tuning changes or
  * its Krylov basis is reallocated.  Per-kernel profiling launches plainly.
- * dg_gmres_noalloc ignores graphs. */
+ * dg_gmres_noalloc ignores graphs (it launches plainly). */
 typedef struct {
   int restart;
   int max_cycles;
@@ -230,21 +230,27 @@ dg_status dg_gmres(dg_mesh_t m, dg_precond_t p, const double* u, const double* r
 
 /* GMRES for callers that cannot allocate device memory (the paper has no
  * counterpart; this is an interface for such callers).  dg_gmres allocates its
- * Krylov basis with cudaMalloc on its first call; code that runs during CUDA
- * stream capture, under a memory pool that has reserved the device, or in a
- * loop that forbids allocator calls cannot do that.  dg_gmres_noalloc solves
- * the same system with the same algorithm and arguments as dg_gmres, but keeps
- * the basis (restart+1 vectors, plus restart preconditioned vectors when p is
- * not NULL) in one static device array of DG_GMRES_NOALLOC_MAX_DOUBLES doubles
+ * Krylov basis with cudaMalloc on its first call; an application whose memory
+ * pool has reserved the whole device up front, or a loop that forbids
+ * allocator calls once it runs, cannot do that.  dg_gmres_noalloc solves the
+ * same system with the same algorithm and arguments as dg_gmres, but keeps the
+ * basis (restart+1 vectors, plus restart preconditioned vectors when p is not
+ * NULL) in one static device array of DG_GMRES_NOALLOC_MAX_DOUBLES doubles
  * (16 MiB) that every GPU loading the library holds until exit; it calls no
- * cudaMalloc, cudaFree or allocating routine.  It returns DG_ERR_ARG when
- * n_dof * (restart + 1 + (p ? restart : 0)) exceeds that size.  The first call
- * on each device looks up the array's device address (cudaGetSymbolAddress),
- * so make that first call before any stream capture.  All calls share the
- * array and it keeps the last call's contents: calls whose work overlaps on the
- * GPU (other streams, other threads) race and must be serialised by the caller.
- * The mesh and preconditioner handles must already exist (they are created
- * with allocation, once, at set-up). */
+ * cudaMalloc, cudaFree or allocating routine.  It ignores cfg->graphs, and it
+ * runs the preconditioner's sweeps as plain kernel launches even when p was
+ * built with graphs != 0 (capturing and instantiating a graph allocates; the
+ * result is the same).  Like dg_gmres, it reads each Hessenberg column back to
+ * the host and synchronises the stream after every Arnoldi step.  It returns
+ * DG_ERR_ARG when n_dof * (restart + 1 + (p ? restart : 0)) exceeds the
+ * array.  The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) as its set-up, so make that first call before any
+ * stream capture.  All calls share the array and it keeps the last call's
+ * contents: calls whose work overlaps on the GPU (other streams, other
+ * threads) race and must be serialised by the caller.  The mesh and
+ * preconditioner handles must already exist (they are created with
+ * allocation, once, at set-up).  Per-kernel profiling (dg_profile_enable)
+ * creates CUDA events; leave it off around this call. */
 #define DG_GMRES_NOALLOC_MAX_DOUBLES 2097152
 dg_status dg_gmres_noalloc(dg_mesh_t m, dg_precond_t p, const double* u, const double* r_u,
                            double t, double dt_a, const double* b, double* x,
@@ -342,6 +348,14 @@ typedef struct {
 } dg_kernel_time;
 dg_status dg_profile_enable(int on);
 dg_status dg_profile_read(dg_kernel_time* out, int cap, int* n);
+
+/* Measured FP64 FMA throughput of this GPU in TFLOP/s (diagnostic, no
+ * counterpart in the paper): reps timed launches of a kernel whose threads run
+ * eight independent fused multiply-add chains at full occupancy, timed with
+ * CUDA events on `stream` after one warm-up launch (2 flops per FMA).  The
+ * residual kernels are bound by this pipe; the benchmark divides their
+ * algorithmic flop rate by this figure. */
+dg_status dg_peak_fp64(int reps, double* tflops, void* stream);
 
 /* Static description of a status code. */
 const char* dg_status_string(dg_status s);

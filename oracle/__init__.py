@@ -24,5 +24,5 @@ except where its docstring says "parity unpinned".
 from .basis import (gauss_legendre, jacobi, modified_basis, gll_points,  # noqa: F401
                     lagrange_basis, tensor_tables)
 from .dg import DG  # noqa: F401
-from .implicit import (jvp, gmres, BRJ, newton, sdirk_step, sdirk_tableau,  # noqa: F401
+from .implicit import (jvp, gmres, BRJ, newton, sdirk_step, sdirk_tableau, bdf2_step,  # noqa: F401
                        NewtonConfig, GmresConfig)

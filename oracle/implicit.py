@@ -331,7 +331,37 @@ def newton(dg, S, t, dt_a, u0, precond=None, cfg=None):
 
 def sdirk_tableau(name):
     """Butcher tableaus of App. A (Tab. RK-coeff): SDIRK2 with
-    lambda = 1 - sqrt(2)/2 and SDIRK3 with lambda = 0.4358665215."""
+    lambda = 1 - sqrt(2)/2, SDIRK3 with lambda = 0.4358665215, and the
+    six-stage fourth-order scheme with an explicit first stage and diagonal
+    1/4 ("esdirk4"); plus backward Euler ("be", one stage with a = b = c = 1),
+    which Sec. 4.3 lists among the implicit schemes.
+
+    The fourth-order table is printed with symbols a^{i1} in its first
+    column: each names the entry beside it in the second column (a^{i0} =
+    a^{i1}, as in the Kennedy-Carpenter scheme the paper cites).  The nodes c
+    are then the row sums; the printed third node (2 - sqrt 2)/2 is read as
+    (2 - sqrt 2)/4, the row sum of (1 - sqrt 2)/8, (1 - sqrt 2)/8, 1/4 (with
+    the printed node the row-sum reading of the first column violates the
+    order conditions).  The weights are the last row (stiffly accurate)."""
+    if name == "be":
+        return np.array([[1.0]]), np.array([1.0]), np.array([1.0])
+    if name == "esdirk4":
+        r2 = np.sqrt(2.0)
+        A = np.zeros((6, 6))
+        A[1, 1] = 0.25
+        A[2, 1], A[2, 2] = (1 - r2) / 8, 0.25
+        A[3, 1], A[3, 2], A[3, 3] = (5 - 7 * r2) / 64, 7 * (1 + r2) / 32, 0.25
+        A[4, 1] = (-13796 - 54539 * r2) / 125000
+        A[4, 2] = (506605 + 132109 * r2) / 437500
+        A[4, 3] = 166 * (-97 + 376 * r2) / 109375
+        A[4, 4] = 0.25
+        A[5, 1] = (1181 - 987 * r2) / 13782
+        A[5, 2] = 47 * (-267 + 1783 * r2) / 273343
+        A[5, 3] = -16 * (-22922 + 3525 * r2) / 571953
+        A[5, 4] = -15625 * (97 + 376 * r2) / 90749876
+        A[5, 5] = 0.25
+        A[1:, 0] = A[1:, 1]
+        return A, A[5].copy(), A.sum(axis=1)
     if name == "sdirk2":
         lam = 1.0 - np.sqrt(2.0) / 2.0
         A = np.array([[lam, 0.0], [1.0 - lam, lam]])
@@ -366,10 +396,24 @@ def sdirk_step(dg, u_n, t, dt, tableau="sdirk2", precond=None, cfg=None,
     st = StepStats(stages=[])
     for m in range(M):
         S = u_n + sum(A[m, i] * E[i] for i in range(m))
-        u0 = S if guess is None else guess(m, S)
-        um, Rm, ns = newton(dg, S, t + c[m] * dt, dt * A[m, m], u0, precond, cfg)
+        if A[m, m] == 0.0:
+            # explicit stage (the first stage of esdirk4): u^m = S_m, no solve
+            um, Rm, ns = S, dg.residual(S, t + c[m] * dt), NewtonStats(converged=True)
+        else:
+            u0 = S if guess is None else guess(m, S)
+            um, Rm, ns = newton(dg, S, t + c[m] * dt, dt * A[m, m], u0, precond, cfg)
         st.newton_iters += ns.iters
         st.gmres_iters += ns.gmres_iters
         st.stages.append(ns)
         E.append(dt * Rm)
     return u_n + sum(b[i] * E[i] for i in range(M)), st
+
+
+def bdf2_step(dg, u_n, u_prev, t, dt, precond=None, cfg=None):
+    """One step of the second-order backward differentiation formula (Sec. 4.3
+    lists it among the implicit schemes) at a constant step size:
+    3 u^{n+1} - 4 u^n + u^{n-1} = 2 dt R(u^{n+1}, t + dt), i.e. Newton on
+    N(u) = u - S - (2 dt / 3) R(u) with S = (4 u^n - u^{n-1}) / 3, from u = S."""
+    S = (4.0 * u_n - u_prev) / 3.0
+    u, _, ns = newton(dg, S, t + dt, 2.0 * dt / 3.0, S, precond, cfg)
+    return u, StepStats(newton_iters=ns.iters, gmres_iters=ns.gmres_iters, stages=[ns])

@@ -11,7 +11,7 @@ import numpy as np
 # identifiers shared with the workloads package (plain integers)
 BC_DIRICHLET, BC_ISO_WALL, BC_ADIA_WALL, BC_FARFIELD = 1, 2, 3, 4
 FIELD_UNIFORM, FIELD_VORTEX, FIELD_POISEUILLE, FIELD_TGV, FIELD_CYLINDER = 0, 1, 2, 3, 4
-RIEMANN_ROE, RIEMANN_HLLC = 0, 1
+RIEMANN_ROE, RIEMANN_HLLC, RIEMANN_HLL, RIEMANN_LF, RIEMANN_AUSM = 0, 1, 2, 3, 4
 FORCING_NONE, FORCING_POISEUILLE = 0, 1
 
 
@@ -156,8 +156,83 @@ def hllc_flux(UL, UR, n, ph):
     return out
 
 
+def hll_flux(UL, UR, n, ph):
+    """HLL flux (Harten, Lax and van Leer; Toro, Ch. 10): one intermediate
+    state between the fastest left- and right-going waves, with the Einfeldt
+    (Roe-averaged) speed estimates of hllc_flux:
+    F = F_L if S_L >= 0, F_R if S_R <= 0, else
+    (S_R F_L - S_L F_R + S_L S_R (U_R - U_L)) / (S_R - S_L)."""
+    g = ph.gamma
+    rL, vL, pL, _ = primitives(UL, ph)
+    rR, vR, pR, _ = primitives(UR, ph)
+    cL, cR = np.sqrt(g * pL / rL), np.sqrt(g * pR / rR)
+    HL = (UL[..., -1] + pL) / rL
+    HR = (UR[..., -1] + pR) / rR
+    sL, sR = np.sqrt(rL), np.sqrt(rR)
+    ut = (sL[..., None] * vL + sR[..., None] * vR) / (sL + sR)[..., None]
+    Ht = (sL * HL + sR * HR) / (sL + sR)
+    ct = np.sqrt((g - 1.0) * (Ht - 0.5 * np.sum(ut * ut, axis=-1)))
+    unL, unR, unt = np.sum(vL * n, -1), np.sum(vR * n, -1), np.sum(ut * n, -1)
+    SL = np.minimum(unL - cL, unt - ct)
+    SR = np.maximum(unR + cR, unt + ct)
+    FL = np.einsum("...iv,...i->...v", euler_flux(UL, ph), n)
+    FR = np.einsum("...iv,...i->...v", euler_flux(UR, ph), n)
+    Fm = (SR[..., None] * FL - SL[..., None] * FR + (SL * SR)[..., None] * (UR - UL)) \
+        / (SR - SL)[..., None]
+    return np.where((SL >= 0)[..., None], FL, np.where((SR <= 0)[..., None], FR, Fm))
+
+
+def lax_friedrichs_flux(UL, UR, n, ph):
+    """Local Lax-Friedrichs (Rusanov) flux: the mean of the two normal fluxes
+    minus a jump penalty at the larger of the two sides' spectral radii
+    |u_n| + c (Toro, Ch. 10)."""
+    g = ph.gamma
+    rL, vL, pL, _ = primitives(UL, ph)
+    rR, vR, pR, _ = primitives(UR, ph)
+    lam = np.maximum(np.abs(np.sum(vL * n, -1)) + np.sqrt(g * pL / rL),
+                     np.abs(np.sum(vR * n, -1)) + np.sqrt(g * pR / rR))
+    FL = np.einsum("...iv,...i->...v", euler_flux(UL, ph), n)
+    FR = np.einsum("...iv,...i->...v", euler_flux(UR, ph), n)
+    return 0.5 * (FL + FR) - 0.5 * lam[..., None] * (UR - UL)
+
+
+def ausm_flux(UL, UR, n, ph):
+    """AUSM flux of Liou and Steffen (1993): the convective part is the
+    interface Mach number m = M+(M_L) + M-(M_R) times the upwinded
+    c (rho, rho u, rho H), the pressure part p+(M_L) p_L + p-(M_R) p_R on the
+    momentum, with the van Leer polynomial splittings
+      M+- = +-(M +- 1)^2 / 4,  p+- = (M +- 1)^2 (2 -+ M) / 4    for |M| <= 1,
+      M+- = (M +- |M|) / 2,    p+- = (1 +- sign M) / 2           otherwise,
+    M = u_n / c on each side (normal velocity along n)."""
+    g = ph.gamma
+    d = UL.shape[-1] - 2
+    rL, vL, pL, _ = primitives(UL, ph)
+    rR, vR, pR, _ = primitives(UR, ph)
+    cL, cR = np.sqrt(g * pL / rL), np.sqrt(g * pR / rR)
+    ML, MR = np.sum(vL * n, -1) / cL, np.sum(vR * n, -1) / cR
+    sub_L, sub_R = np.abs(ML) <= 1.0, np.abs(MR) <= 1.0
+    Mp = np.where(sub_L, 0.25 * (ML + 1.0) ** 2, 0.5 * (ML + np.abs(ML)))
+    Mm = np.where(sub_R, -0.25 * (MR - 1.0) ** 2, 0.5 * (MR - np.abs(MR)))
+    Pp = np.where(sub_L, 0.25 * (ML + 1.0) ** 2 * (2.0 - ML), 0.5 * (1.0 + np.sign(ML)))
+    Pm = np.where(sub_R, 0.25 * (MR - 1.0) ** 2 * (2.0 + MR), 0.5 * (1.0 - np.sign(MR)))
+    m = Mp + Mm
+    p = Pp * pL + Pm * pR
+
+    def phi(U, r, c, pp):     # c (rho, rho u, rho H)
+        return c[..., None] * np.concatenate([r[..., None], U[..., 1:1 + d],
+                                              (U[..., -1] + pp)[..., None]], axis=-1)
+
+    fL, fR = phi(UL, rL, cL, pL), phi(UR, rR, cR, pR)
+    F = 0.5 * m[..., None] * (fL + fR) - 0.5 * np.abs(m)[..., None] * (fR - fL)
+    F[..., 1:1 + d] += p[..., None] * n
+    return F
+
+
 def riemann_flux(UL, UR, n, ph):
-    return roe_flux(UL, UR, n, ph) if ph.riemann == RIEMANN_ROE else hllc_flux(UL, UR, n, ph)
+    """The numerical advection flux selected by ph.riemann (Sec. 4.3 lists
+    Roe, HLL, HLLC, AUSM and Lax-Friedrichs among the solvers' fluxes)."""
+    return {RIEMANN_ROE: roe_flux, RIEMANN_HLLC: hllc_flux, RIEMANN_HLL: hll_flux,
+            RIEMANN_LF: lax_friedrichs_flux, RIEMANN_AUSM: ausm_flux}[ph.riemann](UL, UR, n, ph)
 
 
 # ---------------------------------------------------------------- analytic fields

@@ -18,6 +18,7 @@ STATUS = {0: "ok", -1: "invalid argument", -2: "CUDA error", -3: "out of device 
           -4: "non-finite norm", -5: "not converged", -6: "unsupported", -7: "timeout"}
 DG_ERR_NOT_CONVERGED = -5
 PREC = {"fp64": 0, "fp32": 1, "bf16": 2}
+NOALLOC_MAX_DOUBLES = 2097152   # DG_GMRES_NOALLOC_MAX_DOUBLES of include/dg.h
 
 
 class DGError(RuntimeError):
@@ -124,6 +125,7 @@ SIGNATURES = {
     "dg_guess_params": [VP, I, ctypes.POINTER(ctypes.c_void_p)],
     "dg_profile_enable": [I],
     "dg_profile_read": [ctypes.POINTER(KernelTime), I, ctypes.POINTER(I)],
+    "dg_peak_fp64": [I, ctypes.POINTER(D), VP],
 }
 
 

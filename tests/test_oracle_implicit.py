@@ -203,7 +203,7 @@ class ScalarODE:
         return self.f(u, t)
 
 
-@pytest.mark.parametrize("name", ["sdirk2", "sdirk3"])
+@pytest.mark.parametrize("name", ["sdirk2", "sdirk3", "esdirk4", "be"])
 def test_sdirk_stability_function(name):
     A, b, c = im.sdirk_tableau(name)
     cfg = im.NewtonConfig(abs_tol=1e-15, gmres=im.GmresConfig(restart=2, rtol=1e-14))
@@ -224,7 +224,52 @@ def test_butcher_order_conditions():
     assert abs(lam ** 3 - 3 * lam ** 2 + 1.5 * lam - 1 / 6) < 1e-10
 
 
-@pytest.mark.parametrize("name,order", [("sdirk2", 2), ("sdirk3", 3)])
+def test_esdirk4_order_conditions_and_l_stability():
+    """The fourth-order table (App. A, first column read as a^{i0} = a^{i1}):
+    all eight order conditions up to order 4 hold, the weights are the last
+    row (stiffly accurate), the nodes are the row sums with the printed
+    1/2, 5/8, 26/25, 1, and the stability function vanishes at infinity
+    (L-stable)."""
+    A, b, c = im.sdirk_tableau("esdirk4")
+    assert np.allclose(np.diag(A)[1:], 0.25) and A[0, 0] == 0.0
+    assert np.array_equal(b, A[-1])
+    assert np.allclose(c[[1, 3, 4, 5]], [0.5, 5 / 8, 26 / 25, 1.0], rtol=1e-14)
+    conds = [(b.sum(), 1.0), (b @ c, 1 / 2), (b @ c ** 2, 1 / 3), (b @ A @ c, 1 / 6),
+             (b @ c ** 3, 1 / 4), (b @ (c * (A @ c)), 1 / 8), (b @ A @ c ** 2, 1 / 12),
+             (b @ A @ A @ c, 1 / 24)]
+    for got, want in conds:
+        assert abs(got - want) < 1e-14
+    z = -1e8
+    Rz = 1 + z * b @ np.linalg.solve(np.eye(6) - z * A, np.ones(6))
+    assert abs(Rz) < 1e-6
+
+
+def test_bdf2_step_closed_form_and_order():
+    """BDF2 on y' = z y: one step gives (4 y_n - y_{n-1}) / (3 - 2 z); on the
+    nonlinear ODE of the SDIRK order test its error falls at rate 2."""
+    cfg = im.NewtonConfig(abs_tol=1e-15, gmres=im.GmresConfig(restart=2, rtol=1e-14))
+    for z in (-0.5, -30.0, 0.2):
+        ode = ScalarODE(lambda u, t: z * u)
+        y1, _ = im.bdf2_step(ode, np.full((1, 1, 1), 0.9), np.ones((1, 1, 1)), 0.0, 1.0, None, cfg)
+        assert abs(y1.item() - (4 * 0.9 - 1.0) / (3 - 2 * z)) < 1e-13
+    f = lambda u, t: -u * u + np.cos(t)
+    cfg = im.NewtonConfig(abs_tol=1e-15, max_iters=30, gmres=im.GmresConfig(restart=2, rtol=1e-14))
+    ode = ScalarODE(f)
+
+    def run(n):
+        dt = 1.0 / n
+        y0 = np.full((1, 1, 1), 0.5)
+        y1, _ = im.sdirk_step(ode, y0, 0.0, dt, "esdirk4", None, cfg)   # start-up step
+        for k in range(1, n):
+            y0, (y1, _) = y1, im.bdf2_step(ode, y1, y0, k * dt, dt, None, cfg)
+        return y1.item()
+
+    ref = run(1024)
+    e1, e2 = abs(run(32) - ref), abs(run(64) - ref)
+    assert np.log2(e1 / e2) > 2 - 0.3
+
+
+@pytest.mark.parametrize("name,order", [("sdirk2", 2), ("sdirk3", 3), ("esdirk4", 4), ("be", 1)])
 def test_sdirk_order_on_nonlinear_ode(name, order):
     f = lambda u, t: -u * u + np.cos(t)
     cfg = im.NewtonConfig(abs_tol=1e-15, max_iters=30, gmres=im.GmresConfig(restart=2, rtol=1e-14))

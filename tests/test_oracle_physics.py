@@ -114,7 +114,10 @@ def test_viscous_flux_vanishes_for_rigid_rotation():
     assert np.allclose(phy.viscous_flux(U, dU, ph), 0, atol=1e-13)
 
 
-@pytest.mark.parametrize("riemann", [phy.RIEMANN_ROE, phy.RIEMANN_HLLC])
+ALL_FLUXES = [phy.RIEMANN_ROE, phy.RIEMANN_HLLC, phy.RIEMANN_HLL, phy.RIEMANN_LF, phy.RIEMANN_AUSM]
+
+
+@pytest.mark.parametrize("riemann", ALL_FLUXES)
 @pytest.mark.parametrize("d", [2, 3])
 def test_riemann_consistency_and_conservation(riemann, d):
     ph = ph3(riemann=riemann)
@@ -129,7 +132,8 @@ def test_riemann_consistency_and_conservation(riemann, d):
                        rtol=1e-12, atol=1e-11)
 
 
-@pytest.mark.parametrize("riemann", [phy.RIEMANN_ROE, phy.RIEMANN_HLLC])
+@pytest.mark.parametrize("riemann", [phy.RIEMANN_ROE, phy.RIEMANN_HLLC, phy.RIEMANN_HLL,
+                                     phy.RIEMANN_AUSM])
 def test_riemann_supersonic_upwind_and_contact(riemann):
     ph = ph3(riemann=riemann)
     g = ph.gamma
@@ -139,10 +143,45 @@ def test_riemann_supersonic_upwind_and_contact(riemann):
     UL = phy.conservative(np.array([1.0]), np.array([[3.0 * cL, 0.1]]), np.array([pL]), ph)
     UR = phy.conservative(np.array([0.8]), np.array([[3.1 * cL, 0.0]]), np.array([pR]), ph)
     assert np.allclose(phy.riemann_flux(UL, UR, n, ph), phy.euler_flux(UL, ph)[:, 0], rtol=1e-12)
+    # supersonic flow from the right: the right state's flux
+    UL2 = phy.conservative(np.array([1.0]), np.array([[-3.0 * cL, 0.1]]), np.array([pL]), ph)
+    UR2 = phy.conservative(np.array([0.8]), np.array([[-3.1 * cL, 0.0]]), np.array([pR]), ph)
+    assert np.allclose(phy.riemann_flux(UL2, UR2, n, ph), phy.euler_flux(UR2, ph)[:, 0],
+                       rtol=1e-12)
+    if riemann == phy.RIEMANN_HLL:
+        return    # HLL smears contacts (one intermediate state)
     # stationary contact: same pressure, zero velocity, different density
     UL = phy.conservative(np.array([1.0]), np.array([[0.0, 0.0]]), np.array([pL]), ph)
     UR = phy.conservative(np.array([0.3]), np.array([[0.0, 0.0]]), np.array([pL]), ph)
     assert np.allclose(phy.riemann_flux(UL, UR, n, ph), [[0.0, pL, 0.0, 0.0]], atol=1e-12)
+
+
+@pytest.mark.parametrize("riemann", ALL_FLUXES)
+def test_riemann_flux_dissipates_linear_waves(riemann):
+    """Every flux adds dissipation, none adds energy: the DG Euler operator
+    linearised about a uniform subsonic stream on a periodic 2x2 mesh (P = 1)
+    has no eigenvalue with a positive real part beyond finite-difference
+    noise, while its most damped mode decays at a rate of the order of the
+    acoustic speed over the element size (a dissipation term of the wrong
+    sign would turn it into growth; a central flux without it would leave
+    every eigenvalue on the imaginary axis)."""
+    from oracle.dg import DG
+    import workloads as w
+    c = w.vortex_case(n=2, P=1, viscous=False, riemann=riemann)
+    c.phys.fid = phy.FIELD_UNIFORM
+    c.phys.fpar = (1.0, 3.0, 2.0, 0.0, 1.0)      # rho, u, v, w, T (|u| / c = 0.36)
+    dg = DG(c.mesh, c.P, c.Q, c.phys)
+    u0 = dg.project_exact()
+    n = u0.size
+    J = np.zeros((n, n))
+    for k in range(n):
+        e = np.zeros(n)
+        e[k] = 1e-6 * max(1.0, abs(u0.ravel()[k]))
+        J[:, k] = (dg.residual(u0 + e.reshape(u0.shape)) - dg.residual(u0 - e.reshape(u0.shape))).ravel() / (2 * e[k])
+    lam = np.linalg.eigvals(J)
+    scale = np.abs(lam).max()
+    assert lam.real.max() < 1e-6 * scale, lam.real.max() / scale
+    assert lam.real.min() < -1e-2 * scale
 
 
 def _fd_grad(fn, x, h):

@@ -26,6 +26,9 @@ FIELD_CYLINDER = 4   # uniform stream (1, 0, 0) at T = 1, rho = 1
 
 RIEMANN_ROE = 0
 RIEMANN_HLLC = 1
+RIEMANN_HLL = 2
+RIEMANN_LF = 3       # local Lax-Friedrichs (Rusanov)
+RIEMANN_AUSM = 4
 FORCING_NONE = 0
 FORCING_POISEUILLE = 1
 
@@ -94,6 +97,14 @@ def tgv_case(n=16, P=3, Q=None, Re=1600.0, Ma=0.1, riemann=RIEMANN_ROE):
     m = box_mesh(lines, (True, True, True))
     ph = Physics(Ma=Ma, Re=Re, fid=FIELD_TGV, riemann=riemann)
     return Case(f"tgv{n}^3_P{P}", m, P, Q, ph)
+
+
+def tgv_dt(n, P, Ma, cfl=0.10, factor=10.0):
+    """Time step of the Taylor-Green workloads: factor x the explicit step of
+    Eq. CFL (c_lambda = 0.2, d_RK = 2) at the given CFL on n^3 elements of the
+    periodic box [-pi, pi]^3, with c + |u| = 1/Ma + 1 (T = 1, |u| <= 1)."""
+    dx = 2 * np.pi / n
+    return factor * cfl * 2.0 * dx / (0.2 * (1.0 / Ma + 1.0) * P * P)
 
 
 def small_tgv_case(shape=(4, 3, 2), P=2, Q=None, Re=1600.0, Ma=0.1, riemann=RIEMANN_ROE,
