@@ -149,20 +149,34 @@ class BRJ:
     of G in grad Q) and the trace term with the numerical flux Jacobians
     dH^n/dQ^+- taken by the one-sided finite difference of
     Eq. numerical-Jac-on-traces (boundary states re-evaluated).  The two
-    terms with the trace-gradient and symmetric-flux Jacobians are neglected.
+    terms with the trace-gradient and symmetric-flux Jacobians are neglected
+    (the paper's choice), unless full=True:
+      term 4  (B^G)^T wJ (dH^n/d grad_j Q^+-) (d grad_j Q^+-/d u_e2): H^n
+              depends on the face gradients only through n . G({Q}, {grad Q})
+              (interior face: {grad Q} = the mean of the two sides; boundary:
+              the interior gradient), and G is linear in the gradient, so
+              dH^n_k/d(grad_j Q_l) = -c sum_i n_i G_ik({Q}, e_j (x) e_l),
+              c = 1/2 on interior and 1 on boundary faces;
+      term 5  the symmetric-flux lift sum_i integral d_i phi S_i with
+              dS/dQ^+- by the same one-sided difference as term 3;
+    both enter the diagonal blocks and, on interior faces, the neighbour
+    coupling (L + U), stored then as dense element-pair blocks per face.
     """
 
     assembly_dtype = np.float64
 
-    def __init__(self, dg, u, t, dt_a, J=7, omega=1.0, assembly_dtype=np.float64):
+    def __init__(self, dg, u, t, dt_a, J=7, omega=1.0, assembly_dtype=np.float64, full=False):
         """assembly_dtype: precision of the two volume-term contractions (float32
-        measures the rounding floor of a single-precision block assembly)."""
+        measures the rounding floor of a single-precision block assembly);
+        full: keep terms 4 and 5 of Eq. Jacobian-matrix-form2."""
         self.dg, self.J, self.omega, self.dt_a = dg, J, omega, dt_a
         self.assembly_dtype = assembly_dtype
+        self.full = full and dg.ph.viscous
         d, nv, nm, E = dg.dim, dg.nv, dg.nm, dg.E
         self.nb = nv * nm
         dLdu = self._volume_jacobian(u)                            # [E][v m][l n]
         self.off = []
+        self.off_full = []
         chi = trace_fd_steps(u)
         for g in dg.groups:
             JL, JR = self._trace_jacobians(g, u, t, chi)           # [f][p][k][l]
@@ -175,6 +189,12 @@ class BRJ:
                 blk = np.einsum("pm,fp,fpkl,pn->fkmln", BR, wJ, JR, BR, optimize=True)
                 np.add.at(dLdu, g["eR"], blk.reshape(-1, self.nb, self.nb))
                 self.off.append((g, JL, JR))
+            if self.full:
+                LL, LR, RL, RR = self._viscous_trace_blocks(g, u, t, chi)
+                np.add.at(dLdu, g["eL"], LL)
+                if g["bctype"] is None:
+                    np.add.at(dLdu, g["eR"], RR)
+                    self.off_full.append((g, LR, RL))
         # D = I - dt_a M^-1 dL/du (diagonal blocks), then invert
         Minv = dg.Minv
         MdL = np.einsum("emn,eknlo->ekmlo", Minv, dLdu.reshape(E, nv, nm, nv, nm))
@@ -225,6 +245,78 @@ class BRJ:
         Hh, _ = dg.face_flux(g, QL, QR, Qa, dQa, t)
         return Hh
 
+    def _symmetric_flux(self, g, QL, QR, t):
+        """S_i on group g as a function of the two traces (boundary: QR from
+        QL by the boundary condition), [f][p][i][v]."""
+        dg = self.dg
+        if g["bctype"] is None:
+            Qa = 0.5 * (QL + QR)
+            jump = QL - QR
+        else:
+            _, Qa, _ = phy.boundary_states(dg.ph, g["bctype"], g["x"], t, QL, g["n"])
+            jump = QL - Qa
+        S = phy.viscous_flux(Qa, g["n"][..., :, None] * jump[..., None, :], dg.ph)
+        if g["bctype"] == phy.BC_ADIA_WALL:
+            S[..., -1] = 0.0
+        return S
+
+    def _viscous_trace_blocks(self, g, u, t, chi):
+        """Terms 4 and 5 of Eq. Jacobian-matrix-form2 on group g as dense
+        blocks [f][v m][l n]: (dL_eL/du_eL, dL_eL/du_eR, dL_eR/du_eL,
+        dL_eR/du_eR); the last three are None on boundary faces."""
+        dg, ph = self.dg, self.dg.ph
+        d, nv, nb = dg.dim, dg.nv, self.nb
+        QL, QR, Qa, dQa, _, _ = dg.face_states(g, u, t)
+        n, wJ = g["n"], g["wJ"]
+        interior = g["bctype"] is None
+        c_grad = 0.5 if interior else 1.0
+        # physical derivative of each mode at the face points, [f][p][j][m]
+        GL = np.einsum("fprj,rpm->fpjm", g["ginvL"], np.asarray(dg.Df[g["fL"]]))
+        BL = dg.Bf[g["fL"]]
+        # term 4: dH^n_k / d(grad_j Q_l) (same on both sides of an interior face)
+        KG = np.zeros(QL.shape[:2] + (nv, d, nv))
+        for j in range(d):
+            for l in range(nv):
+                gu = np.zeros(QL.shape[:2] + (d, nv))
+                gu[..., j, l] = 1.0
+                Gu = phy.viscous_flux(Qa, gu, ph)                   # [f][p][i][k]
+                KG[..., j, l] = -c_grad * np.einsum("fpi,fpik->fpk", n, Gu)
+        if g["bctype"] == phy.BC_ADIA_WALL:
+            KG[..., -1, :, :] = 0.0
+        # term 5: dS_i / dQ^side by the one-sided difference of term 3
+        S0 = self._symmetric_flux(g, QL, QR, t)
+        SL = np.zeros(S0.shape + (nv,))
+        SR = np.zeros(S0.shape + (nv,))
+        for l in range(nv):
+            Qp = QL.copy()
+            Qp[..., l] += chi[l]
+            SL[..., l] = (self._symmetric_flux(g, Qp, QR, t) - S0) / chi[l]
+            if interior:
+                Qp = QR.copy()
+                Qp[..., l] += chi[l]
+                SR[..., l] = (self._symmetric_flux(g, QL, Qp, t) - S0) / chi[l]
+        c_sym = (0.5 if interior else 1.0) * ph.beta_s
+
+        def t4(Brow, G_col, sign):
+            # sign * sum_p Brow[p,m] wJ KG[p,k,j,l] G_col[p,j,n]
+            return sign * np.einsum("pm,fp,fpkjl,fpjn->fkmln", Brow, wJ, KG, G_col,
+                                    optimize=True).reshape(-1, nb, nb)
+
+        def t5(G_row, Sd, Bcol):
+            # c sum_p sum_i G_row[p,i,m] wJ dS_i,k/dQ_l B_col[p,n]
+            return c_sym * np.einsum("fpim,fp,fpikl,pn->fkmln", G_row, wJ, Sd, Bcol,
+                                     optimize=True).reshape(-1, nb, nb)
+
+        LL = t4(BL, GL, -1.0) + t5(GL, SL, BL)
+        if not interior:
+            return LL, None, None, None
+        GR = np.einsum("fprj,rpm->fpjm", g["ginvR"], np.asarray(dg.Df[g["fR"]]))
+        BR = dg.Bf[g["fR"]]
+        LR = t4(BL, GR, -1.0) + t5(GL, SR, BR)
+        RL = t4(BR, GL, +1.0) + t5(GR, SL, BL)
+        RR = t4(BR, GR, +1.0) + t5(GR, SR, BR)
+        return LL, LR, RL, RR
+
     def _trace_jacobians(self, g, u, t, chi):
         dg = self.dg
         nv = dg.nv
@@ -254,6 +346,13 @@ class BRJ:
             # dL_L/du_R q_R = -B_L^T wJ JR qR ; dL_R/du_L q_L = +B_R^T wJ JL qL
             out[g["eL"]] -= np.einsum("pm,fp,fpkl,fpl->fkm", dg.Bf[g["fL"]], wJ, JR, qR)
             out[g["eR"]] += np.einsum("pm,fp,fpkl,fpl->fkm", dg.Bf[g["fR"]], wJ, JL, qL)
+        shp = out.shape[1:]
+        for g, LR, RL in self.off_full:
+            # terms 4-5: dense neighbour blocks dL_eL/du_eR and dL_eR/du_eL
+            qR = q[g["eR"]].reshape(len(g["eR"]), -1)
+            qL = q[g["eL"]].reshape(len(g["eL"]), -1)
+            out[g["eL"]] += np.einsum("fab,fb->fa", LR, qR).reshape((-1,) + shp)
+            out[g["eR"]] += np.einsum("fab,fb->fa", RL, qL).reshape((-1,) + shp)
         return -self.dt_a * dg.apply_minv(out)
 
     def diag_solve(self, y):

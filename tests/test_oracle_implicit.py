@@ -365,3 +365,26 @@ def test_jvp_is_homogeneous_in_the_direction():
     for s in (1e-6, 1e6):
         js = im.jvp(dg, u, R, 0.0, s * v, 0.0, 1.0)
         assert np.linalg.norm(js / s - j1) < 1e-9 * np.linalg.norm(j1)
+
+
+# ------------------------------------------------------------------ terms 4-5 of the Jacobian
+
+@pytest.mark.parametrize("mk", [lambda: w.vortex_case(n=3, P=1, Re=20.0),
+                                lambda: w.poiseuille_case(2, nx=2, ny=2, Re=10.0),
+                                lambda: w.small_tgv_case((2, 2, 1), P=1, Re=20.0)])
+def test_brj_with_all_five_terms_equals_the_viscous_jacobian(mk):
+    """With viscosity, the kept-term block matrix D + (L + U) misses the
+    trace-gradient and symmetric-flux terms 4-5 of Eq. Jacobian-matrix-form2;
+    with them it equals dN/du = I - dt_a dR/du (dense central differences),
+    to the rounding of the one-sided trace differences; without them it
+    does not (periodic, Dirichlet and wall faces)."""
+    c = mk()
+    dg = DG(c.mesh, c.P, c.Q, c.phys)
+    u = perturbed_exact(dg) + 0.02 * w.random_direction(dg.project_exact(), 5)
+    dt_a = 0.01
+    Nj = np.eye(u.size) - dt_a * dense_jacobian(lambda x: dg.residual(x), u)
+    scale = np.abs(Nj - np.eye(u.size)).max()
+    full = assemble_brj(im.BRJ(dg, u, 0.0, dt_a, J=7, full=True), u.shape)
+    kept = assemble_brj(im.BRJ(dg, u, 0.0, dt_a, J=7), u.shape)
+    assert np.abs(full - Nj).max() < 1e-4 * scale
+    assert np.abs(kept - Nj).max() > 1e-2 * scale
