@@ -75,10 +75,10 @@ def job_throughput(units_per_rank, world, seconds):
 
 
 def tgv_dt(n, P, Ma, cfl=0.10, factor=10.0):
-    """dt = factor x the explicit step of Eq. CFL (c_lambda = 0.2, d_RK = 2) with
-    c + |u| = 1/Ma + 1 (T = 1, |u| <= 1 for the Taylor-Green field)."""
-    dx = 2 * math.pi / n
-    return factor * cfl * 2.0 * dx / (0.2 * (1.0 / Ma + 1.0) * P * P)
+    """dt = factor x the explicit step of Eq. CFL on the Taylor-Green box (the
+    workload's own rule)."""
+    import workloads as w
+    return w.tgv_dt(n, P, Ma, cfl, factor)
 
 
 def cylinder_dt(wl, frac=1.0):
@@ -197,6 +197,70 @@ def kernel_work(name, launches, E, nb, prec_bytes, P, Q):
     return None, None, None
 
 
+# ------------------------------------------------------------------ variants
+VARIANTS = [("fp64", "plain", True), ("fp32", "plain", False), ("fp32", "plain", True),
+            ("bf16", "plain", True), ("bf16", "extrap", True), ("bf16", "learned", True)]
+
+
+def time_variant(m, u0, dt, precision, guess, fused, steps, warmup, tableau=2):
+    """One form of the step (block precision, Newton initial guess, fused BRJ
+    sweeps) from the same initial field at the same Newton criterion: each
+    stage stops at alpha ||N(S_m)|| (alpha = 1e-3, an absolute number per
+    stage that every form computes from its own S_m).  W untimed steps (at
+    least 6 for the guess forms, whose network and extrapolation need a
+    history), then K steps timed with CUDA events on the launch stream; the
+    preconditioner is rebuilt every FREEZE steps in every form."""
+    import torch
+    import workloads as w
+    import paper_2002_04222_gb300 as dgl
+    u = u0.clone()
+    pc = dgl.Precond(m)
+    kw = dict(restart=30, rtol=5e-2, alpha=1e-3, J=7, precision=precision, tableau=tableau,
+              graphs=True, fused=fused)
+    g = None
+    if guess != "plain":
+        nb = m.info["n_var"] * m.info["n_mode"]
+        params = None
+        if guess == "learned":
+            params = []
+            for st in range(tableau):
+                params += w.mlp_params(3 * nb, 256, nb, seed=101 + st, zero_last=True)
+        g = dgl.Guess(m, params, stages=tableau, hidden=256, lr=1e-3)
+        kw["guess"] = g
+        kw["guess_train_iters"] = 4
+        warmup = max(warmup, 6)
+    state = {"k": 0, "t": 0.0}
+    stats = []
+
+    def step():
+        st = m.sdirk_step(u, state["t"], dt, precond=pc, rebuild=state["k"] % FREEZE == 0, **kw)
+        state["k"] += 1
+        state["t"] += dt
+        stats.append(st)
+
+    for _ in range(warmup):
+        step()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    stats.clear()
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    out = {"blocks": precision, "guess": guess, "fused": fused, "ms_per_step": round(ms, 3),
+           "newton_per_step": sum(s["newton_iters"] for s in stats) / steps,
+           "gmres_per_step": sum(s["gmres_iters"] for s in stats) / steps,
+           "converged": all(s["converged"] for s in stats),
+           "guess_used_per_step": sum(s["guess_used"] for s in stats) / steps}
+    pc.close()
+    if g is not None:
+        g.close()
+    return out
+
+
 # ------------------------------------------------------------------ our arm
 def run_ours(args, rank, world):
     import torch
@@ -292,6 +356,8 @@ def run_ours(args, rank, world):
         step(u)
     prof = dgl.profile_read()
     dgl.profile_enable(False)
+    # measured FP64 FMA throughput of this GPU (the residual kernels' pipe)
+    fp64_peak = dgl.peak_fp64(20)
     total_k = sum(v[1] for v in prof.values())
     dom = max(prof, key=lambda k: prof[k][1])
     pk, how = peaks()
@@ -304,14 +370,13 @@ def run_ours(args, rank, world):
     if tkey in TRAFFIC_PER_ELEM:
         roof["traffic"] = TRAFFIC_PER_ELEM[tkey] * E
         roof["traffic_source"] = "ncu dram bytes of a small-case capture scaled by elements"
-    clock_mhz = clk.get("sm_max_mhz") or pk.get("sm_max_mhz", 2070.0)
     if bound == "hbm":
         roof.update(bound="hbm", achieved=work / (avg_ms / 1e3) / 1e9, peak=pk["hbm_gbs"], unit="GB/s",
                     peak_source=how)
     elif bound == "alu":
-        peak = 4.0 * 152 * clock_mhz * 1e6 / 1e12   # FP64: 2 DFMA/clk/SM
-        roof.update(bound="alu", achieved=work / (avg_ms / 1e3) / 1e12, peak=peak, unit="TFLOP/s",
-                    peak_source="FP64 units x SM clock (152 SMs x 4 flop/clk x sm_max_mhz)")
+        roof.update(bound="alu", achieved=work / (avg_ms / 1e3) / 1e12, peak=fp64_peak,
+                    unit="TFLOP/s",
+                    peak_source="measured in this run: dg_peak_fp64 (FP64 FMA chains)")
     else:
         roof.update(bound=None, achieved=None, peak=None, unit=None)
     if roof.get("achieved") is not None:
@@ -329,6 +394,20 @@ def run_ours(args, rank, world):
     e1.record(stream)
     torch.cuda.synchronize()
     res_ms = e0.elapsed_time(e1) / nres
+    # the residual's roofline: algorithmic FP64 flops (the kernels' own count)
+    # over the measured FP64 FMA throughput of this GPU, taken in this run
+    rflops = sum(residual_flops_per_elem(wl["P"], wl["Q"]).values()) * E
+    res_roof = {"bound": "alu", "achieved": rflops / (res_ms / 1e3) / 1e12, "peak": fp64_peak,
+                "unit": "TFLOP/s", "frac": rflops / (res_ms / 1e3) / 1e12 / fp64_peak,
+                "flops_per_launch": rflops, "avg_ms": res_ms,
+                "peak_source": "measured in this run: dg_peak_fp64 (FP64 FMA chains at full "
+                               "occupancy, CUDA events)"}
+    for kname in ("dg_vol", "dg_face", "dg_lift"):
+        if kname in prof and not cyl:
+            kf = residual_flops_per_elem(wl["P"], wl["Q"])[kname] * E
+            kms = prof[kname][1] / prof[kname][0]
+            res_roof[kname] = {"avg_ms": round(kms, 4),
+                               "frac": round(kf / (kms / 1e3) / 1e12 / fp64_peak, 3)}
 
     # end to end through host buffers
     e2e = None
@@ -349,6 +428,11 @@ def run_ours(args, rank, world):
         e2e = {"value": job_throughput(ndof * args.steps, world, el), "unit": "DOF*step/s",
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
 
+    variants = None
+    if args.variants and not cyl:
+        u0 = m.project(0.0)
+        variants = [time_variant(m, u0, dt, p_, g_, f_, args.steps, args.warmup)
+                    for p_, g_, f_ in VARIANTS]
     newton = [s["newton_iters"] for s in timed_stats]
     gm = [s["gmres_iters"] for s in timed_stats]
     if cyl:
@@ -403,6 +487,8 @@ def run_ours(args, rank, world):
         "gpu_launches": launches,
         "clocks": clk,
         "roofline": roof,
+        "residual_roofline": res_roof,
+        "variants": variants,
         "kernels": kernels,
         "e2e": e2e,
     }
@@ -495,8 +581,12 @@ def main():
                     help="Newton initial guess: S_m, S_m + previous stage increment, or that plus "
                          "the learned MLP correction")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--fused", action="store_true",
-                    help="BRJ sweeps after the first as one off-diagonal + block kernel each")
+    ap.add_argument("--variants", action=argparse.BooleanOptionalAction, default=True,
+                    help="also time the step's forms (FP64/FP32/BF16 blocks, fused sweeps, "
+                         "extrapolated and learned guesses) in the same run")
+    ap.add_argument("--fused", action=argparse.BooleanOptionalAction, default=True,
+                    help="BRJ sweeps after the first as one off-diagonal + block kernel each "
+                         "(default; --no-fused: separate off-diagonal and block launches)")
     ap.add_argument("--workload", default="tgv", choices=["tgv", "tgv24", "cylinder"],
                     help="tgv: the Taylor-Green benchmark (default, 16^3 P=3); tgv24: 24^3 P=4 "
                          "Q=8; cylinder: the curved O-grid workload (SDIRK3, BF16 blocks, learned "

@@ -73,7 +73,13 @@ typedef struct {
   const int32_t* faces; /* host, n_faces*6 */
 } dg_mesh_desc;
 
-enum { DG_RIEMANN_ROE = 0, DG_RIEMANN_HLLC = 1 };
+/* Numerical advection fluxes (Sec. 4.3 lists them among the solvers'
+ * options): Roe without entropy fix; HLLC and HLL with Einfeldt
+ * (Roe-averaged) wave-speed estimates; local Lax-Friedrichs (Rusanov,
+ * penalty = the larger |u_n| + c of the two sides); AUSM of Liou and Steffen
+ * with the van Leer Mach-number and pressure splittings. */
+enum { DG_RIEMANN_ROE = 0, DG_RIEMANN_HLLC = 1, DG_RIEMANN_HLL = 2, DG_RIEMANN_LF = 3,
+       DG_RIEMANN_AUSM = 4 };
 enum { DG_BC_DIRICHLET = 1, DG_BC_ISO_WALL = 2, DG_BC_ADIA_WALL = 3, DG_BC_FARFIELD = 4 };
 enum { DG_FIELD_UNIFORM = 0, DG_FIELD_VORTEX = 1, DG_FIELD_POISEUILLE = 2, DG_FIELD_TGV = 3,
        DG_FIELD_CYLINDER = 4 };
@@ -105,7 +111,7 @@ enum { DG_FORCING_NONE = 0, DG_FORCING_POISEUILLE = 1 };
  * reflection forms.) */
 typedef struct {
   double gamma, Pr, Ma, Re, T_inf_K, beta_s;
-  int viscous, mu_law, riemann, forcing, field;
+  int viscous, mu_law, riemann /* DG_RIEMANN_* */, forcing, field;
   double fpar[8];
   int n_bc;
   int bc[8];
@@ -256,14 +262,26 @@ dg_status dg_gmres_noalloc(dg_mesh_t m, dg_precond_t p, const double* u, const d
                            double t, double dt_a, const double* b, double* x,
                            const dg_gmres_cfg* cfg, dg_gmres_stats* stats, void* stream);
 
-/* One SDIRK step (Sec. 3.2, Eq. rk-stage, rk-final; App. A tableaus): each
- * stage solves N(u) = u - S_m - dt a_mm R(u, t + c_m dt) = 0 by Newton
- * (Eq. Newton-Iteration) from u = S_m, stopping when ||N|| < alpha ||N(S_m)||
- * (Eq. nonlinear-critria) or, if abs_tol > 0, when ||N|| < abs_tol.  The
- * preconditioner in *p_inout is built at (u^n, t) when *p_inout is NULL or
+/* One implicit Runge-Kutta step (Sec. 3.2, Eq. rk-stage, rk-final; App. A
+ * tableaus): each implicit stage solves
+ *   N(u) = u - S_m - dt a_mm R(u, t + c_m dt) = 0,  S_m = u^n + sum_{j<m} a_mj E^j,
+ * by Newton (Eq. Newton-Iteration) from u = S_m, stopping when
+ * ||N|| < alpha ||N(S_m)|| (Eq. nonlinear-critria) or, if abs_tol > 0, when
+ * ||N|| < abs_tol; E^m = dt R(u^m) from the converged iterate, and
+ * u^{n+1} = u^n + sum_m b_m E^m.  Tableaus: DG_BE backward Euler (one stage,
+ * a = b = c = 1), DG_SDIRK2 (lambda = 1 - sqrt(2)/2), DG_SDIRK3
+ * (lambda = 0.4358665215), DG_ESDIRK4 the six-stage fourth-order table of
+ * App. A (explicit first stage, diagonal 1/4, stiffly accurate; its first
+ * column, printed as symbols, is read as a_i0 = a_i1, and its nodes are the
+ * row sums).  The preconditioner in *p_inout is built at (u^n, t) for
+ * dt a_mm (the diagonal all implicit stages share) when *p_inout is NULL or
  * rebuild != 0, and reused otherwise (freezing, Sec. 4.2.2); it is left in
- * *p_inout for the next step. */
-enum { DG_SDIRK2 = 2, DG_SDIRK3 = 3 };
+ * *p_inout for the next step.  A learned guess (cfg.guess) needs a tableau
+ * without an explicit stage and at most as many stages as the guess was
+ * created with (DG_ERR_UNSUPPORTED otherwise).  DG_ERR_ARG for an unknown
+ * tableau. */
+enum { DG_BE = 1, DG_SDIRK2 = 2, DG_SDIRK3 = 3, DG_ESDIRK4 = 4 };
+#define DG_MAX_STAGES 6
 typedef struct {
   int tableau;
   double alpha;
@@ -276,14 +294,30 @@ typedef struct {
   struct dg_guess_s* guess; /* optional learned initial guess (NULL: S_m) */
   int guess_train_iters;    /* Adam steps per converged stage */
 } dg_sdirk_cfg;
+/* Per-step statistics; the stage arrays hold the first DG_MAX_STAGES stages
+ * (an explicit stage reports 0 iterations and residuals). */
 typedef struct {
   int newton_iters, gmres_iters, stages, precond_built;
-  int stage_newton[4], stage_gmres[4];
-  double stage_res0[4], stage_res[4];
+  int stage_newton[DG_MAX_STAGES], stage_gmres[DG_MAX_STAGES];
+  double stage_res0[DG_MAX_STAGES], stage_res[DG_MAX_STAGES];
   int guess_used; /* stages that started from the learned guess */
 } dg_step_stats;
 dg_status sdirk_step(dg_mesh_t m, const dg_sdirk_cfg* cfg, double* u_inout, double t, double dt,
                      dg_precond_t* p_inout, dg_step_stats* stats, void* stream);
+
+/* One step of the second-order backward differentiation formula (Sec. 4.3
+ * lists BDF2 among the implicit schemes) at a constant step size dt:
+ *   3 u^{n+1} - 4 u^n + u^{n-1} = 2 dt R(u^{n+1}, t + dt),
+ * solved as one Newton stage N(u) = u - S - (2 dt/3) R(u, t + dt) with
+ * S = (4 u^n - u^{n-1})/3, from u = S, with the criteria, GMRES and
+ * preconditioner settings of cfg (tableau ignored; the preconditioner is
+ * built for dt_a = 2 dt/3).  u_inout holds u^n on entry and u^{n+1} on return;
+ * u_prev_inout holds u^{n-1} on entry and u^n on return (they must differ).
+ * The first step of a run needs u^{-1}: take it with sdirk_step.  cfg.guess
+ * must be NULL (DG_ERR_UNSUPPORTED).  stats->stages = 1. */
+dg_status bdf2_step(dg_mesh_t m, const dg_sdirk_cfg* cfg, double* u_inout, double* u_prev_inout,
+                    double t, double dt, dg_precond_t* p_inout, dg_step_stats* stats,
+                    void* stream);
 
 /* Learned Newton initial guess.  The paper's guess for stage m is S_m
  * (Eq. Newton-initial-guess); this optional extension starts Newton from

@@ -120,26 +120,51 @@ class Mesh:
         _check("dg_gmres_noalloc", code, ok=(0, _lib.DG_ERR_NOT_CONVERGED))
         return out, {f: getattr(st, f) for f, _ in _lib.GmresStats._fields_}
 
+    @staticmethod
+    def _step_cfg(tableau, alpha, abs_tol, max_newton, rebuild, use_precond, restart, max_cycles,
+                  rtol, J, precision, omega, guess, guess_train_iters, graphs, fused):
+        tab = _lib.TABLEAU[tableau] if isinstance(tableau, str) else tableau
+        return _lib.SdirkCfg(tab, alpha, abs_tol, max_newton, int(rebuild), int(use_precond),
+                             _lib.GmresCfg(restart, max_cycles, rtol, int(graphs)),
+                             _lib.PrecCfg(J, _lib.PREC[precision], omega, int(graphs), 0,
+                                          int(fused)),
+                             guess.handle if guess is not None else None, guess_train_iters)
+
     def sdirk_step(self, u, t, dt, precond=None, tableau=2, alpha=1e-3, abs_tol=0.0,
                    max_newton=20, rebuild=False, restart=30, max_cycles=10, rtol=5e-2,
                    J=7, precision="fp64", omega=1.0, use_precond=True, guess=None,
                    guess_train_iters=4, graphs=False, fused=False, stream=None):
-        """One SDIRK step in place on u; `precond` is a Precond holder whose
-        handle is built (or reused, frozen) by the library; `guess` an optional
-        Guess (learned initial guess, trained on the converged stages);
-        graphs=True replays the BRJ applies and the GMRES Arnoldi steps as
-        CUDA graphs; fused=True runs each BRJ sweep after the first as one
-        kernel."""
-        cfg = _lib.SdirkCfg(tableau, alpha, abs_tol, max_newton, int(rebuild), int(use_precond),
-                            _lib.GmresCfg(restart, max_cycles, rtol, int(graphs)),
-                            _lib.PrecCfg(J, _lib.PREC[precision], omega, int(graphs), 0,
-                                         int(fused)),
-                            guess.handle if guess is not None else None, guess_train_iters)
+        """One implicit Runge-Kutta step in place on u (tableau: 1/"be",
+        2/"sdirk2", 3/"sdirk3", 4/"esdirk4"); `precond` is a Precond holder
+        whose handle is built (or reused, frozen) by the library; `guess` an
+        optional Guess (learned initial guess, trained on the converged
+        stages); graphs=True replays the BRJ applies and the GMRES Arnoldi
+        steps as CUDA graphs; fused=True runs each BRJ sweep after the first
+        as one kernel."""
+        cfg = self._step_cfg(tableau, alpha, abs_tol, max_newton, rebuild, use_precond, restart,
+                             max_cycles, rtol, J, precision, omega, guess, guess_train_iters,
+                             graphs, fused)
         st = _lib.StepStats()
         holder = precond if precond is not None else Precond(self)
         code = self._lib.sdirk_step(self.handle, ctypes.byref(cfg), _ptr(u), t, dt,
                                     ctypes.byref(holder.handle), ctypes.byref(st), _stream(stream))
-        _check("sdirk_step", code, ok=(0, _lib.DG_ERR_NOT_CONVERGED))
+        return self._step_out("sdirk_step", code, st)
+
+    def bdf2_step(self, u, u_prev, t, dt, precond=None, alpha=1e-3, abs_tol=0.0, max_newton=20,
+                  rebuild=False, restart=30, max_cycles=10, rtol=5e-2, J=7, precision="fp64",
+                  omega=1.0, use_precond=True, graphs=False, fused=False, stream=None):
+        """One BDF2 step: u (u^n) becomes u^{n+1} and u_prev (u^{n-1}) becomes u^n."""
+        cfg = self._step_cfg(2, alpha, abs_tol, max_newton, rebuild, use_precond, restart,
+                             max_cycles, rtol, J, precision, omega, None, 0, graphs, fused)
+        st = _lib.StepStats()
+        holder = precond if precond is not None else Precond(self)
+        code = self._lib.bdf2_step(self.handle, ctypes.byref(cfg), _ptr(u), _ptr(u_prev), t, dt,
+                                   ctypes.byref(holder.handle), ctypes.byref(st), _stream(stream))
+        return self._step_out("bdf2_step", code, st)
+
+    @staticmethod
+    def _step_out(name, code, st):
+        _check(name, code, ok=(0, _lib.DG_ERR_NOT_CONVERGED))
         out = {f: getattr(st, f) for f, _ in _lib.StepStats._fields_}
         for k in ("stage_newton", "stage_gmres", "stage_res0", "stage_res"):
             out[k] = list(out[k])[: st.stages]
@@ -184,6 +209,13 @@ class Precond:
 def kernel_launches():
     """Number of CUDA kernels the library has launched since it was loaded."""
     return int(lib().dg_kernel_launches())
+
+
+def peak_fp64(reps=20, stream=None):
+    """Measured FP64 FMA throughput (TFLOP/s) of the current GPU (dg_peak_fp64)."""
+    out = ctypes.c_double()
+    _check("dg_peak_fp64", lib().dg_peak_fp64(reps, ctypes.byref(out), _stream(stream)))
+    return out.value
 
 
 def profile_enable(on=True):

@@ -70,11 +70,15 @@ class SdirkCfg(ctypes.Structure):
                 ("guess_train_iters", ctypes.c_int)]
 
 
+MAX_STAGES = 6   # DG_MAX_STAGES of include/dg.h
+TABLEAU = {"be": 1, "sdirk2": 2, "sdirk3": 3, "esdirk4": 4}
+
+
 class StepStats(ctypes.Structure):
     _fields_ = [("newton_iters", ctypes.c_int), ("gmres_iters", ctypes.c_int), ("stages", ctypes.c_int),
-                ("precond_built", ctypes.c_int), ("stage_newton", ctypes.c_int * 4),
-                ("stage_gmres", ctypes.c_int * 4), ("stage_res0", ctypes.c_double * 4),
-                ("stage_res", ctypes.c_double * 4), ("guess_used", ctypes.c_int)]
+                ("precond_built", ctypes.c_int), ("stage_newton", ctypes.c_int * MAX_STAGES),
+                ("stage_gmres", ctypes.c_int * MAX_STAGES), ("stage_res0", ctypes.c_double * MAX_STAGES),
+                ("stage_res", ctypes.c_double * MAX_STAGES), ("guess_used", ctypes.c_int)]
 
 
 class GuessCfg(ctypes.Structure):
@@ -111,6 +115,8 @@ SIGNATURES = {
     "dg_gmres_noalloc": [VP, VP, VP, VP, D, D, VP, VP, ctypes.POINTER(GmresCfg),
                          ctypes.POINTER(GmresStats), VP],
     "sdirk_step": [VP, ctypes.POINTER(SdirkCfg), VP, D, D, ctypes.POINTER(VP), ctypes.POINTER(StepStats), VP],
+    "bdf2_step": [VP, ctypes.POINTER(SdirkCfg), VP, VP, D, D, ctypes.POINTER(VP),
+                  ctypes.POINTER(StepStats), VP],
     "dg_status_string": [I],
     "dg_kernel_launches": [],
     "dg_autotune": [VP, I, ctypes.POINTER(TuneResult), VP],

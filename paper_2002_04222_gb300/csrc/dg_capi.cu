@@ -315,6 +315,7 @@ dg_status dg_mesh_create(const dg_mesh_desc* md, const dg_physics* ph, void* str
   if (md->geom_order != 1 && md->geom_order != 2) return DG_ERR_UNSUPPORTED;
   if (!supported(d, md->P, md->Q)) return DG_ERR_UNSUPPORTED;
   if (ph->n_bc < 0 || ph->n_bc > 8) return DG_ERR_ARG;
+  if (ph->riemann < DG_RIEMANN_ROE || ph->riemann > DG_RIEMANN_AUSM) return DG_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   const int E = md->n_elem, F = md->n_faces;
   // axis-aligned affine boxes take the diagonal-metric kernels; any other
@@ -756,148 +757,265 @@ dg_status dg_gmres(dg_mesh_t m, dg_precond_t p, const double* u, const double* r
   return gmres_impl(m, p, u, r_u, t, dt_a, b, x, cfg, stats, (cudaStream_t)stream);
 }
 
-// ---------------------------------------------------------------- SDIRK
-static void tableau(int which, double A[3][3], double* b, double* c, int* M) {
-  std::memset(A, 0, sizeof(double) * 9);
-  if (which == DG_SDIRK3) {
+// ---------------------------------------------------------------- SDIRK, BDF2
+struct Tableau {
+  int M;
+  double A[DG_MAX_STAGES][DG_MAX_STAGES], b[DG_MAX_STAGES], c[DG_MAX_STAGES];
+  double gdiag;  // the diagonal shared by the implicit stages
+};
+
+// Butcher tables of App. A (and backward Euler).  The six-stage fourth-order
+// table is printed with symbols in its first column; each names the entry
+// beside it (a_i0 = a_i1), the nodes are the row sums and the weights the
+// last row (stiffly accurate).
+static bool make_tableau(int which, Tableau& T) {
+  std::memset(&T, 0, sizeof(T));
+  if (which == DG_BE) {
+    T.M = 1;
+    T.A[0][0] = 1.0;
+    T.b[0] = 1.0;
+  } else if (which == DG_SDIRK2) {
+    const double l = 1.0 - std::sqrt(2.0) / 2.0;
+    T.M = 2;
+    T.A[0][0] = l;
+    T.A[1][0] = 1 - l;
+    T.A[1][1] = l;
+    T.b[0] = 1 - l;
+    T.b[1] = l;
+  } else if (which == DG_SDIRK3) {
     const double l = 0.4358665215;
     const double b1 = (-6 * l * l + 16 * l - 1) / 4, b2 = (6 * l * l - 20 * l + 5) / 4;
-    A[0][0] = l;
-    A[1][0] = (1 - l) / 2;
-    A[1][1] = l;
-    A[2][0] = b1;
-    A[2][1] = b2;
-    A[2][2] = l;
-    b[0] = b1;
-    b[1] = b2;
-    b[2] = l;
-    *M = 3;
+    T.M = 3;
+    T.A[0][0] = l;
+    T.A[1][0] = (1 - l) / 2;
+    T.A[1][1] = l;
+    T.A[2][0] = b1;
+    T.A[2][1] = b2;
+    T.A[2][2] = l;
+    T.b[0] = b1;
+    T.b[1] = b2;
+    T.b[2] = l;
+  } else if (which == DG_ESDIRK4) {
+    const double r = std::sqrt(2.0);
+    T.M = 6;
+    T.A[1][1] = 0.25;
+    T.A[2][1] = (1 - r) / 8;
+    T.A[2][2] = 0.25;
+    T.A[3][1] = (5 - 7 * r) / 64;
+    T.A[3][2] = 7 * (1 + r) / 32;
+    T.A[3][3] = 0.25;
+    T.A[4][1] = (-13796 - 54539 * r) / 125000;
+    T.A[4][2] = (506605 + 132109 * r) / 437500;
+    T.A[4][3] = 166 * (-97 + 376 * r) / 109375;
+    T.A[4][4] = 0.25;
+    T.A[5][1] = (1181 - 987 * r) / 13782;
+    T.A[5][2] = 47 * (-267 + 1783 * r) / 273343;
+    T.A[5][3] = -16 * (-22922 + 3525 * r) / 571953;
+    T.A[5][4] = -15625 * (97 + 376 * r) / 90749876;
+    T.A[5][5] = 0.25;
+    for (int i = 1; i < 6; ++i) T.A[i][0] = T.A[i][1];
+    for (int j = 0; j < 6; ++j) T.b[j] = T.A[5][j];
   } else {
-    const double l = 1.0 - std::sqrt(2.0) / 2.0;
-    A[0][0] = l;
-    A[1][0] = 1 - l;
-    A[1][1] = l;
-    b[0] = 1 - l;
-    b[1] = l;
-    *M = 2;
+    return false;
   }
-  for (int i = 0; i < *M; ++i) {
-    c[i] = 0;
-    for (int j = 0; j <= i; ++j) c[i] += A[i][j];
+  for (int i = 0; i < T.M; ++i) {
+    T.c[i] = 0;
+    for (int j = 0; j <= i; ++j) T.c[i] += T.A[i][j];
+    if (T.gdiag == 0.0) T.gdiag = T.A[i][i];
+  }
+  return true;
+}
+
+static dg_status check_step_cfg(const dg_sdirk_cfg* cfg) {
+  if (cfg->gmres.restart < 1 || cfg->gmres.restart > MAX_RESTART || cfg->gmres.max_cycles < 1 ||
+      !(cfg->gmres.rtol > 0.0) || cfg->max_newton < 0)
+    return DG_ERR_ARG;
+  return DG_OK;
+}
+
+// the step's device vectors: E^0..E^5, S, U, R, N and the learned guess's
+// candidate U2, R2, N2
+static dg_status step_buffers(dg_mesh_s* m, double** Ev, double** rest) {
+  const size_t n = (size_t)m->ndof;
+  if (!m->stage) DG_CUDA(cudaMalloc(&m->stage, sizeof(double) * n * (DG_MAX_STAGES + 7)));
+  for (int i = 0; i < DG_MAX_STAGES; ++i) Ev[i] = m->stage + i * n;
+  for (int i = 0; i < 7; ++i) rest[i] = m->stage + (DG_MAX_STAGES + i) * n;
+  return DG_OK;
+}
+
+struct StageResult {
+  int it = 0, gits = 0;
+  double res0 = 0.0, res = 0.0;
+  bool conv = false;
+  int guess_used = 0;
+};
+
+// Newton (Eq. Newton-Iteration) on N(u) = u - S - dta R(u, ti) from u = S, or
+// from the learned guess of stage gstage when it lowers ||N||; stops at
+// ||N|| < alpha ||N(S)|| (abs_tol instead when > 0; an absolute number in
+// every case once a guess is in use).  On return U holds the iterate, R its
+// residual R(U, ti) and N = N(U) (the candidate buffers may have been swapped
+// in).
+static dg_status newton_stage(dg_mesh_s* m, const dg_sdirk_cfg* cfg, dg_precond_s* P,
+                              dg_guess_s* G, int gstage, const double* Sv, double ti, double dta,
+                              double*& U, double*& R, double*& Nn, double*& U2, double*& R2,
+                              double*& N2, StageResult* out, cudaStream_t s) {
+  const long long n = m->ndof;
+  double* dx = m->w1;
+  StageResult o;
+  DG_CUDA(cudaMemcpyAsync(U, Sv, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  DG_TRY(dg_residual(m, U, ti, R, s));
+  DG_TRY(newton_resid(Nn, U, Sv, R, dta, n, s));
+  double res;
+  DG_TRY(host_norm(m, Nn, &res, s));
+  o.res0 = res;
+  const double tol = cfg->abs_tol > 0.0 ? cfg->abs_tol : cfg->alpha * o.res0;
+  // with a learned guess the criterion stays alpha ||N(S)||, as an absolute tolerance
+  const bool abs_mode = cfg->abs_tol > 0.0 || G != nullptr;
+  if (G) {
+    int ready = 0;
+    DG_TRY(dg_guess_ready(G, gstage, &ready));
+    if (ready) {
+      DG_TRY(dg_guess_predict(G, gstage, Sv, U2, s));
+      DG_TRY(dg_residual(m, U2, ti, R2, s));
+      DG_TRY(newton_resid(N2, U2, Sv, R2, dta, n, s));
+      double resc;
+      const dg_status ns = host_norm(m, N2, &resc, s);
+      if (ns != DG_OK && ns != DG_ERR_NONFINITE) return ns;
+      // a non-finite candidate (e.g. a predicted state without positive
+      // density) is rejected like any guess that does not lower ||N||
+      if (ns == DG_OK && resc < o.res0) {
+        std::swap(U, U2);
+        std::swap(R, R2);
+        std::swap(Nn, N2);
+        res = resc;
+        o.guess_used = 1;
+      }
+    }
+  }
+  while (true) {
+    if (res <= 0.0 || ((o.it > 0 || abs_mode) && res < tol)) {
+      o.conv = true;
+      break;
+    }
+    if (o.it >= cfg->max_newton) break;
+    dg_gmres_stats gs{};
+    dg_status g = gmres_impl(m, P, U, R, ti, dta, Nn, dx, &cfg->gmres, &gs, s);
+    if (g != DG_OK && g != DG_ERR_NOT_CONVERGED) return g;
+    o.gits += gs.iters;
+    DG_TRY(axpby(U, 1.0, dx, 1.0, n, s));
+    ++o.it;
+    DG_TRY(dg_residual(m, U, ti, R, s));
+    DG_TRY(newton_resid(Nn, U, Sv, R, dta, n, s));
+    DG_TRY(host_norm(m, Nn, &res, s));
+  }
+  o.res = res;
+  *out = o;
+  return DG_OK;
+}
+
+static void record_stage(dg_step_stats& st, int i, const StageResult& o) {
+  st.newton_iters += o.it;
+  st.gmres_iters += o.gits;
+  st.guess_used += o.guess_used;
+  if (i < DG_MAX_STAGES) {
+    st.stage_newton[i] = o.it;
+    st.stage_gmres[i] = o.gits;
+    st.stage_res0[i] = o.res0;
+    st.stage_res[i] = o.res;
   }
 }
 
 dg_status sdirk_step(dg_mesh_t m, const dg_sdirk_cfg* cfg, double* u_n, double t, double dt,
                      dg_precond_t* p_inout, dg_step_stats* stats, void* stream) {
   if (!m || !cfg || !u_n || !(dt > 0.0)) return DG_ERR_ARG;
-  if (cfg->tableau != DG_SDIRK2 && cfg->tableau != DG_SDIRK3) return DG_ERR_ARG;
+  Tableau T;
+  if (!make_tableau(cfg->tableau, T)) return DG_ERR_ARG;
   if (cfg->use_precond && !p_inout) return DG_ERR_ARG;
-  if (cfg->gmres.restart < 1 || cfg->gmres.restart > MAX_RESTART || cfg->gmres.max_cycles < 1 ||
-      !(cfg->gmres.rtol > 0.0) || cfg->max_newton < 0)
-    return DG_ERR_ARG;
+  DG_TRY(check_step_cfg(cfg));
+  dg_guess_s* G = cfg->guess;
+  // the learned guess keeps one network per stage, at most four; the explicit
+  // first stage of the fourth-order scheme would shift the stage indices
+  if (G && (T.M > guess_stage_count(G) || T.A[0][0] == 0.0)) return DG_ERR_UNSUPPORTED;
   cudaStream_t s = (cudaStream_t)stream;
   const long long n = m->ndof;
-  double A[3][3], b[3], c[3];
-  int M;
-  tableau(cfg->tableau, A, b, c, &M);
-  if (!m->stage) DG_CUDA(cudaMalloc(&m->stage, sizeof(double) * (size_t)n * 10));
-  double* Ev[3] = {m->stage, m->stage + n, m->stage + 2 * n};
-  double* Sv = m->stage + 3 * n;
-  double* U = m->stage + 4 * n;
-  double* R = m->stage + 5 * n;
-  double* Nn = m->stage + 6 * n;
-  double* dx = m->w1;
+  double *Ev[DG_MAX_STAGES], *B[7];
+  DG_TRY(step_buffers(m, Ev, B));
+  double *Sv = B[0], *U = B[1], *R = B[2], *Nn = B[3], *U2 = B[4], *R2 = B[5], *N2 = B[6];
   dg_step_stats st{};
-  st.stages = M;
+  st.stages = T.M;
   dg_precond_s* P = nullptr;
   if (cfg->use_precond) {
+    // every implicit stage shares the diagonal a_mm, hence one preconditioner
     if (!*p_inout || cfg->rebuild) {
-      DG_TRY(dg_precond_build(m, u_n, t, dt * A[0][0], &cfg->prec, p_inout, s));
+      DG_TRY(dg_precond_build(m, u_n, t, dt * T.gdiag, &cfg->prec, p_inout, s));
       st.precond_built = 1;
     }
     P = *p_inout;
   }
   dg_status result = DG_OK;
-  dg_guess_s* G = cfg->guess;
-  // candidate buffers for the learned guess (swapped with U, R, N when taken)
-  double* U2 = m->stage + 7 * n;
-  double* R2 = m->stage + 8 * n;
-  double* N2 = m->stage + 9 * n;
   if (G && guess_history_empty(G)) DG_TRY(dg_guess_push(G, u_n, s));
-  for (int i = 0; i < M; ++i) {
+  for (int i = 0; i < T.M; ++i) {
     // S_i = u^n + sum_{j<i} a_ij E^j
     DG_CUDA(cudaMemcpyAsync(Sv, u_n, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-    for (int j = 0; j < i; ++j) DG_TRY(axpby(Sv, A[i][j], Ev[j], 1.0, n, s));
-    DG_CUDA(cudaMemcpyAsync(U, Sv, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-    const double ti = t + c[i] * dt, dta = dt * A[i][i];
-    DG_TRY(dg_residual(m, U, ti, R, s));
-    DG_TRY(newton_resid(Nn, U, Sv, R, dta, n, s));
-    double res;
-    DG_TRY(host_norm(m, Nn, &res, s));
-    const double res0 = res;
-    const double tol = cfg->abs_tol > 0.0 ? cfg->abs_tol : cfg->alpha * res0;
-    // with a learned guess the criterion stays alpha ||N(S_i)||, as an absolute tolerance
-    const bool abs_mode = cfg->abs_tol > 0.0 || G != nullptr;
-    if (G) {
-      int ready = 0;
-      DG_TRY(dg_guess_ready(G, i, &ready));
-      if (ready) {
-        DG_TRY(dg_guess_predict(G, i, Sv, U2, s));
-        DG_TRY(dg_residual(m, U2, ti, R2, s));
-        DG_TRY(newton_resid(N2, U2, Sv, R2, dta, n, s));
-        double resc;
-        const dg_status ns = host_norm(m, N2, &resc, s);
-        if (ns != DG_OK && ns != DG_ERR_NONFINITE) return ns;
-        // a non-finite candidate (e.g. a predicted state without positive
-        // density) is rejected like any guess that does not lower ||N||
-        if (ns == DG_OK && resc < res0) {
-          std::swap(U, U2);
-          std::swap(R, R2);
-          std::swap(Nn, N2);
-          res = resc;
-          st.guess_used++;
-        }
-      }
+    for (int j = 0; j < i; ++j) DG_TRY(axpby(Sv, T.A[i][j], Ev[j], 1.0, n, s));
+    const double ti = t + T.c[i] * dt, dta = dt * T.A[i][i];
+    StageResult o;
+    if (dta == 0.0) {
+      // explicit stage: u^i = S_i
+      DG_TRY(dg_residual(m, Sv, ti, R, s));
+      o.conv = true;
+    } else {
+      DG_TRY(newton_stage(m, cfg, P, G, i, Sv, ti, dta, U, R, Nn, U2, R2, N2, &o, s));
     }
-    int it = 0, gits = 0;
-    bool conv = false;
-    while (true) {
-      if (res <= 0.0 || ((it > 0 || abs_mode) && res < tol)) {
-        conv = true;
-        break;
-      }
-      if (it >= cfg->max_newton) break;
-      dg_gmres_stats gs{};
-      dg_status g = gmres_impl(m, P, U, R, ti, dta, Nn, dx, &cfg->gmres, &gs, s);
-      if (g != DG_OK && g != DG_ERR_NOT_CONVERGED) return g;
-      gits += gs.iters;
-      DG_TRY(axpby(U, 1.0, dx, 1.0, n, s));
-      ++it;
-      DG_TRY(dg_residual(m, U, ti, R, s));
-      DG_TRY(newton_resid(Nn, U, Sv, R, dta, n, s));
-      DG_TRY(host_norm(m, Nn, &res, s));
-    }
-    if (!conv) result = DG_ERR_NOT_CONVERGED;
-    st.newton_iters += it;
-    st.gmres_iters += gits;
-    if (i < 4) {
-      st.stage_newton[i] = it;
-      st.stage_gmres[i] = gits;
-      st.stage_res0[i] = res0;
-      st.stage_res[i] = res;
-    }
+    if (!o.conv) result = DG_ERR_NOT_CONVERGED;
+    record_stage(st, i, o);
     // E^i = dt R(u^i) from the residual of the converged iterate
     DG_TRY(axpby(Ev[i], dt, R, 0.0, n, s));
     // the converged stage trains the stage's network (needs a full history)
     // (and its increment becomes the extrapolation base of the next step)
-    if (G && conv)
+    if (G && o.conv)
       DG_TRY(dg_guess_train(G, i, Sv, U, cfg->guess_train_iters, nullptr, nullptr, nullptr, s));
   }
-  for (int i = 0; i < M; ++i) DG_TRY(axpby(u_n, b[i], Ev[i], 1.0, n, s));
+  for (int i = 0; i < T.M; ++i) DG_TRY(axpby(u_n, T.b[i], Ev[i], 1.0, n, s));
   if (G) DG_TRY(dg_guess_push(G, u_n, s));
   DG_CUDA(cudaStreamSynchronize(s));
   if (stats) *stats = st;
   return result;
+}
+
+dg_status bdf2_step(dg_mesh_t m, const dg_sdirk_cfg* cfg, double* u_n, double* u_prev, double t,
+                    double dt, dg_precond_t* p_inout, dg_step_stats* stats, void* stream) {
+  if (!m || !cfg || !u_n || !u_prev || u_n == u_prev || !(dt > 0.0)) return DG_ERR_ARG;
+  if (cfg->use_precond && !p_inout) return DG_ERR_ARG;
+  if (cfg->guess) return DG_ERR_UNSUPPORTED;
+  DG_TRY(check_step_cfg(cfg));
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long n = m->ndof;
+  double *Ev[DG_MAX_STAGES], *B[7];
+  DG_TRY(step_buffers(m, Ev, B));
+  double *Sv = B[0], *U = B[1], *R = B[2], *Nn = B[3], *U2 = B[4], *R2 = B[5], *N2 = B[6];
+  const double dta = 2.0 * dt / 3.0;
+  dg_step_stats st{};
+  st.stages = 1;
+  dg_precond_s* P = nullptr;
+  if (cfg->use_precond) {
+    if (!*p_inout || cfg->rebuild) {
+      DG_TRY(dg_precond_build(m, u_n, t, dta, &cfg->prec, p_inout, s));
+      st.precond_built = 1;
+    }
+    P = *p_inout;
+  }
+  // S = (4 u^n - u^{n-1}) / 3
+  DG_TRY(lincomb(Sv, u_n, 4.0 / 3.0, u_prev, -1.0 / 3.0, n, s));
+  StageResult o;
+  DG_TRY(newton_stage(m, cfg, P, nullptr, 0, Sv, t + dt, dta, U, R, Nn, U2, R2, N2, &o, s));
+  record_stage(st, 0, o);
+  DG_CUDA(cudaMemcpyAsync(u_prev, u_n, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  DG_CUDA(cudaMemcpyAsync(u_n, U, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  DG_CUDA(cudaStreamSynchronize(s));
+  if (stats) *stats = st;
+  return o.conv ? DG_OK : DG_ERR_NOT_CONVERGED;
 }
 
 }  // extern "C"

@@ -94,7 +94,7 @@ struct dg_mesh_s {
   double* hdev = nullptr;       // [2*(mmax+2)] Hessenberg column on device
   double* hhost = nullptr;      // pinned host mirror
   // SDIRK workspace
-  double* stage = nullptr;      // [4 + 3][ndof]: E^0..E^3, S, R, N
+  double* stage = nullptr;      // [DG_MAX_STAGES + 7][ndof]: E^0..E^5, S, U, R, N, U2, R2, N2
   std::vector<std::vector<int>> elem_faces;  // host: face id of (e, lf)
   // graph replay of GMRES Arnoldi steps (one instantiated graph per step index
   // and operand set; see gmres_impl)
@@ -179,6 +179,7 @@ bool tune_valid(dg_mesh_s* m, const dg_tune_result* t);
 // learned initial guess (dg_learned.cu)
 bool guess_history_empty(const dg_guess_s* g);
 bool guess_history_full(const dg_guess_s* g);
+int guess_stage_count(const dg_guess_s* g);
 
 // dense vector kernels (dg_blas.cu)
 constexpr int RED_BLOCKS = 296;   // 2 per SM: fixed, so reductions repeat bitwise

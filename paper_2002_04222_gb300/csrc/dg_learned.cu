@@ -535,6 +535,7 @@ namespace dg {
 
 bool guess_history_empty(const dg_guess_s* g) { return g->nhist == 0; }
 bool guess_history_full(const dg_guess_s* g) { return g->nhist >= 2; }
+int guess_stage_count(const dg_guess_s* g) { return g->M; }
 
 static dg_status guess_features(dg_guess_s* g, int st, cudaStream_t s) {
   const double* h0 = g->hist[g->head];

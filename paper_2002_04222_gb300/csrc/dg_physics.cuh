@@ -224,13 +224,116 @@ __device__ inline void hllc_flux(const double* UL, const double* UR, const doubl
   }
 }
 
+// HLL flux (one intermediate state between the fastest waves; Toro, Ch. 10)
+// with the same Einfeldt speed estimates as hllc_flux.
+template <int D>
+__device__ inline void hll_flux(const double* UL, const double* UR, const double* n,
+                                const Phys& ph, double* Fh) {
+  double FL[D + 2], FR[D + 2], vL[D], vR[D], pL, pR;
+  euler_flux_n<D>(UL, n, ph, FL, pL, vL);
+  euler_flux_n<D>(UR, n, ph, FR, pR, vR);
+  double rL = UL[0], rR = UR[0];
+  double cL = sqrt(ph.gamma * pL / rL), cR = sqrt(ph.gamma * pR / rR);
+  double HL = (UL[D + 1] + pL) / rL, HR = (UR[D + 1] + pR) / rR;
+  double sL = sqrt(rL), sR = sqrt(rR);
+  double isum = 1.0 / (sL + sR);
+  double q2 = 0, unt = 0, unL = 0, unR = 0;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    double u = (sL * vL[k] + sR * vR[k]) * isum;
+    q2 += u * u;
+    unt += u * n[k];
+    unL += vL[k] * n[k];
+    unR += vR[k] * n[k];
+  }
+  double Ht = (sL * HL + sR * HR) * isum;
+  double ct = sqrt(ph.gm1 * (Ht - 0.5 * q2));
+  double SL = fmin(unL - cL, unt - ct);
+  double SR = fmax(unR + cR, unt + ct);
+  if (SL >= 0.0) {
+#pragma unroll
+    for (int v = 0; v < D + 2; ++v) Fh[v] = FL[v];
+  } else if (SR <= 0.0) {
+#pragma unroll
+    for (int v = 0; v < D + 2; ++v) Fh[v] = FR[v];
+  } else {
+    const double idS = 1.0 / (SR - SL);
+#pragma unroll
+    for (int v = 0; v < D + 2; ++v) Fh[v] = (SR * FL[v] - SL * FR[v] + SL * SR * (UR[v] - UL[v])) * idS;
+  }
+}
+
+// Local Lax-Friedrichs (Rusanov): mean normal flux minus the jump times half
+// the larger spectral radius |u_n| + c of the two sides.
+template <int D>
+__device__ inline void lf_flux(const double* UL, const double* UR, const double* n,
+                               const Phys& ph, double* Fh) {
+  double FL[D + 2], FR[D + 2], vL[D], vR[D], pL, pR;
+  euler_flux_n<D>(UL, n, ph, FL, pL, vL);
+  euler_flux_n<D>(UR, n, ph, FR, pR, vR);
+  double unL = 0, unR = 0;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    unL += vL[k] * n[k];
+    unR += vR[k] * n[k];
+  }
+  const double lam = fmax(fabs(unL) + sqrt(ph.gamma * pL / UL[0]),
+                          fabs(unR) + sqrt(ph.gamma * pR / UR[0]));
+#pragma unroll
+  for (int v = 0; v < D + 2; ++v) Fh[v] = 0.5 * (FL[v] + FR[v]) - 0.5 * lam * (UR[v] - UL[v]);
+}
+
+// AUSM (Liou and Steffen 1993): interface Mach number from the van Leer
+// splittings M+(M_L) + M-(M_R) carries the upwinded c (rho, rho u, rho H); the
+// pressure splittings p+(M_L) p_L + p-(M_R) p_R act on the momentum.
+template <int D>
+__device__ inline void ausm_flux(const double* UL, const double* UR, const double* n,
+                                 const Phys& ph, double* Fh) {
+  double irL, vL[D], pL, TL, irR, vR[D], pR, TR;
+  primitives<D>(UL, ph, irL, vL, pL, TL);
+  primitives<D>(UR, ph, irR, vR, pR, TR);
+  const double cL = sqrt(ph.gamma * pL * irL), cR = sqrt(ph.gamma * pR * irR);
+  double unL = 0, unR = 0;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    unL += vL[k] * n[k];
+    unR += vR[k] * n[k];
+  }
+  const double ML = unL / cL, MR = unR / cR;
+  double Mp, Mm, Pp, Pm;
+  if (fabs(ML) <= 1.0) {
+    Mp = 0.25 * (ML + 1.0) * (ML + 1.0);
+    Pp = Mp * (2.0 - ML);
+  } else {
+    Mp = 0.5 * (ML + fabs(ML));
+    Pp = ML > 0.0 ? 1.0 : 0.0;
+  }
+  if (fabs(MR) <= 1.0) {
+    Mm = -0.25 * (MR - 1.0) * (MR - 1.0);
+    Pm = -Mm * (2.0 + MR);
+  } else {
+    Mm = 0.5 * (MR - fabs(MR));
+    Pm = MR < 0.0 ? 1.0 : 0.0;
+  }
+  const double mh = Mp + Mm, ph2 = Pp * pL + Pm * pR;
+  const double a = 0.5 * (mh + fabs(mh)), b = 0.5 * (mh - fabs(mh));  // upwind weights
+  // c (rho, rho u, rho H) of each side
+  Fh[0] = a * cL * UL[0] + b * cR * UR[0];
+#pragma unroll
+  for (int k = 0; k < D; ++k) Fh[1 + k] = a * cL * UL[1 + k] + b * cR * UR[1 + k] + ph2 * n[k];
+  Fh[D + 1] = a * cL * (UL[D + 1] + pL) + b * cR * (UR[D + 1] + pR);
+}
+
 template <int D>
 __device__ inline void riemann_flux(const double* UL, const double* UR, const double* n,
                                     const Phys& ph, double* Fh) {
-  if (ph.riemann == DG_RIEMANN_HLLC)
-    hllc_flux<D>(UL, UR, n, ph, Fh);
-  else
-    roe_flux<D>(UL, UR, n, ph, Fh);
+  switch (ph.riemann) {
+    case DG_RIEMANN_HLLC: hllc_flux<D>(UL, UR, n, ph, Fh); break;
+    case DG_RIEMANN_HLL: hll_flux<D>(UL, UR, n, ph, Fh); break;
+    case DG_RIEMANN_LF: lf_flux<D>(UL, UR, n, ph, Fh); break;
+    case DG_RIEMANN_AUSM: ausm_flux<D>(UL, UR, n, ph, Fh); break;
+    default: roe_flux<D>(UL, UR, n, ph, Fh);
+  }
 }
 
 // ------------------------------------------------------------ analytic fields
@@ -705,11 +808,11 @@ __device__ inline void numerical_flux_axis(const double* QL, const double* QRin,
       Qj[v] = QR[v];
     }
   }
-  if (ph.riemann == DG_RIEMANN_HLLC) {
+  if (ph.riemann != DG_RIEMANN_ROE) {
     double n[D];
 #pragma unroll
     for (int k = 0; k < D; ++k) n[k] = k == R ? sgn : 0.0;
-    hllc_flux<D>(QL, QR, n, ph, Hn);
+    riemann_flux<D>(QL, QR, n, ph, Hn);
   } else {
     roe_flux_axis<D, R>(QL, QR, sgn, ph, Hn);
   }

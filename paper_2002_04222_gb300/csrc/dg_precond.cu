@@ -1157,6 +1157,11 @@ struct BRJImpl {
       tc_done = true;
       }
     }
+    if (!tc_done && invert_rows_supported(nb, std::is_same<T, double>::value)) {
+      // panel in registers, deferred row interchanges (dg_invert.cu)
+      DG_TRY(launch_invert_rows(blk, std::is_same<T, double>::value, E, nb, ld, fail, s));
+      tc_done = true;
+    }
     if (!tc_done) {
       const size_t ism = sizeof(T) * ((size_t)2 * nb * IB + IB + nb) + sizeof(int) * nb;
       DG_CUDA(cudaFuncSetAttribute(brj_invert_blocked_kernel<T, IB>,

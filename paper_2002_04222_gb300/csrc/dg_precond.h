@@ -46,5 +46,10 @@ dg_status dispatch_sweep(dg_precond_s* p, const double* qprev, const double* q, 
 // the apply as plain kernel launches on s (for capture inside a larger graph)
 dg_status precond_sweeps(dg_precond_s* p, const double* q, double* out, cudaStream_t s);
 void precond_drop_graphs(dg_precond_s* p);
+// in-place inversion of E blocks nb x nb (row stride ld), panel in registers
+// (dg_invert.cu); supported for nb up to 640 (FP32) / 384 (FP64)
+bool invert_rows_supported(int nb, bool fp64);
+dg_status launch_invert_rows(void* blocks, bool fp64, int E, int nb, int ld, int* fail,
+                             cudaStream_t s);
 inline dg_mesh_s* precond_mesh(dg_precond_s* p) { return p->mesh; }
 }  // namespace dg

@@ -48,6 +48,8 @@ def test_null_handles_and_pointers_are_rejected(lib):
         "dg_gmres_noalloc": (NULL, NULL, NULL, NULL, d(0.0), d(0.1), NULL, NULL,
                              ctypes.byref(gcfg), NULL, NULL),
         "sdirk_step": (NULL, NULL, NULL, d(0.0), d(0.1), NULL, NULL, NULL),
+        "bdf2_step": (NULL, NULL, NULL, NULL, d(0.0), d(0.1), NULL, NULL, NULL),
+        "dg_peak_fp64": (0, NULL, NULL),
         "dg_autotune": (NULL, 1, NULL, NULL),
         "dg_set_tune": (NULL, NULL),
         "dg_guess_create": (NULL, NULL, NULL, ctypes.byref(out)),
