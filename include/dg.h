@@ -187,6 +187,16 @@ typedef struct {
                     (J-1 fewer launches and no HBM round trip of the sweep's
                     right-hand side; bitwise the same result; one more
                     n_dof-vector of device memory) */
+  int full_jacobian; /* != 0: keep terms 4 and 5 of Eq. Jacobian-matrix-form2,
+                    which the paper neglects: the numerical flux's dependence
+                    on the face gradients (dH^n/d grad_j Q = -c n . dG/d grad_j Q,
+                    c = 1/2 inside and 1 on a boundary, exact since G is linear
+                    in the gradient) and the symmetric-flux lift with dS/dQ by
+                    the one-sided difference of Eq. numerical-Jac-on-traces, in
+                    the diagonal blocks and in the neighbour coupling (L+U);
+                    viscous flows on meshes of axis-aligned elements, not with
+                    fused (DG_ERR_UNSUPPORTED otherwise); 3 (NV D NV) values per
+                    face point and side are stored */
 } dg_prec_cfg;
 
 /* Build (or rebuild in place, when *inout is not NULL and was built for the

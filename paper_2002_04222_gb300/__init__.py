@@ -122,18 +122,20 @@ class Mesh:
 
     @staticmethod
     def _step_cfg(tableau, alpha, abs_tol, max_newton, rebuild, use_precond, restart, max_cycles,
-                  rtol, J, precision, omega, guess, guess_train_iters, graphs, fused):
+                  rtol, J, precision, omega, guess, guess_train_iters, graphs, fused,
+                  full_jacobian=False):
         tab = _lib.TABLEAU[tableau] if isinstance(tableau, str) else tableau
         return _lib.SdirkCfg(tab, alpha, abs_tol, max_newton, int(rebuild), int(use_precond),
                              _lib.GmresCfg(restart, max_cycles, rtol, int(graphs)),
                              _lib.PrecCfg(J, _lib.PREC[precision], omega, int(graphs), 0,
-                                          int(fused)),
+                                          int(fused), int(full_jacobian)),
                              guess.handle if guess is not None else None, guess_train_iters)
 
     def sdirk_step(self, u, t, dt, precond=None, tableau=2, alpha=1e-3, abs_tol=0.0,
                    max_newton=20, rebuild=False, restart=30, max_cycles=10, rtol=5e-2,
                    J=7, precision="fp64", omega=1.0, use_precond=True, guess=None,
-                   guess_train_iters=4, graphs=False, fused=False, stream=None):
+                   guess_train_iters=4, graphs=False, fused=False, full_jacobian=False,
+                   stream=None):
         """One implicit Runge-Kutta step in place on u (tableau: 1/"be",
         2/"sdirk2", 3/"sdirk3", 4/"esdirk4"); `precond` is a Precond holder
         whose handle is built (or reused, frozen) by the library; `guess` an
@@ -143,7 +145,7 @@ class Mesh:
         as one kernel."""
         cfg = self._step_cfg(tableau, alpha, abs_tol, max_newton, rebuild, use_precond, restart,
                              max_cycles, rtol, J, precision, omega, guess, guess_train_iters,
-                             graphs, fused)
+                             graphs, fused, full_jacobian)
         st = _lib.StepStats()
         holder = precond if precond is not None else Precond(self)
         code = self._lib.sdirk_step(self.handle, ctypes.byref(cfg), _ptr(u), t, dt,
@@ -181,8 +183,11 @@ class Precond:
         self._lib = lib()
 
     def build(self, u, t=0.0, dt_a=0.0, J=7, precision="fp64", omega=1.0, graphs=False,
-              tc_invert=False, fused=False, stream=None):
-        cfg = _lib.PrecCfg(J, _lib.PREC[precision], omega, int(graphs), int(tc_invert), int(fused))
+              tc_invert=False, fused=False, full_jacobian=False, stream=None):
+        """dg_precond_build; full_jacobian=True keeps terms 4-5 of the element
+        Jacobian (the paper neglects them)."""
+        cfg = _lib.PrecCfg(J, _lib.PREC[precision], omega, int(graphs), int(tc_invert), int(fused),
+                           int(full_jacobian))
         _check("dg_precond_build", self._lib.dg_precond_build(
             self.mesh.handle, _ptr(u), t, dt_a, ctypes.byref(cfg), ctypes.byref(self.handle),
             _stream(stream)))

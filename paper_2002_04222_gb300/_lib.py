@@ -50,7 +50,8 @@ class MeshInfo(ctypes.Structure):
 
 class PrecCfg(ctypes.Structure):
     _fields_ = [("J", ctypes.c_int), ("precision", ctypes.c_int), ("omega", ctypes.c_double),
-                ("graphs", ctypes.c_int), ("tc_invert", ctypes.c_int), ("fused", ctypes.c_int)]
+                ("graphs", ctypes.c_int), ("tc_invert", ctypes.c_int), ("fused", ctypes.c_int),
+                ("full_jacobian", ctypes.c_int)]
 
 
 class GmresCfg(ctypes.Structure):

@@ -10,7 +10,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdgjfnk.so")
 SOURCES = ["dg_residual.cu", "dg_precond.cu", "dg_blas.cu", "dg_capi.cu", "dg_noalloc.cu",
-           "dg_learned.cu", "dg_geometry.cu", "dg_sweep.cu", "dg_diag.cu", "dg_invert.cu"]
+           "dg_learned.cu", "dg_geometry.cu", "dg_sweep.cu", "dg_diag.cu", "dg_invert.cu",
+           "dg_brj_visc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xptxas", "-warn-spills"]

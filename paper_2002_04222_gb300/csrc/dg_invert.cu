@@ -205,27 +205,35 @@ __global__ void __launch_bounds__(MAXT) brj_invert_rows_kernel(T* __restrict__ b
 #pragma unroll
       for (int o = 0; o < B; ++o)
         if (o < nout) A[(long long)outRow[o] * ld + c] = ov[o];
-      // rows outside K: A[i][c] + sum_j T[i][j] ak[j]; rows in K: sum_j T[i][j] ak[j]
-      for (int i0 = 0; i0 < nb; i0 += 8) {
-        T acc[8];
+      // rows outside K: A[i][c] + sum_j T[i][j] ak[j]; rows in K: sum_j T[i][j] ak[j];
+      // eight rows per batch, the next batch's loads issued before this
+      // batch's products (different rows of the column: no overlap)
+      auto load8 = [&](int i0, T* v) {
 #pragma unroll
         for (int t = 0; t < 8; ++t) {
           const int i = i0 + t;
-          acc[t] = (i < nb && (i < k0 || i >= k0 + bw)) ? A[(long long)i * ld + c] : (T)0;
+          v[t] = (i < nb && (i < k0 || i >= k0 + bw)) ? A[(long long)i * ld + c] : (T)0;
         }
+      };
+      T cur[8], nxt[8];
+      load8(0, cur);
+      for (int i0 = 0; i0 < nb; i0 += 8) {
+        if (i0 + 8 < nb) load8(i0 + 8, nxt);
 #pragma unroll
         for (int t = 0; t < 8; ++t) {
           const int i = i0 + t;
           if (i >= nb) break;
           const T* u = P + i * B;
-          T a = acc[t];
+          T a = cur[t];
 #pragma unroll
           for (int j = 0; j < B; ++j) a += u[j] * ak[j];
-          acc[t] = a;
+          cur[t] = a;
         }
 #pragma unroll
         for (int t = 0; t < 8; ++t)
-          if (i0 + t < nb) A[(long long)(i0 + t) * ld + c] = acc[t];
+          if (i0 + t < nb) A[(long long)(i0 + t) * ld + c] = cur[t];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) cur[t] = nxt[t];
       }
     }
     __syncthreads();

@@ -1142,6 +1142,8 @@ struct BRJImpl {
           m->tab, m->geo, m->minv, e0, Wbuf, Jd, dta, blk, ld));
       DG_LAUNCHED(1);
     }
+    if (pc->full)  // terms 4-5 of the element with itself, before the inversion
+      DG_TRY(visc_build(m, pc, t, dta, blk, ld, std::is_same<T, double>::value, s));
     int* fail = (int*)(m->scratch + 16);
     DG_CUDA(cudaMemsetAsync(fail, 0, sizeof(int), s));
     constexpr int IB = 32;  // panel width of the blocked inversion
@@ -1310,6 +1312,7 @@ dg_status precond_sweeps(dg_precond_s* pc, const double* q, double* out, cudaStr
   if (pc->omega != 1.0) DG_TRY(axpby(cur, 0.0, cur, pc->omega, pc->mesh->ndof, s));
   for (int j = 1; j < pc->J; ++j) {
     DG_TRY(dispatch_offdiag(pc, cur, q, pc->y, s));
+    if (pc->full) DG_TRY(visc_offdiag(pc, cur, pc->y, s));  // terms 4-5 of (L+U)
     double* nxt = j == pc->J - 1 ? out : pc->qh;
     if (nxt != cur && pc->omega != 1.0)
       DG_CUDA(cudaMemcpyAsync(nxt, cur, sizeof(double) * pc->mesh->ndof, cudaMemcpyDeviceToDevice, s));
@@ -1392,6 +1395,9 @@ static void free_precond(dg_precond_s* p) {
   cudaFree(p->qh2);
   cudaFree(p->y);
   cudaFree(p->work);
+  cudaFree(p->jk);
+  cudaFree(p->jsd);
+  cudaFree(p->jso);
   precond_drop_graphs(p);
   if (p->cs) cudaStreamDestroy(p->cs);
   if (p->ev_in) cudaEventDestroy(p->ev_in);
@@ -1416,8 +1422,11 @@ dg_status dg_precond_build(dg_mesh_t m, const double* u, double t, double dt_a,
   // kernels has not found, so that configuration is not offered (FP32 and
   // BF16 blocks cover the curved workloads at every P)
   if (cfg->precision == DG_PREC_FP64 && m->curved && m->P > 2) return DG_ERR_UNSUPPORTED;
+  // terms 4-5: viscous flows on axis-aligned elements, the two-kernel sweeps
+  const int full = cfg->full_jacobian && m->phys.viscous;
+  if (full && (m->curved || cfg->fused || !visc_supported(d, m->P, m->Q))) return DG_ERR_UNSUPPORTED;
   dg_precond_s* p = *inout;
-  if (p && (p->mesh != m || p->precision != cfg->precision)) {
+  if (p && (p->mesh != m || p->precision != cfg->precision || p->full != full)) {
     free_precond(p);
     *inout = nullptr;
     p = nullptr;
@@ -1451,6 +1460,13 @@ dg_status dg_precond_build(dg_mesh_t m, const double* u, double t, double dt_a,
     alloc((void**)&p->qh, sizeof(double) * (size_t)m->ndof);
     alloc((void**)&p->y, sizeof(double) * (size_t)m->ndof);
     alloc(&p->work, p->work_bytes);
+    if (full) {
+      p->full = 1;
+      const size_t nv3 = (size_t)E * 2 * d * m->nf * visc_values_per_face_point(d) * vb;
+      alloc(&p->jk, nv3);
+      alloc(&p->jsd, nv3);
+      alloc(&p->jso, nv3);
+    }
     // zero padding columns once: the block kernels never write them
     if (err == cudaSuccess) err = cudaMemset(p->blocks, 0, bsz * (size_t)E * nb * ld);
     if (err == cudaSuccess) err = cudaMemset(p->work, 0, p->work_bytes);

@@ -33,6 +33,12 @@ struct dg_precond_s {
   int tc_invert = 0;      // FP32 blocks: trailing updates of the inversion on the tensor cores
   int fused = 0;          // sweeps j >= 2 as one off-diagonal + block kernel
   double* qh2 = nullptr;  // [ndof] second iterate buffer of the fused sweeps (lazily allocated)
+  // terms 4-5 of the element Jacobian (full_jacobian): per element face and
+  // point, K = s wJ dH/d grad Q [k][j][l], S_own / S_nbr = c wJ dS/dQ [i][k][l]
+  int full = 0;
+  void* jk = nullptr;
+  void* jsd = nullptr;
+  void* jso = nullptr;
   std::vector<Graph> graphs;
   cudaStream_t cs = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -49,6 +55,14 @@ void precond_drop_graphs(dg_precond_s* p);
 // in-place inversion of E blocks nb x nb (row stride ld), panel in registers
 // (dg_invert.cu); supported for nb up to 640 (FP32) / 384 (FP64)
 bool invert_rows_supported(int nb, bool fp64);
+// terms 4-5 (dg_brj_visc.cu): supported (dim, P, Q), values per face point
+// and side of each of the three arrays, build (after the block assembly,
+// before the inversion) and the off-diagonal addition y += dt_a M^-1 (...) qh
+bool visc_supported(int dim, int P, int Q);
+size_t visc_values_per_face_point(int dim);
+dg_status visc_build(dg_mesh_s* m, dg_precond_s* pc, double t, double dta, void* blk, int ld,
+                     bool fp64, cudaStream_t s);
+dg_status visc_offdiag(dg_precond_s* pc, const double* qh, double* y, cudaStream_t s);
 dg_status launch_invert_rows(void* blocks, bool fp64, int E, int nb, int ld, int* fail,
                              cudaStream_t s);
 inline dg_mesh_s* precond_mesh(dg_precond_s* p) { return p->mesh; }
