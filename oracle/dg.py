@@ -65,6 +65,16 @@ class DG:
         else:
             self.wf = np.ones(1)
         self._build_faces()
+        # shock-capturing sensor (Sec. 3.1.2): L2 projection onto polynomials of
+        # degree <= P-1 per direction at the Gauss points (reference element)
+        L = np.stack([bs.jacobi(k, 0.0, 0.0, xq)[0] for k in range(P)], axis=1)  # [Q][P]
+        W1 = np.diag(wq)
+        pi1 = L @ np.linalg.solve(L.T @ W1 @ L, L.T @ W1)
+        Pi = np.ones((1, 1))
+        for _ in range(d):
+            Pi = np.kron(pi1, Pi)          # first direction fastest
+        self.sensor_proj = Pi
+        self.h_elem = self.vol ** (1.0 / d)
 
     # ------------------------------------------------------------------ faces
     def _side_geometry(self, elems, lf):
@@ -125,18 +135,53 @@ class DG:
         Qr, Qb, _ = phy.boundary_states(self.ph, g["bctype"], g["x"], t, QL, g["n"])
         return QL, Qr, Qb, dQL, dQL, None
 
-    def face_flux(self, g, QL, QR, Qa, dQa, t):
+    # ------------------------------------------------------ shock capturing
+    def sensor(self, u):
+        """Persson-Peraire modal-decay sensor (Sec. 3.1.2 cites it) per element:
+        s_e = log10(|rho - Pi rho|^2 / |rho|^2), Pi the L2 projection of the
+        density onto polynomials of degree <= P-1 per direction, both norms in
+        the reference element (Gauss rule, exact for these degrees); S_e = 0 for
+        s_e < s0 - kappa, 1 for s_e > s0 + kappa and (1 + sin(pi (s_e - s0) /
+        (2 kappa))) / 2 between, s0 = log10(1/P^4)."""
+        ph = self.ph
+        rq = self.values(u[:, :1], self.B)[..., 0]                     # [E][q]
+        dr = rq - rq @ self.sensor_proj.T
+        num = np.einsum("q,eq->e", self.w, dr * dr)
+        den = np.einsum("q,eq->e", self.w, rq * rq)
+        with np.errstate(divide="ignore"):
+            se = np.log10(num / den)
+        s0, kap = np.log10(1.0 / self.P ** 4), ph.av_kappa
+        ramp = 0.5 * (1.0 + np.sin(np.pi * np.clip(se - s0, -kap, kap) / (2.0 * kap)))
+        return np.where(se < s0 - kap, 0.0, np.where(se > s0 + kap, 1.0, ramp))
+
+    def av_factor(self, u):
+        """mu_0 S_e h_e / P per element (h_e = |Omega_e|^(1/d)); zeros without
+        shock capturing."""
+        if not getattr(self.ph, "av", 0):
+            return np.zeros(self.E)
+        return self.ph.av_mu0 * self.sensor(u) * self.h_elem / self.P
+
+    def face_av(self, g, fac, QL, QR):
+        """Artificial viscosity at the face points: the mean of the two sides'
+        values from their own traces (a boundary face: the interior side's)."""
+        aL = phy.artificial_viscosity(QL, fac[g["eL"]][:, None], self.ph)
+        if g["bctype"] is None:
+            return 0.5 * (aL + phy.artificial_viscosity(QR, fac[g["eR"]][:, None], self.ph))
+        return aL
+
+    def face_flux(self, g, QL, QR, Qa, dQa, t, mu_av=None):
         """Numerical normal flux H^n = F^n - G^n and symmetric fluxes S_j on the
         face points of group g (owner-side normal).  QR is the exterior state
         of the Riemann flux and Qa the state of the viscous flux; the jump is
-        Q_L - Q_R on interior faces and Q_L - Q_b on boundary faces."""
+        Q_L - Q_R on interior faces and Q_L - Q_b on boundary faces.  mu_av:
+        artificial viscosity at the face points (None: none)."""
         n = g["n"]
         Fh = phy.riemann_flux(QL, QR, n, self.ph)
         if not self.ph.viscous:
             return Fh, None
         jump = QL - (QR if g["bctype"] is None else Qa)
-        S = phy.viscous_flux(Qa, n[..., :, None] * jump[..., None, :], self.ph)   # [f][p][i][v]
-        Gv = phy.viscous_flux(Qa, dQa, self.ph) - g["beta"][:, None, None, None] * S
+        S = phy.viscous_flux(Qa, n[..., :, None] * jump[..., None, :], self.ph, mu_av)   # [f][p][i][v]
+        Gv = phy.viscous_flux(Qa, dQa, self.ph, mu_av) - g["beta"][:, None, None, None] * S
         Gh = np.einsum("fpi,fpiv->fpv", n, Gv)
         if g["bctype"] == phy.BC_ADIA_WALL:
             Gh[..., -1] = 0.0
@@ -154,14 +199,18 @@ class DG:
         ph = self.ph
         Qv = self.values(u, self.B)
         dQ = self.gradients(u, self.D, self.ginv)
+        av = getattr(ph, "av", 0)
+        fac = self.av_factor(u) if av else None
         H = phy.euler_flux(Qv, ph)
         if ph.viscous:
-            H = H - phy.viscous_flux(Qv, dQ, ph)
+            mu_q = phy.artificial_viscosity(Qv, fac[:, None], ph) if av else None
+            H = H - phy.viscous_flux(Qv, dQ, ph, mu_q)
         Ht = np.einsum("eqrj,eqjv->eqrv", self.ginv, H) * self.wJ[:, :, None, None]
         L = sum(np.einsum("qm,eqv->evm", self.D[r], Ht[:, :, r]) for r in range(self.dim))
         for g in (self.groups if faces else []):
             QL, QR, Qa, dQa, _, _ = self.face_states(g, u, t)
-            Hh, S = self.face_flux(g, QL, QR, Qa, dQa, t)
+            mu_f = self.face_av(g, fac, QL, QR) if av else None
+            Hh, S = self.face_flux(g, QL, QR, Qa, dQa, t, mu_f)
             wJ = g["wJ"]
             L[g["eL"]] -= np.einsum("pm,fpv->fvm", self.Bf[g["fL"]], Hh * wJ[..., None])
             c = (0.5 if g["bctype"] is None else 1.0) * ph.beta_s

@@ -174,6 +174,9 @@ class BRJ:
         self.full = full and dg.ph.viscous
         d, nv, nm, E = dg.dim, dg.nv, dg.nm, dg.E
         self.nb = nv * nm
+        # artificial viscosity frozen at u (Sec. 4.2.2: its derivatives are neglected)
+        self.av = getattr(dg.ph, "av", 0) and dg.ph.viscous
+        self.fac = dg.av_factor(u) if self.av else None
         dLdu = self._volume_jacobian(u)                            # [E][v m][l n]
         self.off = []
         self.off_full = []
@@ -207,6 +210,8 @@ class BRJ:
         d, nv, nm, E = dg.dim, dg.nv, dg.nm, dg.E
         Qv = dg.values(u, dg.B)
         dQ = dg.gradients(u, dg.D, dg.ginv)
+        mu_q = (phy.artificial_viscosity(Qv, self.fac[:, None], ph)
+                if getattr(self, "av", 0) else None)
         h = 1e-30
         # A0[e,q,j,k,l] = dH_jk/dQ_l at fixed grad Q (complex step)
         A0 = np.zeros(Qv.shape[:2] + (d, nv, nv))
@@ -215,7 +220,7 @@ class BRJ:
             Qc[..., l] += 1j * h
             Hc = phy.euler_flux(Qc, ph)
             if ph.viscous:
-                Hc = Hc - phy.viscous_flux(Qc, dQ.astype(complex), ph)
+                Hc = Hc - phy.viscous_flux(Qc, dQ.astype(complex), ph, mu_q)
             A0[..., l] = Hc.imag / h
         # A1[e,q,j,i,k,l] = dH_jk / d(grad_i Q_l) = -G_jk(Q, e_i (x) e_l)
         A1 = np.zeros(Qv.shape[:2] + (d, d, nv, nv))
@@ -224,7 +229,7 @@ class BRJ:
                 for l in range(nv):
                     gu = np.zeros(dQ.shape)
                     gu[..., i, l] = 1.0
-                    A1[..., :, i, :, l] = -phy.viscous_flux(Qv, gu, ph)
+                    A1[..., :, i, :, l] = -phy.viscous_flux(Qv, gu, ph, mu_q)
         # physical derivative tables DB[e,j,q,m] = sum_r ginv[e,q,r,j] D_r[q,m]
         DB = np.einsum("eqrj,rqm->ejqm", dg.ginv, dg.D)
         wJ = dg.wJ
@@ -234,7 +239,7 @@ class BRJ:
         T += np.einsum("eq,ejqm,eqjikl,eiqn->ekmln", c(wJ), c(DB), c(A1), c(DB), optimize=True)
         return T.astype(np.float64).reshape(E, nv * nm, nv * nm)
 
-    def _flux_only(self, g, QL, QR, dQa, t):
+    def _flux_only(self, g, QL, QR, dQa, t, mu_f=None):
         """H^n on group g as a function of the two traces at fixed gradients;
         on boundary faces QR is recomputed from QL by the boundary condition."""
         dg = self.dg
@@ -242,10 +247,10 @@ class BRJ:
             Qa = 0.5 * (QL + QR)
         else:
             QR, Qa, _ = phy.boundary_states(dg.ph, g["bctype"], g["x"], t, QL, g["n"])
-        Hh, _ = dg.face_flux(g, QL, QR, Qa, dQa, t)
+        Hh, _ = dg.face_flux(g, QL, QR, Qa, dQa, t, mu_f)
         return Hh
 
-    def _symmetric_flux(self, g, QL, QR, t):
+    def _symmetric_flux(self, g, QL, QR, t, mu_f=None):
         """S_i on group g as a function of the two traces (boundary: QR from
         QL by the boundary condition), [f][p][i][v]."""
         dg = self.dg
@@ -255,7 +260,7 @@ class BRJ:
         else:
             _, Qa, _ = phy.boundary_states(dg.ph, g["bctype"], g["x"], t, QL, g["n"])
             jump = QL - Qa
-        S = phy.viscous_flux(Qa, g["n"][..., :, None] * jump[..., None, :], dg.ph)
+        S = phy.viscous_flux(Qa, g["n"][..., :, None] * jump[..., None, :], dg.ph, mu_f)
         if g["bctype"] == phy.BC_ADIA_WALL:
             S[..., -1] = 0.0
         return S
@@ -267,6 +272,7 @@ class BRJ:
         dg, ph = self.dg, self.dg.ph
         d, nv, nb = dg.dim, dg.nv, self.nb
         QL, QR, Qa, dQa, _, _ = dg.face_states(g, u, t)
+        mu_f = dg.face_av(g, self.fac, QL, QR) if self.av else None
         n, wJ = g["n"], g["wJ"]
         interior = g["bctype"] is None
         c_grad = 0.5 if interior else 1.0
@@ -279,22 +285,22 @@ class BRJ:
             for l in range(nv):
                 gu = np.zeros(QL.shape[:2] + (d, nv))
                 gu[..., j, l] = 1.0
-                Gu = phy.viscous_flux(Qa, gu, ph)                   # [f][p][i][k]
+                Gu = phy.viscous_flux(Qa, gu, ph, mu_f)             # [f][p][i][k]
                 KG[..., j, l] = -c_grad * np.einsum("fpi,fpik->fpk", n, Gu)
         if g["bctype"] == phy.BC_ADIA_WALL:
             KG[..., -1, :, :] = 0.0
         # term 5: dS_i / dQ^side by the one-sided difference of term 3
-        S0 = self._symmetric_flux(g, QL, QR, t)
+        S0 = self._symmetric_flux(g, QL, QR, t, mu_f)
         SL = np.zeros(S0.shape + (nv,))
         SR = np.zeros(S0.shape + (nv,))
         for l in range(nv):
             Qp = QL.copy()
             Qp[..., l] += chi[l]
-            SL[..., l] = (self._symmetric_flux(g, Qp, QR, t) - S0) / chi[l]
+            SL[..., l] = (self._symmetric_flux(g, Qp, QR, t, mu_f) - S0) / chi[l]
             if interior:
                 Qp = QR.copy()
                 Qp[..., l] += chi[l]
-                SR[..., l] = (self._symmetric_flux(g, QL, Qp, t) - S0) / chi[l]
+                SR[..., l] = (self._symmetric_flux(g, QL, Qp, t, mu_f) - S0) / chi[l]
         c_sym = (0.5 if interior else 1.0) * ph.beta_s
 
         def t4(Brow, G_col, sign):
@@ -321,17 +327,18 @@ class BRJ:
         dg = self.dg
         nv = dg.nv
         QL, QR, Qa, dQa, _, _ = dg.face_states(g, u, t)
-        H0 = self._flux_only(g, QL, QR, dQa, t)
+        mu_f = dg.face_av(g, self.fac, QL, QR) if self.av else None
+        H0 = self._flux_only(g, QL, QR, dQa, t, mu_f)
         JL = np.zeros(QL.shape + (nv,))
         JR = np.zeros(QL.shape + (nv,))
         for l in range(nv):
             Qp = QL.copy()
             Qp[..., l] += chi[l]
-            JL[..., l] = (self._flux_only(g, Qp, QR, dQa, t) - H0) / chi[l]
+            JL[..., l] = (self._flux_only(g, Qp, QR, dQa, t, mu_f) - H0) / chi[l]
             if g["bctype"] is None:
                 Qp = QR.copy()
                 Qp[..., l] += chi[l]
-                JR[..., l] = (self._flux_only(g, QL, Qp, dQa, t) - H0) / chi[l]
+                JR[..., l] = (self._flux_only(g, QL, Qp, dQa, t, mu_f) - H0) / chi[l]
         return JL, JR
 
     def offdiag(self, q):

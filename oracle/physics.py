@@ -10,7 +10,7 @@ import numpy as np
 
 # identifiers shared with the workloads package (plain integers)
 BC_DIRICHLET, BC_ISO_WALL, BC_ADIA_WALL, BC_FARFIELD = 1, 2, 3, 4
-FIELD_UNIFORM, FIELD_VORTEX, FIELD_POISEUILLE, FIELD_TGV, FIELD_CYLINDER = 0, 1, 2, 3, 4
+FIELD_UNIFORM, FIELD_VORTEX, FIELD_POISEUILLE, FIELD_TGV, FIELD_CYLINDER, FIELD_SHOCK = 0, 1, 2, 3, 4, 5
 RIEMANN_ROE, RIEMANN_HLLC, RIEMANN_HLL, RIEMANN_LF, RIEMANN_AUSM = 0, 1, 2, 3, 4
 FORCING_NONE, FORCING_POISEUILLE = 0, 1
 
@@ -54,15 +54,28 @@ def viscosity(T, ph):
     return T ** 1.5 / ph.Re * (1.0 + s) / (T + s)
 
 
-def viscous_flux(U, dU, ph):
+def artificial_viscosity(U, factor, ph):
+    """mu_av = mu_0 rho (h/P) (c + |u|) S (Sec. 3.1.2) at each point, with the
+    element factor mu_0 S h / P given (factor, broadcast over the points)."""
+    rho, vel, p, _ = primitives(U, ph)
+    c = np.sqrt(ph.gamma * p / rho)
+    return factor * rho * (c + np.sqrt(np.sum(vel * vel, axis=-1)))
+
+
+def viscous_flux(U, dU, ph, mu_av=None):
     """Diffusion flux G_i = (0, tau_i1..tau_id, u_j tau_ij - q_i) with the
     Stokes stress tau_ij = mu (du_i/dx_j + du_j/dx_i) - 2/3 mu div(u) delta_ij and
     Fourier heat flux q_i = -mu / (Ma^2 Pr (gamma-1)) dT/dx_i.  dU[..., j, v]
-    is the gradient of the conservative variables; G is linear in dU."""
+    is the gradient of the conservative variables; G is linear in dU.  mu_av
+    (optional, per point): artificial viscosity added to mu; its conductivity
+    mu_av C_p / Pr (Sec. 3.1.2) has the physical factor 1/(Ma^2 Pr (gamma-1))
+    because C_p = 1/((gamma-1) Ma^2) in these units."""
     d = U.shape[-1] - 2
     g, Ma = ph.gamma, ph.Ma
     rho, vel, p, T = primitives(U, ph)
     mu = viscosity(T, ph)
+    if mu_av is not None:
+        mu = mu + mu_av
     drho = dU[..., 0]                                  # [..., j]
     dvel = (dU[..., 1:1 + d] - vel[..., None, :] * drho[..., :, None]) / rho[..., None, None]
     # dvel[..., j, k] = d u_k / d x_j
@@ -280,6 +293,19 @@ def exact_state(ph, x, t):
         vel[..., 0] = -dpdx / (2 * mu) * (y * (L - y) + theta * y * y * (L - y) ** 2)
         p = 1.0 / (g * Ma ** 2) + dpdx * x[..., 0]
         T = g * Ma ** 2 * p / rho
+    elif ph.fid == FIELD_SHOCK:
+        # oblique shock of angle beta (to the x axis) reaching the line y = 0
+        # at x = x_sh: the uniform stream (1, 0) at T = 1 below the shock
+        # line y = (x_sh - x) tan(beta), the Rankine-Hugoniot state above it
+        beta, xsh = np.radians(ph.fpar[0]), ph.fpar[1]
+        r2, v2, p2 = oblique_shock_state(beta, ph)
+        post = x[..., 1] > (xsh - x[..., 0]) * np.tan(beta)
+        rho = np.where(post, r2, 1.0)
+        vel = np.zeros(shp + (d,))
+        vel[..., 0] = np.where(post, v2[0], 1.0)
+        vel[..., 1] = np.where(post, v2[1], 0.0)
+        p = np.where(post, p2, 1.0 / (g * Ma ** 2))
+        T = g * Ma ** 2 * p / rho
     elif ph.fid == FIELD_TGV:
         X, Y, Z = x[..., 0], x[..., 1], x[..., 2]
         vel = np.stack([np.sin(X) * np.cos(Y) * np.cos(Z), -np.cos(X) * np.sin(Y) * np.cos(Z),
@@ -292,6 +318,23 @@ def exact_state(ph, x, t):
         raise ValueError(ph.fid)
     p = rho * T / (g * Ma ** 2)
     return conservative(rho, vel, p, ph)
+
+
+def oblique_shock_state(beta, ph):
+    """State behind an oblique shock of angle beta met by the stream (1, 0),
+    rho = 1, p = 1/(gamma Ma^2) (Rankine-Hugoniot relations for the normal
+    Mach number Ma sin(beta); the tangential velocity is continuous; the shock
+    normal n = (sin beta, cos beta) points from the upstream side).  Returns
+    (rho2, velocity2, p2)."""
+    g, Ma = ph.gamma, ph.Ma
+    n = np.array([np.sin(beta), np.cos(beta)])
+    t = np.array([np.cos(beta), -np.sin(beta)])
+    u1 = np.array([1.0, 0.0])
+    m1n2 = (Ma * np.sin(beta)) ** 2
+    r2 = (g + 1) * m1n2 / ((g - 1) * m1n2 + 2)
+    p2 = (1 + 2 * g / (g + 1) * (m1n2 - 1)) / (g * Ma ** 2)
+    v2 = (u1 @ n) / r2 * n + (u1 @ t) * t
+    return r2, v2, p2
 
 
 def forcing(ph, x, t):

@@ -111,3 +111,43 @@ def test_learned_guess_cuts_newton_iterations(dgl):
         assert used > 0, mode
         assert sum(itl[-last:]) < sum(itp[-last:]), (mode, itp, itl)
         assert np.linalg.norm(ul - up) / np.linalg.norm(up) < 1e-3, mode
+
+
+def test_learned_correction_against_extrapolation_alone(dgl, parity_record):
+    """What the trained network adds over the method without it: the same
+    SDIRK2 steps (vortex 8x8 P=2, dt = 0.02) from the previous stage increment
+    alone and from that increment plus the MLP correction (online Adam, the
+    correction used once its loss is below 0.2 of the zero correction's), at
+    the same tolerance alpha ||N(S_m)||.  The counts of both are recorded; the
+    learned form is never worse over the last 8 steps (its guess is only taken
+    when it lowers ||N||) and reaches the same solution."""
+    c = w.vortex_case(n=8, P=2)
+    dg = DG(c.mesh, c.P, c.Q, c.phys)
+    u0 = dev(dg.project_exact())
+    m = dgl.Mesh.from_case(c)
+    E, nv, nm = m.shape
+    nb = nv * nm
+    dt, nsteps, last = 0.02, 20, 8
+    params = (w.mlp_params(3 * nb, 64, nb, seed=11, zero_last=True)
+              + w.mlp_params(3 * nb, 64, nb, seed=12, zero_last=True))
+    runs = {}
+    for mode in ("extrapolated", "learned"):
+        u = u0.clone()
+        pc = dgl.Precond(m)
+        guess = (dgl.Guess(m, None, stages=2) if mode == "extrapolated"
+                 else dgl.Guess(m, params, stages=2, hidden=64, lr=1e-3))
+        newton, gm = [], []
+        for k in range(nsteps):
+            st = m.sdirk_step(u, k * dt, dt, precond=pc, rebuild=(k % 10 == 0), restart=20, J=7,
+                              guess=guess, guess_train_iters=10)
+            assert st["converged"]
+            newton.append(st["newton_iters"])
+            gm.append(st["gmres_iters"])
+        runs[mode] = (u.cpu().numpy(), newton, gm)
+    ue, ne, ge = runs["extrapolated"]
+    ul, nl, gl = runs["learned"]
+    parity_record("learned_vs_extrapolated", "vortex8_P2_dt0.02_last8",
+                  "Newton(learned) / Newton(extrapolated)", sum(nl[-last:]) / sum(ne[-last:]), 1.0,
+                  newton_extrap=ne, newton_learned=nl, gmres_extrap=ge, gmres_learned=gl)
+    assert sum(nl[-last:]) <= sum(ne[-last:]), (ne, nl)
+    assert np.linalg.norm(ul - ue) / np.linalg.norm(ue) < 1e-3

@@ -21,6 +21,7 @@ FIELD_VORTEX = 1
 FIELD_POISEUILLE = 2
 FIELD_TGV = 3
 FIELD_CYLINDER = 4   # uniform stream (1, 0, 0) at T = 1, rho = 1
+FIELD_SHOCK = 5      # oblique shock: stream (1, 0) below the shock line, post-shock state above
 # FIELD_UNIFORM is the uniform state fpar = (rho, u, v, w, T), or the stream
 # (1, 1, 0, 0, 1) when fpar is empty
 
@@ -50,6 +51,9 @@ class Physics:
     # Poiseuille: theta, L, dpdx; uniform: rho, u, v, w, T)
     fpar: tuple = ()
     bc: list = dc_field(default_factory=list)   # bc[id] = type
+    av: int = 0                # shock capturing: artificial viscosity from the modal sensor
+    av_mu0: float = 0.25       # mu_0 of Sec. 3.1.2
+    av_kappa: float = 1.0      # half-width of the sensor's ramp (decades)
 
     @property
     def mu(self):
@@ -189,4 +193,30 @@ def small_cylinder_case(n_r=3, n_theta=8, n_z=2, P=2, Q=None, Re=3900.0, Ma=0.2,
     m = ogrid_mesh(n_r, n_theta, n_z, 0.5, r_out, 1.08, np.pi)
     ph = Physics(Ma=Ma, Re=Re, fid=FIELD_CYLINDER, bc=list(bc), fpar=(0.5, wall_layer))
     return Case(f"cylinder{n_r}x{n_theta}x{n_z}_P{P}", m, P, Q, ph)
+
+
+def wall_spacing(n, ratio, length=1.0):
+    """Grid lines on [0, length] with n cells growing geometrically by `ratio`
+    away from 0 (one wall)."""
+    h = ratio ** np.arange(n)
+    return np.concatenate([[0.0], np.cumsum(h)]) / h.sum() * length
+
+
+def swbli_case(nx=119, ny=39, P=3, Q=None, Ma=2.15, Re=1.0e5, beta_deg=30.8, x0=0.3, x1=2.0,
+               height=1.0, ratio=1.1, av=1, riemann=RIEMANN_ROE):
+    """Shock-wave / boundary-layer interaction of the kind of Sec. 6.5: an
+    oblique shock of angle beta_deg (to the stream) generated above the plate
+    reaches the adiabatic no-slip wall y = 0 at x = 1 (the unit length, on
+    which Re is based); the domain [x0, x1] x [0, height] (nx x ny quads,
+    spacing growing by `ratio` away from the wall), the uniform stream at Ma
+    below the shock line and the Rankine-Hugoniot state above it imposed on
+    the inflow (x = x0) and top sides, a characteristic far-field outflow,
+    the artificial-viscosity shock capturing of Sec. 3.1.2 (av = 1)."""
+    Q = P + 2 if Q is None else Q
+    xl = np.linspace(x0, x1, nx + 1)
+    yl = wall_spacing(ny, ratio, height)
+    m = box_mesh([xl, yl], (False, False), side_bc=[0, 1, 2, 0])
+    ph = Physics(Ma=Ma, Re=Re, fid=FIELD_SHOCK, fpar=(beta_deg, 1.0),
+                 bc=[BC_DIRICHLET, BC_FARFIELD, BC_ADIA_WALL], av=av, riemann=riemann)
+    return Case(f"swbli{nx}x{ny}_P{P}", m, P, Q, ph)
 
