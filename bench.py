@@ -42,6 +42,11 @@ CYLINDER = {"n_r": 64, "n_theta": 96, "n_z": 12, "P": 3, "Q": 6, "Re": 3900.0, "
             "cfl_c": 1.7, "seed": 5, "wall_layer": 0.1, "ramp": (0.25, 0.5)}
 # the same flow at P = 4 on 24^3 hexes (over-integration Q = 8)
 TGV24 = {"n": 24, "P": 4, "Q": 8, "Re": 1600.0, "Ma": 0.1, "cfl": 0.10, "dt_factor": 10.0}
+# supersonic shock-wave / boundary-layer interaction of Sec. 6.5 (119 x 39 quads,
+# P = 3, Ma 2.15, Re 1e5 on the shock's foot distance, shock at 30.8 degrees),
+# artificial-viscosity shock capturing (Sec. 3.1.2), SDIRK2; time step from
+# Eq. CFL on the first cell at the wall with c + |u| = 1/Ma + 1
+SWBLI = {"nx": 119, "ny": 39, "P": 3, "Q": 5, "Ma": 2.15, "Re": 1.0e5, "beta": 30.8, "cfl": 100.0}
 SAMPLE_N = 3          # CPU sample: the same case on 3^3 elements (same P, Q, CFL)
 FREEZE = 10
 # DRAM bytes (read + write) per element and launch from one ncu capture of the
@@ -88,6 +93,16 @@ def cylinder_dt(wl, frac=1.0):
     h = 1.08 ** (wl["n_r"] - 1 - __import__("numpy").arange(wl["n_r"]))
     dr = (20.0 - 0.5) * 1.0 / h.sum()            # first cell (geometric growth 1.08)
     return frac * wl["cfl_c"] * dr / wl["P"]
+
+
+def swbli_dt(case, wl):
+    """dt of Eq. CFL: CFL d_RK dx / (c_lambda (c + |u|) P^2), c_lambda = 0.2,
+    d_RK = 2, c + |u| = 1/Ma + 1, dx = the smallest element edge (the first
+    cell at the wall)."""
+    import numpy as np
+    ys = np.unique(case.mesh.nodes[..., 1])
+    dx = float(np.diff(ys).min())
+    return wl["cfl"] * 2.0 * dx / (0.2 * (1.0 / wl["Ma"] + 1.0) * wl["P"] ** 2)
 
 
 def cylinder_initial(m, wl):
@@ -178,11 +193,12 @@ def residual_flops_per_elem(P, Q, d=3):
     return {"dg_vol": vol, "dg_face": face, "dg_lift": lift}
 
 
-def kernel_work(name, launches, E, nb, prec_bytes, P, Q):
-    """(bound, algorithmic units per launch, unit) of a kernel family."""
+def kernel_work(name, launches, E, nb, prec_bytes, P, Q, d=3):
+    """(bound, algorithmic units per launch, unit) of a kernel family.  The
+    residual kernels' flop counts are those of the 3-D kernels."""
     f = residual_flops_per_elem(P, Q)
     if name in f:
-        return "alu", f[name] * E, "flop"
+        return ("alu", f[name] * E, "flop") if d == 3 else (None, None, None)
     if name == "brj_diag":
         return "hbm", E * (nb * nb * prec_bytes + 2 * nb * 8), "byte"
     if name == "brj_sweep":
@@ -190,8 +206,9 @@ def kernel_work(name, launches, E, nb, prec_bytes, P, Q):
         # point), q, the own previous iterate and the output, the neighbours'
         # face-slice coefficients (3-D workloads)
         sj = 8 if prec_bytes == 8 else 4
-        per = (nb * nb * prec_bytes + 6 * 25 * Q * Q * sj + 3 * nb * 8
-               + 6 * 5 * (P + 1) ** 2 * 8)
+        nv = d + 2
+        per = (nb * nb * prec_bytes + 2 * d * nv * nv * Q ** (d - 1) * sj + 3 * nb * 8
+               + 2 * d * nv * (P + 1) ** (d - 1) * 8)
         return "hbm", E * per, "byte"
     if name in ("multi_dot", "multi_axpy", "dot", "vector"):
         return "hbm", None, "byte"
@@ -271,11 +288,17 @@ def run_ours(args, rank, world):
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
     cyl = args.workload == "cylinder"
-    wl = CYLINDER if cyl else (TGV24 if args.workload == "tgv24" else WORKLOAD)
+    sw = args.workload == "swbli"
+    wl = {"cylinder": CYLINDER, "tgv24": TGV24, "swbli": SWBLI}.get(args.workload, WORKLOAD)
     if cyl:
         case = w.cylinder_case(wl["n_r"], wl["n_theta"], wl["n_z"], P=wl["P"], Q=wl["Q"],
                                Re=wl["Re"], Ma=wl["Ma"], wall_layer=wl["wall_layer"])
         dt = cylinder_dt(wl)
+    elif sw:
+        wl["cfl"] = args.cfl if args.cfl is not None else wl["cfl"]
+        case = w.swbli_case(nx=wl["nx"], ny=wl["ny"], P=wl["P"], Q=wl["Q"], Ma=wl["Ma"],
+                            Re=wl["Re"], beta_deg=wl["beta"])
+        dt = swbli_dt(case, wl)
     else:
         case = w.tgv_case(n=wl["n"], P=wl["P"], Q=wl["Q"], Re=wl["Re"], Ma=wl["Ma"])
         dt = tgv_dt(wl["n"], wl["P"], wl["Ma"], wl["cfl"], wl["dt_factor"])
@@ -363,7 +386,8 @@ def run_ours(args, rank, world):
     dom = max(prof, key=lambda k: prof[k][1])
     pk, how = peaks()
     prec_bytes = {"fp64": 8, "fp32": 4, "bf16": 2}[args.precision]
-    bound, work, unit = kernel_work(dom, prof[dom][0], E, nb, prec_bytes, wl["P"], wl["Q"])
+    dim = m.info["dim"]
+    bound, work, unit = kernel_work(dom, prof[dom][0], E, nb, prec_bytes, wl["P"], wl["Q"], dim)
     avg_ms = prof[dom][1] / prof[dom][0]
     roof = {"kernel": dom, "launches": prof[dom][0], "avg_ms": avg_ms,
             "share": prof[dom][1] / total_k, "traffic": None}
@@ -403,8 +427,11 @@ def run_ours(args, rank, world):
                 "flops_per_launch": rflops, "avg_ms": res_ms,
                 "peak_source": "measured in this run: dg_peak_fp64 (FP64 FMA chains at full "
                                "occupancy, CUDA events)"}
+    if dim != 3:
+        res_roof = {"bound": "alu", "achieved": None, "peak": fp64_peak, "unit": "TFLOP/s",
+                    "avg_ms": res_ms, "note": "flop counts are those of the 3-D kernels"}
     for kname in ("dg_vol", "dg_face", "dg_lift"):
-        if kname in prof and not cyl:
+        if kname in prof and not cyl and dim == 3:
             kf = residual_flops_per_elem(wl["P"], wl["Q"])[kname] * E
             kms = prof[kname][1] / prof[kname][0]
             res_roof[kname] = {"avg_ms": round(kms, 4),
@@ -430,13 +457,21 @@ def run_ours(args, rank, world):
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
 
     variants = None
-    if args.variants and not cyl:
+    if args.variants and not cyl and not sw:
         u0 = m.project(0.0)
         variants = [time_variant(m, u0, dt, p_, g_, f_, args.steps, args.warmup)
                     for p_, g_, f_ in VARIANTS]
     newton = [s["newton_iters"] for s in timed_stats]
     gm = [s["gmres_iters"] for s in timed_stats]
-    if cyl:
+    if sw:
+        metric = ("SDIRK2 step throughput at fixed Newton tolerance (DOF-steps/s); SWBLI "
+                  f"{wl['nx']}x{wl['ny']} quads P={wl['P']}, Ma {wl['Ma']:g}, artificial viscosity, "
+                  f"CFL {wl['cfl']:g}")
+        wname = (f"swbli{wl['nx']}x{wl['ny']}_P{wl['P']}_Q{wl['Q']}_Ma{wl['Ma']:g}_av_sdirk2"
+                 f"_cfl{wl['cfl']:g}")
+        data = ("synthetic (the projected oblique-shock field: uniform stream below the shock "
+                "line, Rankine-Hugoniot state above)")
+    elif cyl:
         metric = ("SDIRK3 step throughput at fixed Newton tolerance (DOF-steps/s); curved O-grid "
                   f"{wl['n_r']}x{wl['n_theta']}x{wl['n_z']} quadratic hexes P=3, CFL_c {wl['cfl_c']:g}")
         wname = (f"cylinder_ogrid{wl['n_r']}x{wl['n_theta']}x{wl['n_z']}_P{wl['P']}_Q{wl['Q']}"
@@ -588,10 +623,13 @@ def main():
     ap.add_argument("--fused", action=argparse.BooleanOptionalAction, default=True,
                     help="BRJ sweeps after the first as one off-diagonal + block kernel each "
                          "(default; --no-fused: separate off-diagonal and block launches)")
-    ap.add_argument("--workload", default="tgv", choices=["tgv", "tgv24", "cylinder"],
+    ap.add_argument("--workload", default="tgv", choices=["tgv", "tgv24", "cylinder", "swbli"],
                     help="tgv: the Taylor-Green benchmark (default, 16^3 P=3); tgv24: 24^3 P=4 "
                          "Q=8; cylinder: the curved O-grid workload (SDIRK3, BF16 blocks, learned "
-                         "guess unless overridden)")
+                         "guess unless overridden); swbli: the supersonic shock / boundary-layer "
+                         "workload with artificial viscosity (SDIRK2, 119x39 P=3)")
+    ap.add_argument("--cfl", type=float, default=None,
+                    help="swbli only: CFL of Eq. CFL (default 100)")
     ap.add_argument("--elems", type=int, default=WORKLOAD["n"],
                     help="elements per direction (16 = the benchmark; smaller only for profiler captures)")
     args = ap.parse_args()

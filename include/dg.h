@@ -82,7 +82,7 @@ enum { DG_RIEMANN_ROE = 0, DG_RIEMANN_HLLC = 1, DG_RIEMANN_HLL = 2, DG_RIEMANN_L
        DG_RIEMANN_AUSM = 4 };
 enum { DG_BC_DIRICHLET = 1, DG_BC_ISO_WALL = 2, DG_BC_ADIA_WALL = 3, DG_BC_FARFIELD = 4 };
 enum { DG_FIELD_UNIFORM = 0, DG_FIELD_VORTEX = 1, DG_FIELD_POISEUILLE = 2, DG_FIELD_TGV = 3,
-       DG_FIELD_CYLINDER = 4 };
+       DG_FIELD_CYLINDER = 4, DG_FIELD_SHOCK = 5 };
 enum { DG_FORCING_NONE = 0, DG_FORCING_POISEUILLE = 1 };
 
 /* Physical model, Sec. 2.1: p = rho T / (gamma Ma^2), constant mu = 1/Re
@@ -93,7 +93,10 @@ enum { DG_FORCING_NONE = 0, DG_FORCING_POISEUILLE = 1 };
  * xc, yc, scale; Poiseuille: theta, L, dp/dx; uniform: rho, u, v, w, T, or
  * the stream (1, 1, 0, 0, 1) when fpar[0] = 0; cylinder: that stream,
  * brought to rest at the wall radius fpar[0] by the factor
- * 1 - exp(-(r - fpar[0]) / fpar[1]) when fpar[1] > 0).
+ * 1 - exp(-(r - fpar[0]) / fpar[1]) when fpar[1] > 0; shock: an oblique
+ * shock at fpar[0] degrees to the x axis meeting y = 0 at x = fpar[1], the
+ * stream (1, 0) at T = 1 below the line and the Rankine-Hugoniot state
+ * behind it above).
  * bc[i] is the type of boundary i:
  *   DG_BC_DIRICHLET  exterior and viscous state = the analytic field
  *   DG_BC_ISO_WALL   no-slip wall at the analytic wall temperature
@@ -115,6 +118,21 @@ typedef struct {
   double fpar[8];
   int n_bc;
   int bc[8];
+  /* Shock capturing by artificial viscosity (Sec. 3.1.2; av = 1, viscous
+   * only).  Per element, the modal sensor of the density
+   *   s_e = log10(|rho - Pi rho|^2 / |rho|^2),
+   * Pi the L2 projection onto degree <= P-1 in each reference direction and
+   * both norms on the reference element, gives S_e = 0 below s0 - av_kappa,
+   * 1 above s0 + av_kappa and (1 + sin(pi (s_e - s0) / (2 av_kappa))) / 2
+   * between, s0 = log10(1/P^4).  The viscosity mu + mu_av and conductivity
+   * (mu + mu_av) C_p / Pr use mu_av = av_mu0 S_e (h_e / P) rho (c + |u|) at
+   * each volume point, h_e = |element|^(1/dim); on a face the mean of the
+   * two sides' values from their traces (the interior side's on a boundary).
+   * The residual recomputes S_e from its argument on every call; the BRJ
+   * preconditioner holds mu_av at its linearisation state.  av = 0 leaves
+   * the model unchanged. */
+  int av;
+  double av_mu0, av_kappa;
 } dg_physics;
 
 typedef struct {
@@ -154,6 +172,13 @@ dg_status dg_project(dg_mesh_t m, double t, double* u, void* stream);
  * (Sec. 3.1, Eq. matrix-form-equations; Sec. 3.2, Eq. ode).  u and r must
  * not alias. */
 dg_status dg_residual(dg_mesh_t m, const double* u, double t, double* r, void* stream);
+
+/* Shock capturing (Sec. 3.1.2): fac[e] = av_mu0 S_e h_e / P for every
+ * element at the state u (device, [n_elem]), the factor that multiplies
+ * rho (c + |u|) in the artificial viscosity; S_e = fac[e] P / (av_mu0 h_e) is
+ * the modal sensor.  The same kernel runs at the start of every residual
+ * evaluation.  DG_ERR_UNSUPPORTED when the mesh was created with av = 0. */
+dg_status dg_av_factor(dg_mesh_t m, const double* u, double* fac, void* stream);
 
 /* Jacobian-free product (Sec. 4.2.2, Eq. Jacobian-free-matrix, eps-JF):
  *   out = alpha*v + beta*(R(u + eps v, t) - r_u)/eps,

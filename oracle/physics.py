@@ -296,15 +296,28 @@ def exact_state(ph, x, t):
     elif ph.fid == FIELD_SHOCK:
         # oblique shock of angle beta (to the x axis) reaching the line y = 0
         # at x = x_sh: the uniform stream (1, 0) at T = 1 below the shock
-        # line y = (x_sh - x) tan(beta), the Rankine-Hugoniot state above it
+        # line y = (x_sh - x) tan(beta), the Rankine-Hugoniot state above it.
+        # fpar[2] = w > 0: the primitive variables pass from one state to the
+        # other by the fraction (1 + tanh(s / w)) / 2 of the signed distance
+        # s = y cos(beta) - (x_sh - x) sin(beta) to the line; fpar[3] = l > 0:
+        # the velocity is brought to rest at the wall y = 0 by 1 - exp(-y / l)
         beta, xsh = np.radians(ph.fpar[0]), ph.fpar[1]
+        width = ph.fpar[2] if len(ph.fpar) > 2 else 0.0
+        layer = ph.fpar[3] if len(ph.fpar) > 3 else 0.0
         r2, v2, p2 = oblique_shock_state(beta, ph)
-        post = x[..., 1] > (xsh - x[..., 0]) * np.tan(beta)
-        rho = np.where(post, r2, 1.0)
+        if width > 0.0:
+            dist = x[..., 1] * np.cos(beta) - (xsh - x[..., 0]) * np.sin(beta)
+            post = 0.5 * (1.0 + np.tanh(dist / width))
+        else:
+            post = (x[..., 1] > (xsh - x[..., 0]) * np.tan(beta)).astype(float)
+        p1 = 1.0 / (g * Ma ** 2)
+        rho = 1.0 + post * (r2 - 1.0)
         vel = np.zeros(shp + (d,))
-        vel[..., 0] = np.where(post, v2[0], 1.0)
-        vel[..., 1] = np.where(post, v2[1], 0.0)
-        p = np.where(post, p2, 1.0 / (g * Ma ** 2))
+        vel[..., 0] = 1.0 + post * (v2[0] - 1.0)
+        vel[..., 1] = post * v2[1]
+        if layer > 0.0:
+            vel *= (1.0 - np.exp(-x[..., 1] / layer))[..., None]
+        p = p1 + post * (p2 - p1)
         T = g * Ma ** 2 * p / rho
     elif ph.fid == FIELD_TGV:
         X, Y, Z = x[..., 0], x[..., 1], x[..., 2]

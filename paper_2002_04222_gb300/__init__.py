@@ -89,6 +89,14 @@ class Mesh:
                                                     _stream(stream)))
         return out
 
+    def av_factor(self, u, out=None, stream=None):
+        """Per-element artificial-viscosity factor mu_0 S_e h_e / P at u
+        (shock capturing, Sec. 3.1.2): a float64 tensor of n_elem values."""
+        out = torch.empty(self.shape[0], dtype=torch.float64, device=u.device) if out is None else out
+        _check("dg_av_factor", self._lib.dg_av_factor(self.handle, _ptr(u), _ptr(out),
+                                                      _stream(stream)))
+        return out
+
     def jvp(self, u, r_u, v, t=0.0, alpha=0.0, beta=1.0, out=None, stream=None):
         out = self.empty() if out is None else out
         _check("dg_jvp", self._lib.dg_jvp(self.handle, _ptr(u), _ptr(r_u), t, _ptr(v), alpha, beta,

@@ -39,7 +39,8 @@ class Physics(ctypes.Structure):
                 ("Re", ctypes.c_double), ("T_inf_K", ctypes.c_double), ("beta_s", ctypes.c_double),
                 ("viscous", ctypes.c_int), ("mu_law", ctypes.c_int), ("riemann", ctypes.c_int),
                 ("forcing", ctypes.c_int), ("field", ctypes.c_int),
-                ("fpar", ctypes.c_double * 8), ("n_bc", ctypes.c_int), ("bc", ctypes.c_int * 8)]
+                ("fpar", ctypes.c_double * 8), ("n_bc", ctypes.c_int), ("bc", ctypes.c_int * 8),
+                ("av", ctypes.c_int), ("av_mu0", ctypes.c_double), ("av_kappa", ctypes.c_double)]
 
 
 class MeshInfo(ctypes.Structure):
@@ -108,6 +109,7 @@ SIGNATURES = {
     "dg_mesh_info": [VP, ctypes.POINTER(MeshInfo)],
     "dg_project": [VP, D, VP, VP],
     "dg_residual": [VP, VP, D, VP, VP],
+    "dg_av_factor": [VP, VP, VP, VP],
     "dg_jvp": [VP, VP, VP, D, VP, D, D, VP, VP],
     "dg_precond_build": [VP, VP, D, D, ctypes.POINTER(PrecCfg), ctypes.POINTER(VP), VP],
     "dg_precond_apply": [VP, VP, VP, VP],
@@ -170,4 +172,7 @@ def physics(ph):
     p.n_bc = len(ph.bc)
     for i, v in enumerate(ph.bc):
         p.bc[i] = v
+    p.av = int(getattr(ph, "av", 0))
+    p.av_mu0 = float(getattr(ph, "av_mu0", 0.0))
+    p.av_kappa = float(getattr(ph, "av_kappa", 1.0))
     return p

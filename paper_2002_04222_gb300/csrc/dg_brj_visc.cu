@@ -30,7 +30,7 @@ namespace dg {
 template <int D>
 __device__ inline void symmetric_flux(const double* QL, const double* QRin, int bctype,
                                       const double* x, double t, const double* n, const Phys& ph,
-                                      double S[D][D + 2], double* Qa_out) {
+                                      double S[D][D + 2], double* Qa_out, double mu_add) {
   constexpr int NV = D + 2;
   double QR[NV], Qa[NV], jump[NV];
   bool adiabatic = false;
@@ -50,7 +50,7 @@ __device__ inline void symmetric_flux(const double* QL, const double* QRin, int 
   for (int j = 0; j < D; ++j)
 #pragma unroll
     for (int v = 0; v < NV; ++v) gS[j][v] = n[j] * jump[v];
-  viscous_flux<D>(Qa, gS, ph, S);
+  viscous_flux<D>(Qa, gS, ph, S, mu_add);
   if (adiabatic)
 #pragma unroll
     for (int j = 0; j < D; ++j) S[j][NV - 1] = 0.0;
@@ -120,7 +120,9 @@ __global__ void __launch_bounds__(128) brj_visc_trace_kernel(
   const double cg = interior ? 0.5 : 1.0;
   const double cs = cg * ph.beta_s;
   double S0[DIM][NV], S1[DIM][NV], Qa[NV];
-  symmetric_flux<DIM>(QL, QR, bctype, x, t, n, ph, S0, Qa);
+  // artificial viscosity held at the linearisation state's traces
+  const double mua = av_face<DIM>(ph, eL, eR, QL, QR);
+  symmetric_flux<DIM>(QL, QR, bctype, x, t, n, ph, S0, Qa, mua);
   const bool adiabatic = bctype == DG_BC_ADIA_WALL;
   TJ* kl = Kd + (((long long)eL * 2 * DIM + fL) * NF + p) * NK;
   TJ* kr = interior ? Kd + (((long long)eR * 2 * DIM + fR) * NF + p) * NK : nullptr;
@@ -132,7 +134,7 @@ __global__ void __launch_bounds__(128) brj_visc_trace_kernel(
       for (int a = 0; a < DIM; ++a)
 #pragma unroll
         for (int v = 0; v < NV; ++v) gu[a][v] = (a == j && v == l) ? 1.0 : 0.0;
-      viscous_flux<DIM>(Qa, gu, ph, G);
+      viscous_flux<DIM>(Qa, gu, ph, G, mua);
 #pragma unroll
       for (int k = 0; k < NV; ++k) {
         const double dh = (adiabatic && k == NV - 1) ? 0.0 : -cg * sgn * G[r][k];
@@ -150,7 +152,7 @@ __global__ void __launch_bounds__(128) brj_visc_trace_kernel(
     double Qp[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) Qp[v] = QL[v] + (v == l ? h : 0.0);
-    symmetric_flux<DIM>(Qp, QR, bctype, x, t, n, ph, S1, nullptr);
+    symmetric_flux<DIM>(Qp, QR, bctype, x, t, n, ph, S1, nullptr, mua);
 #pragma unroll
     for (int i = 0; i < DIM; ++i)
 #pragma unroll
@@ -162,7 +164,7 @@ __global__ void __launch_bounds__(128) brj_visc_trace_kernel(
     if (interior) {
 #pragma unroll
       for (int v = 0; v < NV; ++v) Qp[v] = QR[v] + (v == l ? h : 0.0);
-      symmetric_flux<DIM>(QL, Qp, bctype, x, t, n, ph, S1, nullptr);
+      symmetric_flux<DIM>(QL, Qp, bctype, x, t, n, ph, S1, nullptr, mua);
 #pragma unroll
       for (int i = 0; i < DIM; ++i)
 #pragma unroll

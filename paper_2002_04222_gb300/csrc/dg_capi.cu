@@ -18,7 +18,7 @@ long long g_launches = 0;
 static const char* kernel_names[K_COUNT] = {
     "dg_vol", "dg_face", "dg_lift", "dg_project", "dot", "multi_dot", "multi_axpy", "vector",
     "brj_weights", "brj_tracejac", "brj_block", "brj_invert", "brj_diag",
-    "brj_offdiag", "mlp_gemm", "brj_sweep"};
+    "brj_offdiag", "mlp_gemm", "brj_sweep", "dg_sensor"};
 struct ProfRec {
   int id;
   cudaEvent_t a, b;
@@ -217,6 +217,23 @@ static void build_tables(int P, int Q, Tables& t) {
   for (int k = 0; k < n; ++k) t.dpp[k] = dphi[k];
 }
 
+// Modal sensor table: the Legendre coefficients of the modified basis,
+// T[a][k] = (2a+1)/2 sum_q w_q L_a(x_q) psi_k(x_q) (the Gauss rule is exact,
+// the product has degree <= 2P <= 2Q-1), and |L_a|^2 = 2/(2a+1).
+static void build_sensor_table(int P, const Tables& t, SensorTab& st) {
+  std::memset(&st, 0, sizeof(st));
+  const int n = P + 1;
+  for (int q = 0; q < t.q; ++q) {
+    double L[NMAX];
+    L[0] = 1.0;
+    if (n > 1) L[1] = t.x[q];
+    for (int a = 2; a < n; ++a) L[a] = ((2 * a - 1) * t.x[q] * L[a - 1] - (a - 1) * L[a - 2]) / a;
+    for (int a = 0; a < n; ++a)
+      for (int k = 0; k < n; ++k) st.T[a * n + k] += 0.5 * (2 * a + 1) * t.w[q] * L[a] * t.B[q * n + k];
+  }
+  for (int a = 0; a < n; ++a) st.nrm[a] = 2.0 / (2 * a + 1);
+}
+
 void drop_arnoldi_graphs(dg_mesh_s* m) {
   for (auto& g : m->agraphs) cudaGraphExecDestroy(g.exec);
   m->agraphs.clear();
@@ -291,6 +308,7 @@ static void free_mesh(dg_mesh_s* m) {
   cudaFree(m->fbeta);
   cudaFree(m->minv);
   cudaFree(m->force);
+  cudaFree(m->avf);
   cudaFree(m->scratch);
   cudaFree(m->red);
   cudaFree(m->w1);
@@ -316,6 +334,9 @@ dg_status dg_mesh_create(const dg_mesh_desc* md, const dg_physics* ph, void* str
   if (!supported(d, md->P, md->Q)) return DG_ERR_UNSUPPORTED;
   if (ph->n_bc < 0 || ph->n_bc > 8) return DG_ERR_ARG;
   if (ph->riemann < DG_RIEMANN_ROE || ph->riemann > DG_RIEMANN_AUSM) return DG_ERR_ARG;
+  if (ph->av != 0 && ph->av != 1) return DG_ERR_ARG;
+  if (ph->av && (!ph->viscous || !(ph->av_mu0 >= 0.0) || !(ph->av_kappa > 0.0)))
+    return DG_ERR_ARG;  // artificial viscosity enters through the diffusion flux
   cudaStream_t s = (cudaStream_t)stream;
   const int E = md->n_elem, F = md->n_faces;
   // axis-aligned affine boxes take the diagonal-metric kernels; any other
@@ -423,6 +444,13 @@ dg_status dg_mesh_create(const dg_mesh_desc* md, const dg_physics* ph, void* str
   alloc((void**)&m->w1, sizeof(double) * nd);
   alloc((void**)&m->w2, sizeof(double) * nd);
   if (ph->forcing) alloc((void**)&m->force, sizeof(double) * nd);
+  if (ph->av) {
+    alloc((void**)&m->avf, sizeof(double) * E);
+    p.avf = m->avf;
+    p.av_mu0 = ph->av_mu0;
+    p.av_kappa = ph->av_kappa;
+    build_sensor_table(md->P, m->tab, m->stab);
+  }
   if (err != cudaSuccess) {
     free_mesh(m);
     return cuda_status(err);
@@ -498,6 +526,12 @@ dg_status dg_set_tune(dg_mesh_t m, const dg_tune_result* t) {
 dg_status dg_project(dg_mesh_t m, double t, double* u, void* stream) {
   if (!m || !u) return DG_ERR_ARG;
   return launch_project(m, 0, t, u, (cudaStream_t)stream);
+}
+
+dg_status dg_av_factor(dg_mesh_t m, const double* u, double* fac, void* stream) {
+  if (!m || !u || !fac) return DG_ERR_ARG;
+  if (!m->phys.avf) return DG_ERR_UNSUPPORTED;
+  return launch_sensor(m, u, fac, (cudaStream_t)stream);
 }
 
 dg_status dg_residual(dg_mesh_t m, const double* u, double t, double* r, void* stream) {

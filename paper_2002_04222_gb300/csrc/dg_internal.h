@@ -30,6 +30,18 @@ struct Phys {
   int viscous, mu_law, riemann, forcing, field;
   double fpar[8];
   int bc[8];
+  // shock capturing (Sec. 3.1.2): mu_0 and the ramp half-width of the modal
+  // sensor; avf = the per-element factor mu_0 S_e h_e / P of the state last
+  // passed to the residual (device, [E]; nullptr without shock capturing)
+  double av_mu0, av_kappa;
+  const double* avf;
+};
+
+// Modified-basis-to-Legendre transform of one direction for the modal sensor:
+// T[a*n + k] = Legendre coefficient a of psi_k, nrm[a] = |L_a|^2 = 2/(2a+1).
+struct SensorTab {
+  double T[NMAX * NMAX];
+  double nrm[NMAX];
 };
 
 // Element geometry of an axis-aligned affine element: origin and edge lengths.
@@ -83,6 +95,8 @@ struct dg_mesh_s {
   double* tbuf = nullptr;       // [E][2dim][(1+dim)nv][nf] face traces
   double* fbuf = nullptr;       // [E][2dim][(1+dim)nv][nf] face fluxes to lift
   double* force = nullptr;      // [ndof] M^-1 B^T wJ f (nullptr when no forcing)
+  double* avf = nullptr;        // [E] artificial-viscosity factor (shock capturing only)
+  dg::SensorTab stab;
   double* scratch = nullptr;    // [64]: [0,4) JFNK eps, 1/eps, norms; [8,13) BRJ chi;
                                 //   [16] inversion failure flag; [24,26) GMRES {t, -dt_a}
   double* red = nullptr;        // reduction partials
@@ -132,7 +146,7 @@ extern long long g_launches;
 enum KernelId {
   K_VOL, K_FACE, K_LIFT, K_PROJECT, K_DOT, K_MULTIDOT, K_MULTIAXPY, K_VEC,
   K_BRJ_WEIGHTS, K_BRJ_TRACEJAC, K_BRJ_BLOCK, K_BRJ_INVERT, K_BRJ_DIAG,
-  K_BRJ_OFFDIAG, K_MLP, K_BRJ_SWEEP, K_COUNT
+  K_BRJ_OFFDIAG, K_MLP, K_BRJ_SWEEP, K_SENSOR, K_COUNT
 };
 int prof_begin(int id, cudaStream_t s);
 void prof_end(int handle, cudaStream_t s);
@@ -167,6 +181,8 @@ struct EvalArgs {
 dg_status launch_residual(dg_mesh_s* m, const EvalArgs& a, cudaStream_t s);
 dg_status build_general_geometry(dg_mesh_s* m, const double* nodes_host, int g, cudaStream_t s);
 dg_status launch_project(dg_mesh_s* m, int what, double t, double* out, cudaStream_t s);
+// artificial-viscosity factor mu_0 S_e h_e / P of every element at u into out [E]
+dg_status launch_sensor(dg_mesh_s* m, const double* u, double* out, cudaStream_t s);
 bool supported(int dim, int P, int Q);
 bool supported_curved(int dim, int P, int Q);  // general-geometry instances
 inline GenGeo gen_geo(const dg_mesh_s* m) {

@@ -73,13 +73,17 @@ __device__ inline void euler_flux(const T* U, const Phys& ph, T F[D][D + 2]) {
 }
 
 // Diffusion flux G[i][v] of Eq. (conserved fluxes) from the physical gradient
-// dU[j][v] of the conservative variables (linear in dU at fixed U).
+// dU[j][v] of the conservative variables (linear in dU at fixed U).  mu_add:
+// artificial viscosity added to mu (and, through kappa_fac, its conductivity
+// mu_add C_p / Pr); a constant here, so a dual-number U does not carry its
+// derivative.
 template <int D, typename T, typename TG>
 __device__ inline void viscous_flux(const T* U, const TG dU[D][D + 2], const Phys& ph,
-                                    T G[D][D + 2]) {
+                                    T G[D][D + 2], double mu_add = 0.0) {
   T irho, vel[D], p, temp;
   primitives<D>(U, ph, irho, vel, p, temp);
   T mu = viscosity(temp, ph);
+  if (mu_add != 0.0) mu += T(mu_add);
   T e = U[D + 1] * irho;
   T dvel[D][D], dT[D];
 #pragma unroll
@@ -111,6 +115,33 @@ __device__ inline void viscous_flux(const T* U, const TG dU[D][D + 2], const Phy
     }
     G[i][D + 1] = en;
   }
+}
+
+// ------------------------------------------------------------ shock capturing
+// Artificial viscosity at a point (Sec. 3.1.2): mu_av = f_e rho (c + |u|),
+// f_e = mu_0 S_e h_e / P the element factor of the modal sensor.
+template <int D>
+__device__ inline double av_point(const double* U, const Phys& ph, double fe) {
+  if (fe == 0.0) return 0.0;
+  const double irho = 1.0 / U[0];
+  double ke = 0.0;
+#pragma unroll
+  for (int k = 0; k < D; ++k) ke = fma(U[1 + k], U[1 + k], ke);
+  ke *= irho;  // rho |u|^2
+  const double p = ph.gm1 * (U[D + 1] - 0.5 * ke);
+  return fe * U[0] * (sqrt(ph.gamma * p * irho) + sqrt(ke * irho));
+}
+
+// Artificial viscosity on a face point: the mean of the two sides' values,
+// each from its own trace and element factor; the interior side's alone on a
+// boundary face (eR < 0).
+template <int D>
+__device__ inline double av_face(const Phys& ph, int eL, int eR, const double* QL,
+                                 const double* QR) {
+  if (!ph.avf) return 0.0;
+  const double a = av_point<D>(QL, ph, ph.avf[eL]);
+  if (eR < 0) return a;
+  return 0.5 * (a + av_point<D>(QR, ph, ph.avf[eR]));
 }
 
 // Normal Euler flux F(U).n
@@ -386,6 +417,35 @@ __device__ inline void exact_state(int D, const Phys& ph, const double* x, doubl
     rho = ph.fpar[0];
     for (int k = 0; k < D; ++k) vel[k] = ph.fpar[1 + k];
     temp = ph.fpar[4];
+  } else if (ph.field == DG_FIELD_SHOCK) {
+    // oblique shock at beta = fpar[0] degrees to the x axis, meeting y = 0 at
+    // x = fpar[1]: the stream (1, 0) below the line, above it the state the
+    // Rankine-Hugoniot jump conditions give for the normal Mach number
+    // Ma sin(beta) (tangential velocity unchanged)
+    // fpar[2] > 0: a smooth passage between the two states over the width
+    // fpar[2] (fraction (1 + tanh(s / w)) / 2 of the signed distance s to the
+    // line, on the primitive variables); fpar[3] > 0: the velocity brought to
+    // rest at y = 0 by 1 - exp(-y / fpar[3])
+    const double beta = ph.fpar[0] * (PI / 180.0);
+    const double sb = sin(beta), cb = cos(beta);
+    double post;
+    if (ph.fpar[2] > 0.0)
+      post = 0.5 * (1.0 + tanh((x[1] * cb - (ph.fpar[1] - x[0]) * sb) / ph.fpar[2]));
+    else
+      post = x[1] > (ph.fpar[1] - x[0]) * (sb / cb) ? 1.0 : 0.0;
+    const double mn2 = ph.Ma * ph.Ma * sb * sb;
+    const double rr = (ph.gamma + 1.0) * mn2 / (ph.gm1 * mn2 + 2.0);   // rho2 / rho1
+    const double pr = 1.0 + 2.0 * ph.gamma / (ph.gamma + 1.0) * (mn2 - 1.0);  // p2 / p1
+    const double un = sb / rr, ut = cb;  // normal and tangential speeds behind
+    rho = 1.0 + post * (rr - 1.0);
+    vel[0] = 1.0 + post * (un * sb + ut * cb - 1.0);
+    vel[1] = post * (un * cb - ut * sb);
+    if (ph.fpar[3] > 0.0) {
+      const double f = 1.0 - exp(-x[1] / ph.fpar[3]);
+      vel[0] *= f;
+      vel[1] *= f;
+    }
+    temp = (1.0 + post * (pr - 1.0)) / rho;  // gamma Ma^2 p / rho with p1 = 1/(gamma Ma^2)
   } else if (ph.field == DG_FIELD_CYLINDER && ph.fpar[1] > 0.0) {
     // stream brought to rest at the wall r = fpar[0] over the length fpar[1]
     const double r = sqrt(x[0] * x[0] + x[1] * x[1]);
@@ -519,7 +579,7 @@ template <int D>
 __device__ inline void numerical_flux_n(const double* QL, const double* QRin, int bctype,
                                         const double* x, double t, const double dQa[D][D + 2],
                                         const double* n, double beta, const Phys& ph,
-                                        double* Hn, double S[D][D + 2]) {
+                                        double* Hn, double S[D][D + 2], double mu_add = 0.0) {
   constexpr int NV = D + 2;
   double QR[NV], Qa[NV], jump[NV];
   bool adiabatic = false;
@@ -542,9 +602,9 @@ __device__ inline void numerical_flux_n(const double* QL, const double* QRin, in
     for (int j = 0; j < D; ++j)
 #pragma unroll
       for (int v = 0; v < NV; ++v) gS[j][v] = n[j] * jump[v];
-    viscous_flux<D>(Qa, gS, ph, S);
+    viscous_flux<D>(Qa, gS, ph, S, mu_add);
     double Gv[D][NV];
-    viscous_flux<D>(Qa, dQa, ph, Gv);
+    viscous_flux<D>(Qa, dQa, ph, Gv, mu_add);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       if (adiabatic && v == NV - 1) continue;
@@ -569,11 +629,11 @@ template <int D>
 __device__ inline void numerical_flux(const double* QL, const double* QRin, int bctype,
                                       const double* x, double t, const double dQa[D][D + 2],
                                       int r, double sgn, double beta, const Phys& ph,
-                                      double* Hn, double S[D][D + 2]) {
+                                      double* Hn, double S[D][D + 2], double mu_add = 0.0) {
   double n[D];
 #pragma unroll
   for (int k = 0; k < D; ++k) n[k] = k == r ? sgn : 0.0;
-  numerical_flux_n<D>(QL, QRin, bctype, x, t, dQa, n, beta, ph, Hn, S);
+  numerical_flux_n<D>(QL, QRin, bctype, x, t, dQa, n, beta, ph, Hn, S, mu_add);
 }
 
 // ------------------------------------------------------------ fused / axis-specialised forms
@@ -586,7 +646,7 @@ __device__ inline void numerical_flux(const double* QL, const double* QRin, int 
 // H = F - G at a volume point with shared primitive variables
 template <int D>
 __device__ inline void ns_volume_flux(const double* U, const double dU[D][D + 2], const Phys& ph,
-                                      double H[D][D + 2]) {
+                                      double H[D][D + 2], double fe = 0.0) {
   constexpr int NV = D + 2;
   const double irho = 1.0 / U[0];
   double vel[D], ke = 0.0;
@@ -607,7 +667,8 @@ __device__ inline void ns_volume_flux(const double* U, const double dU[D][D + 2]
   }
   if (!ph.viscous) return;
   const double temp = ph.gMa2 * p * irho;
-  const double mu = viscosity(temp, ph);
+  double mu = viscosity(temp, ph);
+  if (fe != 0.0) mu += fe * U[0] * (sqrt(ph.gamma * p * irho) + sqrt(ke * irho));
   const double kap = mu * ph.kappa_fac;
   const double e = U[D + 1] * irho;
   double dvel[D][D], dT[D];
@@ -710,7 +771,8 @@ struct ViscPrim {
   double irho, vel[D], e, mu, kap;
 };
 template <int D>
-__device__ inline void visc_prim(const double* U, const Phys& ph, ViscPrim<D>& s) {
+__device__ inline void visc_prim(const double* U, const Phys& ph, ViscPrim<D>& s,
+                                 double mu_add = 0.0) {
   s.irho = 1.0 / U[0];
   double ke = 0.0;
 #pragma unroll
@@ -721,6 +783,7 @@ __device__ inline void visc_prim(const double* U, const Phys& ph, ViscPrim<D>& s
   const double p = ph.gm1 * (U[D + 1] - 0.5 * ke);
   s.e = U[D + 1] * s.irho;
   s.mu = viscosity(ph.gMa2 * p * s.irho, ph);
+  if (mu_add != 0.0) s.mu += mu_add;
   s.kap = s.mu * ph.kappa_fac;
 }
 
@@ -789,7 +852,8 @@ template <int D, int R>
 __device__ inline void numerical_flux_axis(const double* QL, const double* QRin, int bctype,
                                            const double* x, double t,
                                            const double dQa[D][D + 2], double sgn, double beta,
-                                           const Phys& ph, double* Hn, double S[D][D + 2]) {
+                                           const Phys& ph, double* Hn, double S[D][D + 2],
+                                           double mu_add = 0.0) {
   constexpr int NV = D + 2;
   double QR[NV], Qa[NV], Qj[NV];
   bool adiabatic = false;
@@ -818,7 +882,7 @@ __device__ inline void numerical_flux_axis(const double* QL, const double* QRin,
   }
   if (ph.viscous) {
     ViscPrim<D> pa;
-    visc_prim<D>(Qa, ph, pa);
+    visc_prim<D>(Qa, ph, pa, mu_add);
     double g[NV], Gr[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) g[v] = sgn * (QL[v] - Qj[v]);

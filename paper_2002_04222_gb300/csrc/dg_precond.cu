@@ -117,6 +117,8 @@ __global__ void __launch_bounds__(256) brj_weights_kernel(const __grid_constant_
           dU[j][v] = a;
         }
       }
+      // artificial viscosity held at the linearisation state (not differentiated)
+      const double mua = ph.avf ? av_point<DIM>(U, ph, ph.avf[e]) : 0.0;
       TW* Wq = W + (long long)el * NQ * NW + q;  // [(k NV + l) JA + ja][NQ]
       for (int l = 0; l < NV; ++l) {
         Dual Ud[NV];
@@ -126,7 +128,7 @@ __global__ void __launch_bounds__(256) brj_weights_kernel(const __grid_constant_
         euler_flux<DIM>(Ud, ph, F);
         if (ph.viscous) {
           Dual G[DIM][NV];
-          viscous_flux<DIM, Dual, double>(Ud, dU, ph, G);
+          viscous_flux<DIM, Dual, double>(Ud, dU, ph, G, mua);
 #pragma unroll
           for (int j = 0; j < DIM; ++j)
 #pragma unroll
@@ -155,7 +157,7 @@ __global__ void __launch_bounds__(256) brj_weights_kernel(const __grid_constant_
             for (int a = 0; a < DIM; ++a)
 #pragma unroll
               for (int v = 0; v < NV; ++v) gu[a][v] = (a == i && v == l) ? 1.0 : 0.0;
-            viscous_flux<DIM>(U, gu, ph, G);
+            viscous_flux<DIM>(U, gu, ph, G, mua);
 #pragma unroll
             for (int r = 0; r < DIM; ++r)
 #pragma unroll
@@ -197,6 +199,7 @@ __global__ void __launch_bounds__(256) brj_weights_kernel(const __grid_constant_
 #pragma unroll
       for (int r = 0; r < DIM; ++r) dU[r][v] = sG[(r * NV + v) * NQ + q] * rh[r];
     }
+    const double mua = ph.avf ? av_point<DIM>(U, ph, ph.avf[e]) : 0.0;
     TW* Wq = W + (long long)el * NQ * NW + q;  // [(k NV + l) JA + ja][NQ]
     for (int l = 0; l < NV; ++l) {
       Dual Ud[NV];
@@ -206,7 +209,7 @@ __global__ void __launch_bounds__(256) brj_weights_kernel(const __grid_constant_
       euler_flux<DIM>(Ud, ph, F);
       if (ph.viscous) {
         Dual G[DIM][NV];
-        viscous_flux<DIM, Dual, double>(Ud, dU, ph, G);
+        viscous_flux<DIM, Dual, double>(Ud, dU, ph, G, mua);
 #pragma unroll
         for (int j = 0; j < DIM; ++j)
 #pragma unroll
@@ -227,7 +230,7 @@ __global__ void __launch_bounds__(256) brj_weights_kernel(const __grid_constant_
           for (int a = 0; a < DIM; ++a)
 #pragma unroll
             for (int v = 0; v < NV; ++v) gu[a][v] = (a == i && v == l) ? 1.0 : 0.0;
-          viscous_flux<DIM>(U, gu, ph, G);
+          viscous_flux<DIM>(U, gu, ph, G, mua);
         } else {
 #pragma unroll
           for (int a = 0; a < DIM; ++a)
@@ -306,7 +309,9 @@ __global__ void __launch_bounds__(128) brj_tracejac_kernel(
   }
   const double beta = (double)((P + 1) * (P + 1)) / hmin;
   double H0[NV], H1[NV], S[DIM][NV];
-  numerical_flux<DIM>(QL, QR, bctype, x, t, dQa, r, sgn, beta, ph, H0, S);
+  // artificial viscosity held at the linearisation state's traces
+  const double mua = av_face<DIM>(ph, eL, eR, QL, QR);
+  numerical_flux<DIM>(QL, QR, bctype, x, t, dQa, r, sgn, beta, ph, H0, S, mua);
   TJ* jdl = Jd + (((long long)eL * 2 * DIM + fL) * NF + p) * NV * NV;
   TJ* jol = Jo + ((long long)eL * 2 * DIM + fL) * NV * NV * NF + p;
   TJ* jdr = eR >= 0 ? Jd + (((long long)eR * 2 * DIM + fR) * NF + p) * NV * NV : nullptr;
@@ -317,7 +322,7 @@ __global__ void __launch_bounds__(128) brj_tracejac_kernel(
     double Qp[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) Qp[v] = QL[v] + (v == l ? h : 0.0);
-    numerical_flux<DIM>(Qp, QR, bctype, x, t, dQa, r, sgn, beta, ph, H1, S);
+    numerical_flux<DIM>(Qp, QR, bctype, x, t, dQa, r, sgn, beta, ph, H1, S, mua);
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
       const double dHdL = (H1[k] - H0[k]) * ih;
@@ -327,7 +332,7 @@ __global__ void __launch_bounds__(128) brj_tracejac_kernel(
     if (eR >= 0) {
 #pragma unroll
       for (int v = 0; v < NV; ++v) Qp[v] = QR[v] + (v == l ? h : 0.0);
-      numerical_flux<DIM>(QL, Qp, bctype, x, t, dQa, r, sgn, beta, ph, H1, S);
+      numerical_flux<DIM>(QL, Qp, bctype, x, t, dQa, r, sgn, beta, ph, H1, S, mua);
 #pragma unroll
       for (int k = 0; k < NV; ++k) {
         const double dHdR = (H1[k] - H0[k]) * ih;
@@ -388,7 +393,8 @@ __global__ void __launch_bounds__(128) brj_tracejac_gen_kernel(
     for (int v = 0; v < NV; ++v) QR[v] = 0.0;
   }
   double H0[NV], H1[NV], S[DIM][NV];
-  numerical_flux_n<DIM>(QL, QR, bctype, x, t, dQa, n, beta, ph, H0, S);
+  const double mua = av_face<DIM>(ph, eL, eR, QL, QR);
+  numerical_flux_n<DIM>(QL, QR, bctype, x, t, dQa, n, beta, ph, H0, S, mua);
   TJ* jdl = Jd + (((long long)eL * 2 * DIM + fL) * NF + p) * NV * NV;
   TJ* jol = Jo + ((long long)eL * 2 * DIM + fL) * NV * NV * NF + p;
   TJ* jdr = eR >= 0 ? Jd + (((long long)eR * 2 * DIM + fR) * NF + p) * NV * NV : nullptr;
@@ -399,7 +405,7 @@ __global__ void __launch_bounds__(128) brj_tracejac_gen_kernel(
     double Qp[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) Qp[v] = QL[v] + (v == l ? h : 0.0);
-    numerical_flux_n<DIM>(Qp, QR, bctype, x, t, dQa, n, beta, ph, H1, S);
+    numerical_flux_n<DIM>(Qp, QR, bctype, x, t, dQa, n, beta, ph, H1, S, mua);
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
       const double dHdL = (H1[k] - H0[k]) * ih;
@@ -409,7 +415,7 @@ __global__ void __launch_bounds__(128) brj_tracejac_gen_kernel(
     if (eR >= 0) {
 #pragma unroll
       for (int v = 0; v < NV; ++v) Qp[v] = QR[v] + (v == l ? h : 0.0);
-      numerical_flux_n<DIM>(QL, Qp, bctype, x, t, dQa, n, beta, ph, H1, S);
+      numerical_flux_n<DIM>(QL, Qp, bctype, x, t, dQa, n, beta, ph, H1, S, mua);
 #pragma unroll
       for (int k = 0; k < NV; ++k) {
         const double dHdR = (H1[k] - H0[k]) * ih;

@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(256) vol_kernel(const __grid_constant__ Tables
           dU[j][vv] = a;
         }
       }
-      ns_volume_flux<DIM>(U, dU, ph, H);
+      ns_volume_flux<DIM>(U, dU, ph, H, ph.avf ? ph.avf[e] : 0.0);
       double* hb = hbuf + (long long)e * DIM * NV * NQ + q;
 #pragma unroll
       for (int r = 0; r < DIM; ++r)
@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(256) vol_kernel(const __grid_constant__ Tables
 #pragma unroll
       for (int r = 0; r < DIM; ++r) dU[r][vv] = sG[((r * EPB + eb) * NV + vv) * NQ + q] * rh[r];
     }
-    ns_volume_flux<DIM>(U, dU, ph, H);
+    ns_volume_flux<DIM>(U, dU, ph, H, ph.avf ? ph.avf[e] : 0.0);
     double wJ = sw[c[0]] * sw[c[1]] * (DIM == 3 ? sw[c[2]] : 1.0);
     wJ *= g.detJ;
     double* hb = hbuf + (long long)e * DIM * NV * NQ + q;
@@ -307,12 +307,13 @@ __global__ void __launch_bounds__(128) face_kernel(const __grid_constant__ Table
   }
   double Hn[NV], S[DIM][NV];
   const double beta = (double)((P + 1) * (P + 1)) * 0.5 * rmax;  // (P+1)^2 / h
+  const double mua = av_face<DIM>(ph, eL, eR, QL, QR);
   if (r == 0)
-    numerical_flux_axis<DIM, 0>(QL, QR, bctype, x, t, dQa, sgn, beta, ph, Hn, S);
+    numerical_flux_axis<DIM, 0>(QL, QR, bctype, x, t, dQa, sgn, beta, ph, Hn, S, mua);
   else if (r == 1)
-    numerical_flux_axis<DIM, 1>(QL, QR, bctype, x, t, dQa, sgn, beta, ph, Hn, S);
+    numerical_flux_axis<DIM, 1>(QL, QR, bctype, x, t, dQa, sgn, beta, ph, Hn, S, mua);
   else
-    numerical_flux_axis<DIM, DIM - 1>(QL, QR, bctype, x, t, dQa, sgn, beta, ph, Hn, S);
+    numerical_flux_axis<DIM, DIM - 1>(QL, QR, bctype, x, t, dQa, sgn, beta, ph, Hn, S, mua);
   double* fl = fbuf + (long long)eL * NTR + (fL * (1 + DIM)) * NV * NF + p;
   const double cs = ph.viscous ? cfac * ph.beta_s * wJf : 0.0;
   double csL[DIM];
@@ -389,7 +390,8 @@ __global__ void __launch_bounds__(128) face_kernel_gen(const __grid_constant__ P
     for (int vv = 0; vv < NV; ++vv) QR[vv] = 0.0;
   }
   double Hn[NV], S[DIM][NV];
-  numerical_flux_n<DIM>(QL, QR, bctype, x, t, dQa, n, gg.fbeta[f], ph, Hn, S);
+  numerical_flux_n<DIM>(QL, QR, bctype, x, t, dQa, n, gg.fbeta[f], ph, Hn, S,
+                        av_face<DIM>(ph, eL, eR, QL, QR));
   const double cs = ph.viscous ? cfac * ph.beta_s * wJf : 0.0;
 #pragma unroll
   for (int side = 0; side < 2; ++side) {
@@ -653,6 +655,94 @@ __global__ void __launch_bounds__(256) project_kernel(const __grid_constant__ Ta
   }
 }
 
+// ---------------------------------------------------------------- shock sensor
+// Artificial-viscosity factor f_e = mu_0 S_e h_e / P of every element at the
+// state u (+ eps v) (Sec. 3.1.2).  One warp per element: the density's
+// modified-basis coefficients go to Legendre coefficients c by the 1-D
+// transform along each direction; the reference-element L2 norms are then
+// sums of c^2 times the Legendre norms, and the part removed by the
+// projection onto degree <= P-1 per direction is the set of modes with some
+// index equal to P.
+constexpr int SENSOR_WARPS = 8;
+template <int DIM, int P, int Q, bool CV>
+__global__ void __launch_bounds__(32 * SENSOR_WARPS) sensor_kernel(
+    const __grid_constant__ SensorTab st, const __grid_constant__ Phys ph,
+    const ElemGeo* __restrict__ geo, const __grid_constant__ GenGeo gg, int E,
+    const double* __restrict__ u, const double* __restrict__ v, const double* __restrict__ epsp,
+    double* __restrict__ avf) {
+  using C = Cfg<DIM, P, Q>;
+  constexpr int N = C::N, NV = C::NV, NM = C::NM, NQ = C::NQ;
+  __shared__ double sA[SENSOR_WARPS][NM], sC[SENSOR_WARPS][NM];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int e = blockIdx.x * SENSOR_WARPS + w;
+  if (e >= E) return;  // warp-uniform; the kernel has no block-wide barrier
+  const double eps = v ? epsp[0] : 0.0;
+  const long long base = (long long)e * NV * NM;  // variable 0: density
+  for (int k = lane; k < NM; k += 32) {
+    double val = u[base + k];
+    if (v) val = fma(eps, v[base + k], val);
+    sA[w][k] = val;
+  }
+  __syncwarp();
+  double* src = sA[w];
+  double* dst = sC[w];
+  int stride = 1;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    for (int mm = lane; mm < NM; mm += 32) {
+      const int id = (mm / stride) % N;
+      const int m0 = mm - id * stride;
+      double a = 0.0;
+#pragma unroll
+      for (int k = 0; k < N; ++k) a = fma(st.T[id * N + k], src[m0 + k * stride], a);
+      dst[mm] = a;
+    }
+    __syncwarp();
+    double* tmp = src;
+    src = dst;
+    dst = tmp;
+    stride *= N;
+  }
+  double num = 0.0, den = 0.0, vol = 0.0;
+  for (int mm = lane; mm < NM; mm += 32) {
+    int r = mm;
+    double wgt = 1.0;
+    bool top = false;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      const int id = r % N;
+      r /= N;
+      wgt *= st.nrm[id];
+      top = top || id == P;
+    }
+    const double c2 = src[mm] * src[mm] * wgt;
+    den += c2;
+    if (top) num += c2;
+  }
+  if constexpr (CV) {
+    const double* wj = gg.vgeo + (long long)e * (DIM * DIM + 1) * NQ + DIM * DIM * NQ;
+    for (int q = lane; q < NQ; q += 32) vol += wj[q];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    num += __shfl_xor_sync(0xffffffffu, num, o);
+    den += __shfl_xor_sync(0xffffffffu, den, o);
+    vol += __shfl_xor_sync(0xffffffffu, vol, o);
+  }
+  if (lane != 0) return;
+  if constexpr (!CV) vol = geo[e].detJ * (double)(1 << DIM);
+  const double h = DIM == 2 ? sqrt(vol) : cbrt(vol);
+  double S = 0.0;
+  if (num > 0.0 && den > 0.0) {
+    const double se = log10(num / den), s0 = -4.0 * log10((double)P), kap = ph.av_kappa;
+    if (se > s0 + kap)
+      S = 1.0;
+    else if (se >= s0 - kap)
+      S = 0.5 * (1.0 + sin(3.14159265358979323846 * (se - s0) / (2.0 * kap)));
+  }
+  avf[e] = ph.av_mu0 * S * h / (double)P;
+}
+
 // ---------------------------------------------------------------- launchers
 template <int DIM, int P, int Q, bool CV>
 static dg_status run_residual_g(dg_mesh_s* m, const EvalArgs& a, cudaStream_t s) {
@@ -666,6 +756,12 @@ static dg_status run_residual_g(dg_mesh_s* m, const EvalArgs& a, cudaStream_t s)
   DG_CUDA(cudaFuncSetAttribute(lift_kernel<DIM, P, Q, CV>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm));
   if (!a.skip_vol) {
+    if (m->phys.avf) {
+      DG_PROF(K_SENSOR, s, sensor_kernel<DIM, P, Q, CV><<<(m->E + SENSOR_WARPS - 1) / SENSOR_WARPS,
+                                                          32 * SENSOR_WARPS, 0, s>>>(
+          m->stab, m->phys, m->geo, gg, m->E, a.u, a.v, a.eps, m->avf));
+      DG_LAUNCHED(1);
+    }
     DG_PROF(K_VOL, s, vol_kernel<DIM, P, Q, CV><<<(m->E + vepb - 1) / vepb, vnt, vsm, s>>>(
         m->tab, m->phys, m->geo, gg, m->E, a.u, a.v, a.eps, m->hbuf, m->tbuf, vepb));
     DG_LAUNCHED(1);
@@ -767,6 +863,33 @@ bool supported(int dim, int P, int Q) {
 dg_status launch_residual(dg_mesh_s* m, const EvalArgs& a, cudaStream_t s) {
 #define DG_RUN(D_, P_, Q_) \
   if (m->dim == D_ && m->P == P_ && m->Q == Q_) return run_residual<D_, P_, Q_>(m, a, s);
+  DG_INSTANCES(DG_RUN)
+#undef DG_RUN
+  return DG_ERR_UNSUPPORTED;
+}
+
+template <int DIM, int P, int Q>
+static dg_status run_sensor(dg_mesh_s* m, const double* u, double* out, cudaStream_t s) {
+  const GenGeo gg = gen_geo(m);
+  const int nb = (m->E + SENSOR_WARPS - 1) / SENSOR_WARPS;
+  if (m->curved) {
+    if constexpr (has_curved<DIM, P, Q>()) {
+      DG_PROF(K_SENSOR, s, sensor_kernel<DIM, P, Q, true><<<nb, 32 * SENSOR_WARPS, 0, s>>>(
+          m->stab, m->phys, m->geo, gg, m->E, u, nullptr, nullptr, out));
+      DG_LAUNCHED(1);
+      return DG_OK;
+    }
+    return DG_ERR_UNSUPPORTED;
+  }
+  DG_PROF(K_SENSOR, s, sensor_kernel<DIM, P, Q, false><<<nb, 32 * SENSOR_WARPS, 0, s>>>(
+      m->stab, m->phys, m->geo, gg, m->E, u, nullptr, nullptr, out));
+  DG_LAUNCHED(1);
+  return DG_OK;
+}
+
+dg_status launch_sensor(dg_mesh_s* m, const double* u, double* out, cudaStream_t s) {
+#define DG_RUN(D_, P_, Q_) \
+  if (m->dim == D_ && m->P == P_ && m->Q == Q_) return run_sensor<D_, P_, Q_>(m, u, out, s);
   DG_INSTANCES(DG_RUN)
 #undef DG_RUN
   return DG_ERR_UNSUPPORTED;

@@ -38,6 +38,7 @@ def test_null_handles_and_pointers_are_rejected(lib):
         "dg_mesh_info": (NULL, NULL),
         "dg_project": (NULL, d(0.0), NULL, NULL),
         "dg_residual": (NULL, NULL, d(0.0), NULL, NULL),
+        "dg_av_factor": (NULL, NULL, NULL, NULL),
         "dg_jvp": (NULL, NULL, NULL, d(0.0), NULL, d(0.0), d(1.0), NULL, NULL),
         "dg_precond_build": (NULL, NULL, d(0.0), d(0.1), ctypes.byref(pcfg), ctypes.byref(out),
                              NULL),

@@ -45,6 +45,35 @@ def test_shock_field_states_on_both_sides_of_the_line():
     assert np.allclose(U[2, :3], [r2, r2 * v2[0], r2 * v2[1]])        # behind the foot
 
 
+def test_smoothed_shock_field_limits():
+    """width w > 0: the sharp states a few w away from the line, the mean of
+    the two primitive states on it; wall layer l > 0: velocity zero at y = 0
+    and within 1e-12 of the layer-free field at y = 30 l."""
+    sharp = w.Physics(Ma=2.15, fid=phy.FIELD_SHOCK, fpar=(30.8, 1.0))
+    smooth = w.Physics(Ma=2.15, fid=phy.FIELD_SHOCK, fpar=(30.8, 1.0, 0.01, 0.0))
+    beta = np.radians(30.8)
+    nrm = np.array([np.sin(beta), np.cos(beta)])          # unit normal, post side
+    foot = np.array([1.0, 0.0])
+    for sgn in (-1.0, 1.0):
+        x = (foot + np.array([-0.5, 0.3]) + sgn * 0.2 * nrm)[None, :]
+        assert np.allclose(phy.exact_state(smooth, x, 0.0), phy.exact_state(sharp, x, 0.0),
+                           rtol=1e-12, atol=1e-12)
+    on = (foot + np.array([-0.5, 0.3]))                    # a point of the line y = (1-x) tan b
+    on[1] = (1.0 - on[0]) * np.tan(beta)
+    rho, vel, p, _ = phy.primitives(phy.exact_state(smooth, on[None, :], 0.0), smooth)
+    r2, v2, p2 = phy.oblique_shock_state(beta, smooth)
+    p1 = 1.0 / (smooth.gamma * smooth.Ma ** 2)
+    assert np.allclose([rho[0], vel[0, 0], vel[0, 1], p[0]],
+                       [(1 + r2) / 2, (1 + v2[0]) / 2, v2[1] / 2, (p1 + p2) / 2], rtol=1e-13)
+    layer = w.Physics(Ma=2.15, fid=phy.FIELD_SHOCK, fpar=(30.8, 1.0, 0.01, 0.02))
+    xw = np.array([[1.5, 0.0], [0.5, 0.0], [1.5, 0.6]])
+    U = phy.exact_state(layer, xw, 0.0)
+    _, vel, _, _ = phy.primitives(U, layer)
+    assert np.all(vel[:2] == 0.0)
+    U0 = phy.exact_state(smooth, xw[2:], 0.0)
+    assert np.allclose(U[2:], U0, rtol=1e-12, atol=1e-12)
+
+
 def sensor_case(P=3, n=2):
     c = w.vortex_case(n=n, P=P, Q=P + 2)
     c.phys.av = 1

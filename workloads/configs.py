@@ -203,7 +203,8 @@ def wall_spacing(n, ratio, length=1.0):
 
 
 def swbli_case(nx=119, ny=39, P=3, Q=None, Ma=2.15, Re=1.0e5, beta_deg=30.8, x0=0.3, x1=2.0,
-               height=1.0, ratio=1.1, av=1, riemann=RIEMANN_ROE):
+               height=1.0, ratio=1.1, av=1, riemann=RIEMANN_ROE, shock_width=0.02,
+               wall_layer=0.01):
     """Shock-wave / boundary-layer interaction of the kind of Sec. 6.5: an
     oblique shock of angle beta_deg (to the stream) generated above the plate
     reaches the adiabatic no-slip wall y = 0 at x = 1 (the unit length, on
@@ -211,12 +212,15 @@ def swbli_case(nx=119, ny=39, P=3, Q=None, Ma=2.15, Re=1.0e5, beta_deg=30.8, x0=
     spacing growing by `ratio` away from the wall), the uniform stream at Ma
     below the shock line and the Rankine-Hugoniot state above it imposed on
     the inflow (x = x0) and top sides, a characteristic far-field outflow,
-    the artificial-viscosity shock capturing of Sec. 3.1.2 (av = 1)."""
+    the artificial-viscosity shock capturing of Sec. 3.1.2 (av = 1).  The field
+    (initial state and boundary data) passes through the shock over
+    `shock_width` and has the velocity brought to rest at the wall over
+    `wall_layer` (0: a sharp jump, a uniform stream down to the wall)."""
     Q = P + 2 if Q is None else Q
     xl = np.linspace(x0, x1, nx + 1)
     yl = wall_spacing(ny, ratio, height)
     m = box_mesh([xl, yl], (False, False), side_bc=[0, 1, 2, 0])
-    ph = Physics(Ma=Ma, Re=Re, fid=FIELD_SHOCK, fpar=(beta_deg, 1.0),
+    ph = Physics(Ma=Ma, Re=Re, fid=FIELD_SHOCK, fpar=(beta_deg, 1.0, shock_width, wall_layer),
                  bc=[BC_DIRICHLET, BC_FARFIELD, BC_ADIA_WALL], av=av, riemann=riemann)
     return Case(f"swbli{nx}x{ny}_P{P}", m, P, Q, ph)
 
