@@ -46,7 +46,8 @@ TGV24 = {"n": 24, "P": 4, "Q": 8, "Re": 1600.0, "Ma": 0.1, "cfl": 0.10, "dt_fact
 # P = 3, Ma 2.15, Re 1e5 on the shock's foot distance, shock at 30.8 degrees),
 # artificial-viscosity shock capturing (Sec. 3.1.2), SDIRK2; time step from
 # Eq. CFL on the first cell at the wall with c + |u| = 1/Ma + 1
-SWBLI = {"nx": 119, "ny": 39, "P": 3, "Q": 5, "Ma": 2.15, "Re": 1.0e5, "beta": 30.8, "cfl": 100.0}
+SWBLI = {"nx": 119, "ny": 39, "P": 3, "Q": 5, "Ma": 2.15, "Re": 1.0e5, "beta": 30.8, "cfl": 100.0,
+         "ramp": (0.1,), "kappa": 1.0}
 SAMPLE_N = 3          # CPU sample: the same case on 3^3 elements (same P, Q, CFL)
 FREEZE = 10
 # DRAM bytes (read + write) per element and launch from one ncu capture of the
@@ -296,8 +297,11 @@ def run_ours(args, rank, world):
         dt = cylinder_dt(wl)
     elif sw:
         wl["cfl"] = args.cfl if args.cfl is not None else wl["cfl"]
+        wl["beta"] = args.shock_angle if args.shock_angle is not None else wl["beta"]
+        wl["kappa"] = args.av_kappa if args.av_kappa is not None else wl["kappa"]
         case = w.swbli_case(nx=wl["nx"], ny=wl["ny"], P=wl["P"], Q=wl["Q"], Ma=wl["Ma"],
                             Re=wl["Re"], beta_deg=wl["beta"])
+        case.phys.av_kappa = wl["kappa"]
         dt = swbli_dt(case, wl)
     else:
         case = w.tgv_case(n=wl["n"], P=wl["P"], Q=wl["Q"], Re=wl["Re"], Ma=wl["Ma"])
@@ -337,12 +341,13 @@ def run_ours(args, rank, world):
         stats.append(st)
         return st
 
-    if cyl:
-        # start-up (untimed): steps at dt/4 and dt/2 from the synthetic field,
-        # preconditioner rebuilt at every step size, then the step counter
-        # restarts so that the timed steps see the regular rebuild cadence
+    if cyl or sw:
+        # start-up (untimed): steps at fractions of dt from the synthetic field
+        # (cylinder: dt/4, dt/2; SWBLI: dt/10), preconditioner rebuilt at every
+        # step size, then the step counter restarts so that the timed steps see
+        # the regular rebuild cadence
         for f in wl["ramp"]:
-            step(u, cylinder_dt(wl, f), rebuild=True)
+            step(u, dt * f, rebuild=True)
         state["k"] = 0
 
     def barrier():
@@ -461,14 +466,15 @@ def run_ours(args, rank, world):
         u0 = m.project(0.0)
         variants = [time_variant(m, u0, dt, p_, g_, f_, args.steps, args.warmup)
                     for p_, g_, f_ in VARIANTS]
+    av_elements = int((m.av_factor(u) > 0).sum().item()) if sw else None
     newton = [s["newton_iters"] for s in timed_stats]
     gm = [s["gmres_iters"] for s in timed_stats]
     if sw:
         metric = ("SDIRK2 step throughput at fixed Newton tolerance (DOF-steps/s); SWBLI "
-                  f"{wl['nx']}x{wl['ny']} quads P={wl['P']}, Ma {wl['Ma']:g}, artificial viscosity, "
-                  f"CFL {wl['cfl']:g}")
-        wname = (f"swbli{wl['nx']}x{wl['ny']}_P{wl['P']}_Q{wl['Q']}_Ma{wl['Ma']:g}_av_sdirk2"
-                 f"_cfl{wl['cfl']:g}")
+                  f"{wl['nx']}x{wl['ny']} quads P={wl['P']}, Ma {wl['Ma']:g}, shock {wl['beta']:g} deg, "
+                  f"artificial viscosity, CFL {wl['cfl']:g}")
+        wname = (f"swbli{wl['nx']}x{wl['ny']}_P{wl['P']}_Q{wl['Q']}_Ma{wl['Ma']:g}_beta{wl['beta']:g}"
+                 f"_av_k{wl['kappa']:g}_sdirk2_cfl{wl['cfl']:g}")
         data = ("synthetic (the projected oblique-shock field: uniform stream below the shock "
                 "line, Rankine-Hugoniot state above)")
     elif cyl:
@@ -510,6 +516,7 @@ def run_ours(args, rank, world):
                                                              "lift_threads")}
                                      if tuning else "built-in defaults")},
         "newton_per_step": sum(newton) / len(newton),
+        "av_elements": av_elements,
         "gmres_per_step": sum(gm) / len(gm),
         "residual_gdofs": ndof / (res_ms / 1e3) / 1e9,
         "residual_ms": res_ms,
@@ -630,6 +637,10 @@ def main():
                          "workload with artificial viscosity (SDIRK2, 119x39 P=3)")
     ap.add_argument("--cfl", type=float, default=None,
                     help="swbli only: CFL of Eq. CFL (default 100)")
+    ap.add_argument("--shock-angle", type=float, default=None,
+                    help="swbli only: shock angle in degrees (default 30.8)")
+    ap.add_argument("--av-kappa", type=float, default=None,
+                    help="swbli only: half-width of the sensor's ramp in decades (default 1)")
     ap.add_argument("--elems", type=int, default=WORKLOAD["n"],
                     help="elements per direction (16 = the benchmark; smaller only for profiler captures)")
     args = ap.parse_args()

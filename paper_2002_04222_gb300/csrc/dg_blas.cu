@@ -116,11 +116,13 @@ dg_status multi_axpy(double* w, const double* V, int k, const double* h, long lo
   return DG_OK;
 }
 
-__global__ void axpby_kernel(double* __restrict__ y, double a, const double* __restrict__ x,
-                             double b, long long n) {
+// y = a x + b y; with b = 0, y is output only and is not read (a fresh
+// buffer may hold anything, and 0 * NaN is NaN).  x may be y (scaling in
+// place), hence no __restrict__.
+__global__ void axpby_kernel(double* y, double a, const double* x, double b, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
-    y[i] = fma(a, x[i], b * y[i]);
+    y[i] = b == 0.0 ? a * x[i] : fma(a, x[i], b * y[i]);
 }
 dg_status axpby(double* y, double a, const double* x, double b, long long n, cudaStream_t s) {
   DG_PROF(K_VEC, s, axpby_kernel<<<grid_for(n), 256, 0, s>>>(y, a, x, b, n));

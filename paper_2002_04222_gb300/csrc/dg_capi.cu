@@ -429,8 +429,11 @@ dg_status dg_mesh_create(const dg_mesh_desc* md, const dg_physics* ph, void* str
   const size_t nd = (size_t)m->ndof;
   const size_t ntr = (size_t)E * 2 * d * (1 + d) * m->nv * m->nf;
   cudaError_t err = cudaSuccess;
+  // every workspace starts zeroed: no kernel result may depend on what an
+  // earlier allocation left in the memory
   auto alloc = [&](void** ptr, size_t bytes) {
     if (err == cudaSuccess) err = cudaMalloc(ptr, bytes);
+    if (err == cudaSuccess) err = cudaMemsetAsync(*ptr, 0, bytes, s);
   };
   alloc((void**)&m->geo, sizeof(ElemGeo) * E);
   alloc((void**)&m->faces, sizeof(int32_t) * 6 * F);
@@ -569,6 +572,7 @@ static dg_status ensure_krylov(dg_mesh_s* m, int restart) {
   m->krylov = nullptr;
   const size_t nd = (size_t)m->ndof;
   DG_CUDA(cudaMalloc(&m->krylov, sizeof(double) * nd * (2 * (size_t)restart + 1)));
+  DG_CUDA(cudaMemset(m->krylov, 0, sizeof(double) * nd * (2 * (size_t)restart + 1)));
   m->krylov_m = restart;
   return DG_OK;
 }
@@ -871,7 +875,10 @@ static dg_status check_step_cfg(const dg_sdirk_cfg* cfg) {
 // candidate U2, R2, N2
 static dg_status step_buffers(dg_mesh_s* m, double** Ev, double** rest) {
   const size_t n = (size_t)m->ndof;
-  if (!m->stage) DG_CUDA(cudaMalloc(&m->stage, sizeof(double) * n * (DG_MAX_STAGES + 7)));
+  if (!m->stage) {
+    DG_CUDA(cudaMalloc(&m->stage, sizeof(double) * n * (DG_MAX_STAGES + 7)));
+    DG_CUDA(cudaMemset(m->stage, 0, sizeof(double) * n * (DG_MAX_STAGES + 7)));
+  }
   for (int i = 0; i < DG_MAX_STAGES; ++i) Ev[i] = m->stage + i * n;
   for (int i = 0; i < 7; ++i) rest[i] = m->stage + (DG_MAX_STAGES + i) * n;
   return DG_OK;

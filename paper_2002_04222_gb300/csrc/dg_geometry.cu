@@ -320,6 +320,7 @@ dg_status build_general_geometry(dg_mesh_s* m, const double* nodes_host, int g, 
   cudaError_t err = cudaSuccess;
   auto alloc = [&](void** ptr, size_t bytes) {
     if (err == cudaSuccess) err = cudaMalloc(ptr, bytes);
+    if (err == cudaSuccess) err = cudaMemsetAsync(*ptr, 0, bytes, s);
   };
   alloc((void**)&m->vgeo, sizeof(double) * (size_t)E * (D * D + 1) * m->nq);
   alloc((void**)&m->vx, sizeof(double) * (size_t)E * D * m->nq);

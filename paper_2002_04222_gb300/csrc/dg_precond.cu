@@ -481,6 +481,18 @@ __global__ void __launch_bounds__(256) brj_block_kernel(
   auto ftab = [&](int j, int r) -> const T* { return r == j ? sD1 : sB1; };
   auto gtab = [&](int a, int r) -> const T* { return r == a - 1 ? sD1 : sB1; };
   if constexpr (DIM == 3) {
+    // products of the test and trial factors of one direction,
+    // FG[c][q][m + N n] = f(q, m) g(q, n) with f = d if c & 2 else b and
+    // g = d if c & 1 else b: each contraction below is then one FMA per term,
+    // and a thread keeps N outputs in registers per operand it loads
+    T* FG = Y;  // Y is free until the mass-matrix step
+    for (int i = threadIdx.x; i < 4 * Q * N2; i += blockDim.x) {
+      const int c = i / (Q * N2), rem = i % (Q * N2);
+      const int q = rem / N2, mn = rem % N2;
+      const T* f = (c & 2) ? sD1 : sB1;
+      const T* g = (c & 1) ? sD1 : sB1;
+      FG[i] = f[q * N + mn % N] * g[q * N + mn / N];
+    }
     // one pass per factor type of direction 2 (f2, g2 in {b, d}): the (j, a)
     // of that type are contracted over q0 and q1 into T2, then q2 into X
     for (int i = threadIdx.x; i < NM * NM; i += blockDim.x) X[i] = (T)0;
@@ -490,43 +502,68 @@ __global__ void __launch_bounds__(256) brj_block_kernel(
       for (int ja = 0; ja < JA; ++ja) {
         const int j = ja / (DIM + 1), a = ja % (DIM + 1);
         if ((j == 2 ? 2 : 0) + (a == 3 ? 1 : 0) != type) continue;
-        const T* f0 = ftab(j, 0); const T* g0 = gtab(a, 0);
-        const T* f1 = ftab(j, 1); const T* g1 = gtab(a, 1);
+        const T* fg0 = FG + ((j == 0 ? 2 : 0) + (a == 1 ? 1 : 0)) * Q * N2;
+        const T* fg1 = FG + ((j == 1 ? 2 : 0) + (a == 2 ? 1 : 0)) * Q * N2;
         const T* w = sW + ja * NQ;
-        // contract q0: T1[(m0 + N n0)][q1 + Q q2]
-        for (int i = threadIdx.x; i < N2 * Q * Q; i += blockDim.x) {
-          const int mn = i / (Q * Q), qq = i % (Q * Q);
-          const int m0 = mn % N, n0 = mn / N;
-          T acc = (T)0;
+        // contract q0: T1[(m0 + N n0)][q1 + Q q2], a thread per (q1 q2, n0), m0 in registers
+        for (int i = threadIdx.x; i < Q * Q * N; i += blockDim.x) {
+          const int qq = i % (Q * Q), n0 = i / (Q * Q);
+          T acc[N];
 #pragma unroll
-          for (int q0 = 0; q0 < Q; ++q0) acc += f0[q0 * N + m0] * g0[q0 * N + n0] * w[q0 + Q * qq];
-          T1[i] = acc;
+          for (int m0 = 0; m0 < N; ++m0) acc[m0] = (T)0;
+#pragma unroll
+          for (int q0 = 0; q0 < Q; ++q0) {
+            const T wv = w[q0 + Q * qq];
+            const T* fr = fg0 + q0 * N2 + N * n0;
+#pragma unroll
+            for (int m0 = 0; m0 < N; ++m0) acc[m0] += fr[m0] * wv;
+          }
+#pragma unroll
+          for (int m0 = 0; m0 < N; ++m0) T1[(m0 + N * n0) * Q * Q + qq] = acc[m0];
         }
         __syncthreads();
-        // contract q1: T2[((m0 + N n0) N2 + m1 + N n1) Q + q2] +=
-        for (int i = threadIdx.x; i < N2 * N2 * Q; i += blockDim.x) {
+        // contract q1: T2[((m0 + N n0) N2 + m1 + N n1) Q + q2] +=, a thread per
+        // (mn0, q2, n1), m1 in registers
+        for (int i = threadIdx.x; i < N2 * Q * N; i += blockDim.x) {
           const int q2 = i % Q, r = i / Q;
-          const int m1 = r % N, n1 = (r / N) % N, mn0 = r / N2;
-          T acc = (T)0;
+          const int n1 = r % N, mn0 = r / N;
+          T acc[N];
 #pragma unroll
-          for (int q1 = 0; q1 < Q; ++q1)
-            acc += f1[q1 * N + m1] * g1[q1 * N + n1] * T1[mn0 * Q * Q + q1 + Q * q2];
-          T2[i] += acc;
+          for (int m1 = 0; m1 < N; ++m1) acc[m1] = (T)0;
+#pragma unroll
+          for (int q1 = 0; q1 < Q; ++q1) {
+            const T tv = T1[mn0 * Q * Q + q1 + Q * q2];
+            const T* fr = fg1 + q1 * N2 + N * n1;
+#pragma unroll
+            for (int m1 = 0; m1 < N; ++m1) acc[m1] += fr[m1] * tv;
+          }
+#pragma unroll
+          for (int m1 = 0; m1 < N; ++m1) T2[(mn0 * N2 + m1 + N * n1) * Q + q2] += acc[m1];
         }
         __syncthreads();
       }
-      // contract q2 into X[n][m]
-      const T* f2 = (type & 2) ? sD1 : sB1;
-      const T* g2 = (type & 1) ? sD1 : sB1;
-      for (int i = threadIdx.x; i < NM * NM; i += blockDim.x) {
-        const int n = i / NM, m = i % NM;
-        const int m0 = m % N, m1 = (m / N) % N, m2 = m / N2;
-        const int n0 = n % N, n1 = (n / N) % N, n2 = n / N2;
-        const T* t2 = T2 + ((m0 + N * n0) * N2 + m1 + N * n1) * Q;
-        T acc = (T)0;
+      // contract q2 into X[n][m], a thread per (m0, m1, n0, n1, n2) (m0, m1
+      // fastest: neighbouring threads touch neighbouring rows of X), m2 in
+      // registers
+      const T* fg2 = FG + type * Q * N2;
+      for (int i = threadIdx.x; i < N2 * N2 * N; i += blockDim.x) {
+        const int m0 = i % N, m1 = (i / N) % N, n0 = (i / N2) % N, n1 = (i / (N2 * N)) % N;
+        const int n2 = i / (N2 * N2);
+        const int mn0 = m0 + N * n0, mn1 = m1 + N * n1;
+        const T* t2 = T2 + (mn0 * N2 + mn1) * Q;
+        T acc[N];
 #pragma unroll
-        for (int q2 = 0; q2 < Q; ++q2) acc += f2[q2 * N + m2] * g2[q2 * N + n2] * t2[q2];
-        X[i] += acc;
+        for (int m2 = 0; m2 < N; ++m2) acc[m2] = (T)0;
+#pragma unroll
+        for (int q2 = 0; q2 < Q; ++q2) {
+          const T tv = t2[q2];
+          const T* fr = fg2 + q2 * N2 + N * n2;
+#pragma unroll
+          for (int m2 = 0; m2 < N; ++m2) acc[m2] += fr[m2] * tv;
+        }
+        const int n = n0 + N * (n1 + N * n2);
+#pragma unroll
+        for (int m2 = 0; m2 < N; ++m2) X[n * NM + m0 + N * (m1 + N * m2)] += acc[m2];
       }
       __syncthreads();
     }
@@ -1456,8 +1493,10 @@ dg_status dg_precond_build(dg_mesh_t m, const double* u, double t, double dt_a,
     const size_t stage = cfg->precision == DG_PREC_BF16 ? sizeof(float) * (size_t)E * nb * ld : 0;
     p->work_bytes = stage + per * ch;
     cudaError_t err = cudaSuccess;
+    // zeroed workspaces (the blocks' padding columns included)
     auto alloc = [&](void** ptr, size_t bytes) {
       if (err == cudaSuccess) err = cudaMalloc(ptr, bytes);
+      if (err == cudaSuccess) err = cudaMemset(*ptr, 0, bytes);
     };
     alloc(&p->blocks, bsz * (size_t)E * nb * ld);
     alloc(&p->jd, vb * njac);
@@ -1509,7 +1548,10 @@ dg_status dg_precond_build(dg_mesh_t m, const double* u, double t, double dt_a,
   if (p->gen == 0 || p->J != cfg->J || p->omega != cfg->omega || p->dt_a != dt_a ||
       p->fused != (cfg->fused != 0))
     p->gen = __atomic_add_fetch(&g_gen, 1ULL, __ATOMIC_RELAXED);
-  if (cfg->fused && !p->qh2) DG_CUDA(cudaMalloc((void**)&p->qh2, sizeof(double) * (size_t)m->ndof));
+  if (cfg->fused && !p->qh2) {
+    DG_CUDA(cudaMalloc((void**)&p->qh2, sizeof(double) * (size_t)m->ndof));
+    DG_CUDA(cudaMemset(p->qh2, 0, sizeof(double) * (size_t)m->ndof));
+  }
   p->fused = cfg->fused != 0;
   p->use_graphs = cfg->graphs;
   p->tc_invert = cfg->tc_invert;

@@ -30,6 +30,7 @@ max(1e-12, 16 s) ||R|| + max(1e-12, 16 s_av) ||dR||;
 JFNK product by the residual difference at u + eps v over eps; BRJ apply
 1e-6 (FP64 blocks); SDIRK with equal Newton and GMRES counts and u^{n+1} to
 1e-9."""
+import copy
 import itertools
 
 import numpy as np
@@ -161,8 +162,9 @@ def test_residual_parity_with_artificial_viscosity(dgl, name, parity_record):
     m = dgl.Mesh.from_case(c)
     R_ref = dg.residual(u, 0.0)
     R = m.residual(to_dev(u)).cpu().numpy()
-    c.phys.av = 0
-    dg0 = DG(c.mesh, c.P, c.Q, c.phys)
+    ph0 = copy.copy(c.phys)                    # dg keeps c.phys: change a copy
+    ph0.av = 0
+    dg0 = DG(c.mesh, c.P, c.Q, ph0)
     R_plain = dg0.residual(u, 0.0)
     dR = R_ref - R_plain                       # the artificial-viscosity contribution
     rng = np.random.default_rng(123)
@@ -180,6 +182,7 @@ def test_residual_parity_with_artificial_viscosity(dgl, name, parity_record):
     parity_record("residual_av", name, "||R_gpu-R_or||/||R_or||", rel(R, R_ref), tol, floor_s=s,
                   floor_s_av=s_av, av_effect=rel(R_plain, R_ref))
     assert rel(R_plain, R_ref) > 1e-6          # the test is not vacuous
+    assert s < 1e-10 and s_av < 1e-10          # floors of FP64 evaluations
     assert rel(R, R_ref) < tol, (rel(R, R_ref), tol)
 
 
@@ -214,8 +217,9 @@ def test_brj_apply_parity_with_frozen_artificial_viscosity(dgl, name, full, pari
     ref = ref_pc.apply(q)
     pc = dgl.Precond(m).build(to_dev(u), 0.0, dt_a, J=7, full_jacobian=full)
     got = pc.apply(to_dev(q)).cpu().numpy()
-    c.phys.av = 0
-    plain = im.BRJ(DG(c.mesh, c.P, c.Q, c.phys), u, 0.0, dt_a, J=7, full=full).apply(q)
+    ph0 = copy.copy(c.phys)
+    ph0.av = 0
+    plain = im.BRJ(DG(c.mesh, c.P, c.Q, ph0), u, 0.0, dt_a, J=7, full=full).apply(q)
     parity_record("brj_apply_av", f"{name}{'_full' if full else ''}",
                   "||P^-1q_gpu-P^-1q_or||/||P^-1q_or||", rel(got, ref), 1e-6,
                   av_effect=rel(plain, ref))
