@@ -9,6 +9,9 @@
 
 namespace dg {
 
+// columns of each chunk of the block prefetched to L2 at the start of a sweep
+constexpr int SWEEP_PREFETCH_COLS = 8;
+
 // One whole relaxation sweep per element (Eq. precond-Jacobi, j >= 2):
 // y_e = q_e - (L+U)_e qprev is formed in shared memory by the off-diagonal
 // product and multiplied by the block in the same block of threads, so y never
@@ -27,6 +30,16 @@ __global__ void DG_DIAG_BOUNDS(TB)
   TA* sy = reinterpret_cast<TA*>(smraw);                 // [nb]
   TA* part = sy + nb;                                    // [split][ld]
   const int e = blockIdx.x;
+  // the block's first columns of each thread group's chunk start their way
+  // from DRAM while the off-diagonal gather runs (a bounded share of the
+  // block, so that the prefetches of the resident blocks fit in L2)
+  if (threadIdx.x >= 32 && threadIdx.x < 32 + split) {
+    const int chunk = (nb + split - 1) / split;
+    const int c0 = (threadIdx.x - 32) * chunk;
+    const int nc = min(SWEEP_PREFETCH_COLS, min(chunk, nb - c0));
+    if (nc > 0)
+      prefetch_l2(blocks + (long long)e * nb * ld + (long long)c0 * ld, sizeof(TB) * (size_t)nc * ld);
+  }
   offdiag_element<DIM, P, Q, TA, TJ, CV, NTH>(tab, geo, minv, Jo, nbr, qprev, q, dta, e,
                                               [&](int i, double v) { sy[i] = (TA)v; });
   __syncthreads();

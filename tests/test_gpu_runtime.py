@@ -266,3 +266,30 @@ def test_fused_sweeps_sdirk_bitwise(dgl):
         res.append((u, stats))
     assert res[0][1] == res[1][1]
     assert torch.equal(res[0][0], res[1][0])
+
+
+def test_results_do_not_depend_on_earlier_allocations(dgl):
+    """Two SDIRK2 steps on a fresh mesh and preconditioner give the same bits
+    whether the device memory they get was never used or held NaNs just
+    before (a 1 GiB NaN-filled tensor freed back to the driver): no kernel may
+    read a workspace before writing it (0 * NaN is NaN)."""
+    c = w.vortex_case(n=8, P=2)
+    runs = []
+    for poison in (False, True):
+        if poison:
+            junk = torch.full((1 << 27,), float("nan"), dtype=torch.float64, device="cuda")
+            torch.cuda.synchronize()
+            del junk
+            torch.cuda.empty_cache()
+        m = dgl.Mesh.from_case(c)
+        u = m.project()
+        pc = dgl.Precond(m)
+        for k in range(2):
+            st = m.sdirk_step(u, 0.02 * k, 0.02, precond=pc, rebuild=(k == 0), restart=20, J=7,
+                              precision="fp32", fused=True)
+            assert st["converged"]
+        runs.append(u.clone())
+        pc.close()
+        m.close()
+    assert torch.isfinite(runs[1]).all()
+    assert torch.equal(runs[0], runs[1])
