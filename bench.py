@@ -52,7 +52,8 @@ SAMPLE_N = 3          # CPU sample: the same case on 3^3 elements (same P, Q, CF
 FREEZE = 10
 # DRAM bytes (read + write) per element and launch from one ncu capture of the
 # kernel as it stands (profiles/); a kernel changed since then has no entry
-TRAFFIC_PER_ELEM = {("brj_diag", "fp32", 3, 6): 418_400.0, ("brj_diag", "bf16", 3, 6): 209_770.0}
+TRAFFIC_PER_ELEM = {("brj_diag", "fp32", 3, 6): 418_400.0, ("brj_diag", "bf16", 3, 6): 209_770.0,
+                    ("brj_sweep", "fp32", 3, 6): 439_400.0}
 
 
 def max_over_ranks(x, world, device="cuda"):

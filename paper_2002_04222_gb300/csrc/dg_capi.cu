@@ -220,7 +220,7 @@ static void build_tables(int P, int Q, Tables& t) {
 // Modal sensor table: the Legendre coefficients of the modified basis,
 // T[a][k] = (2a+1)/2 sum_q w_q L_a(x_q) psi_k(x_q) (the Gauss rule is exact,
 // the product has degree <= 2P <= 2Q-1), and |L_a|^2 = 2/(2a+1).
-static void build_sensor_table(int P, const Tables& t, SensorTab& st) {
+static void build_sensor_table(int P, double kappa, const Tables& t, SensorTab& st) {
   std::memset(&st, 0, sizeof(st));
   const int n = P + 1;
   for (int q = 0; q < t.q; ++q) {
@@ -232,6 +232,9 @@ static void build_sensor_table(int P, const Tables& t, SensorTab& st) {
       for (int k = 0; k < n; ++k) st.T[a * n + k] += 0.5 * (2 * a + 1) * t.w[q] * L[a] * t.B[q * n + k];
   }
   for (int a = 0; a < n; ++a) st.nrm[a] = 2.0 / (2 * a + 1);
+  const double p4 = 1.0 / ((double)P * P * P * P);
+  st.lo = p4 * std::pow(10.0, -kappa);
+  st.hi = p4 * std::pow(10.0, kappa);
 }
 
 void drop_arnoldi_graphs(dg_mesh_s* m) {
@@ -452,7 +455,7 @@ dg_status dg_mesh_create(const dg_mesh_desc* md, const dg_physics* ph, void* str
     p.avf = m->avf;
     p.av_mu0 = ph->av_mu0;
     p.av_kappa = ph->av_kappa;
-    build_sensor_table(md->P, m->tab, m->stab);
+    build_sensor_table(md->P, ph->av_kappa, m->tab, m->stab);
   }
   if (err != cudaSuccess) {
     free_mesh(m);

@@ -39,9 +39,11 @@ struct Phys {
 
 // Modified-basis-to-Legendre transform of one direction for the modal sensor:
 // T[a*n + k] = Legendre coefficient a of psi_k, nrm[a] = |L_a|^2 = 2/(2a+1).
+// lo, hi: the ramp's ends as energy ratios, 10^(s0 -+ kappa) with s0 = log10(P^-4).
 struct SensorTab {
   double T[NMAX * NMAX];
   double nrm[NMAX];
+  double lo, hi;
 };
 
 // Element geometry of an axis-aligned affine element: origin and edge lengths.

@@ -705,7 +705,9 @@ template <int D, int R>
 __device__ inline void roe_flux_axis(const double* UL, const double* UR, double sgn,
                                      const Phys& ph, double* Fh) {
   constexpr int NV = D + 2;
-  const double iL = 1.0 / UL[0], iR = 1.0 / UR[0];
+  // 1/rho and sqrt(rho) of both sides from one reciprocal square root each
+  const double rsL = rsqrt(UL[0]), rsR = rsqrt(UR[0]);
+  const double iL = rsL * rsL, iR = rsR * rsR;
   double vL[D], vR[D], keL = 0.0, keR = 0.0;
 #pragma unroll
   for (int k = 0; k < D; ++k) {
@@ -729,7 +731,7 @@ __device__ inline void roe_flux_axis(const double* UL, const double* UR, double 
   FL[D + 1] = (UL[D + 1] + pL) * unL;
   FR[D + 1] = (UR[D + 1] + pR) * unR;
   const double HL = (UL[D + 1] + pL) * iL, HR = (UR[D + 1] + pR) * iR;
-  const double sL = sqrt(UL[0]), sR = sqrt(UR[0]);
+  const double sL = UL[0] * rsL, sR = UR[0] * rsR;
   const double rt = sL * sR;
   const double isum = 1.0 / (sL + sR);
   double ut[D], du[D], q2 = 0.0, udu = 0.0;
@@ -743,8 +745,8 @@ __device__ inline void roe_flux_axis(const double* UL, const double* UR, double 
   const double unt = sgn * ut[R], dun = sgn * du[R];
   const double Ht = (sL * HL + sR * HR) * isum;
   const double c2 = ph.gm1 * (Ht - 0.5 * q2);
-  const double c = sqrt(c2);
-  const double ic2 = 1.0 / c2;
+  const double rc = rsqrt(c2);
+  const double c = c2 * rc, ic2 = rc * rc;
   const double dp = pR - pL;
   const double a1 = (dp - rt * c * dun) * 0.5 * ic2;
   const double a5 = (dp + rt * c * dun) * 0.5 * ic2;

@@ -22,6 +22,105 @@
 
 namespace dg {
 
+// ---------------------------------------------------------------- shock sensor
+// Artificial-viscosity factor f_e = mu_0 S_e h_e / P of element e (Sec. 3.1.2),
+// by one warp: the density's modified-basis coefficients (in A, overwritten;
+// B is scratch of the same size) go to Legendre coefficients c by the 1-D
+// transform along each direction; the reference-element L2 norms are then
+// sums of c^2 times the Legendre norms, and the part removed by the
+// projection onto degree <= P-1 per direction is the set of modes with some
+// index equal to P.  Lane 0 writes avf[e].
+template <int DIM, int P, int Q, bool CV>
+__device__ void sensor_element(const SensorTab& st, const Phys& ph,
+                               const ElemGeo* __restrict__ geo, const GenGeo& gg, int e,
+                               double* A, double* B, int lane, double* __restrict__ avf) {
+  using C = Cfg<DIM, P, Q>;
+  constexpr int N = C::N, NM = C::NM, NQ = C::NQ;
+  double* src = A;
+  double* dst = B;
+  int stride = 1;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    for (int mm = lane; mm < NM; mm += 32) {
+      const int id = (mm / stride) % N;
+      const int m0 = mm - id * stride;
+      double a = 0.0;
+#pragma unroll
+      for (int k = 0; k < N; ++k) a = fma(st.T[id * N + k], src[m0 + k * stride], a);
+      dst[mm] = a;
+    }
+    __syncwarp();
+    double* tmp = src;
+    src = dst;
+    dst = tmp;
+    stride *= N;
+  }
+  double num = 0.0, den = 0.0, vol = 0.0;
+  for (int mm = lane; mm < NM; mm += 32) {
+    int r = mm;
+    double wgt = 1.0;
+    bool top = false;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      const int id = r % N;
+      r /= N;
+      wgt *= st.nrm[id];
+      top = top || id == P;
+    }
+    const double c2 = src[mm] * src[mm] * wgt;
+    den += c2;
+    if (top) num += c2;
+  }
+  if constexpr (CV) {
+    const double* wj = gg.vgeo + (long long)e * (DIM * DIM + 1) * NQ + DIM * DIM * NQ;
+    for (int q = lane; q < NQ; q += 32) vol += wj[q];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    num += __shfl_xor_sync(0xffffffffu, num, o);
+    den += __shfl_xor_sync(0xffffffffu, den, o);
+    vol += __shfl_xor_sync(0xffffffffu, vol, o);
+  }
+  if (lane != 0) return;
+  // below the ramp (the common case) no logarithm, sine or root is taken
+  double S = 0.0;
+  if (num > 0.0 && den > 0.0 && num >= st.lo * den) {
+    if (num > st.hi * den) {
+      S = 1.0;
+    } else {
+      const double se = log10(num / den), s0 = -4.0 * log10((double)P), kap = ph.av_kappa;
+      S = 0.5 * (1.0 + sin(3.14159265358979323846 * (se - s0) / (2.0 * kap)));
+    }
+  }
+  if (S == 0.0) {
+    avf[e] = 0.0;
+    return;
+  }
+  if constexpr (!CV) vol = geo[e].detJ * (double)(1 << DIM);
+  const double h = DIM == 2 ? sqrt(vol) : cbrt(vol);
+  avf[e] = ph.av_mu0 * S * h / (double)P;
+}
+
+// The factor of every element at u alone (dg_av_factor); the residual
+// computes it inside the volume kernel.  One warp per element.
+constexpr int SENSOR_WARPS = 8;
+template <int DIM, int P, int Q, bool CV>
+__global__ void __launch_bounds__(32 * SENSOR_WARPS) sensor_kernel(
+    const __grid_constant__ SensorTab st, const __grid_constant__ Phys ph,
+    const ElemGeo* __restrict__ geo, const __grid_constant__ GenGeo gg, int E,
+    const double* __restrict__ u, double* __restrict__ avf) {
+  using C = Cfg<DIM, P, Q>;
+  constexpr int NV = C::NV, NM = C::NM;
+  __shared__ double sA[SENSOR_WARPS][NM], sC[SENSOR_WARPS][NM];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int e = blockIdx.x * SENSOR_WARPS + w;
+  if (e >= E) return;  // warp-uniform; the kernel has no block-wide barrier
+  const long long base = (long long)e * NV * NM;  // variable 0: density
+  for (int k = lane; k < NM; k += 32) sA[w][k] = u[base + k];
+  __syncwarp();
+  sensor_element<DIM, P, Q, CV>(st, ph, geo, gg, e, sA[w], sC[w], lane, avf);
+}
+
 // ---------------------------------------------------------------- kernel 1
 template <int DIM, int P, int Q, bool CV>
 __global__ void __launch_bounds__(256) vol_kernel(const __grid_constant__ Tables tab,
@@ -32,7 +131,9 @@ __global__ void __launch_bounds__(256) vol_kernel(const __grid_constant__ Tables
                                                   const double* __restrict__ v,
                                                   const double* __restrict__ epsp,
                                                   double* __restrict__ hbuf,
-                                                  double* __restrict__ tbuf, const int EPB) {
+                                                  double* __restrict__ tbuf, const int EPB,
+                                                  const __grid_constant__ SensorTab st,
+                                                  double* __restrict__ avf_out) {
   using C = Cfg<DIM, P, Q>;
   constexpr int N = C::N, NV = C::NV, NM = C::NM, NQ = C::NQ, NF = C::NF;
   constexpr int Q2 = C::Q2, N2 = C::N2;
@@ -61,6 +162,22 @@ __global__ void __launch_bounds__(256) vol_kernel(const __grid_constant__ Tables
     sU[i] = val;
   }
   __syncthreads();
+  if (avf_out) {
+    // shock capturing: the factor of each element at the evaluated state, one
+    // warp per element, the density coefficients copied to scratch in sQ
+    // (free until BwdTrans); the volume flux below and the face kernel read it
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int eb = wp; eb < EPB; eb += nw) {
+      if (e0 + eb >= E) continue;  // warp-uniform
+      double* A = sQ + (long long)eb * NV * NQ;
+      double* Bs = A + NM;
+      for (int k = lane; k < NM; k += 32) A[k] = sU[eb * NV * NM + k];
+      __syncwarp();
+      sensor_element<DIM, P, Q, CV>(st, ph, geo, gg, e0 + eb, A, Bs, lane, avf_out);
+      __syncwarp();
+    }
+    __syncthreads();
+  }
   // BwdTrans: contract direction 0, 1 (, 2) with B
   if (DIM == 2) {
     contract<N, N, 1, 0, Q, N, 1, false>(sU, sT, sB, nrep);
@@ -655,94 +772,6 @@ __global__ void __launch_bounds__(256) project_kernel(const __grid_constant__ Ta
   }
 }
 
-// ---------------------------------------------------------------- shock sensor
-// Artificial-viscosity factor f_e = mu_0 S_e h_e / P of every element at the
-// state u (+ eps v) (Sec. 3.1.2).  One warp per element: the density's
-// modified-basis coefficients go to Legendre coefficients c by the 1-D
-// transform along each direction; the reference-element L2 norms are then
-// sums of c^2 times the Legendre norms, and the part removed by the
-// projection onto degree <= P-1 per direction is the set of modes with some
-// index equal to P.
-constexpr int SENSOR_WARPS = 8;
-template <int DIM, int P, int Q, bool CV>
-__global__ void __launch_bounds__(32 * SENSOR_WARPS) sensor_kernel(
-    const __grid_constant__ SensorTab st, const __grid_constant__ Phys ph,
-    const ElemGeo* __restrict__ geo, const __grid_constant__ GenGeo gg, int E,
-    const double* __restrict__ u, const double* __restrict__ v, const double* __restrict__ epsp,
-    double* __restrict__ avf) {
-  using C = Cfg<DIM, P, Q>;
-  constexpr int N = C::N, NV = C::NV, NM = C::NM, NQ = C::NQ;
-  __shared__ double sA[SENSOR_WARPS][NM], sC[SENSOR_WARPS][NM];
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int e = blockIdx.x * SENSOR_WARPS + w;
-  if (e >= E) return;  // warp-uniform; the kernel has no block-wide barrier
-  const double eps = v ? epsp[0] : 0.0;
-  const long long base = (long long)e * NV * NM;  // variable 0: density
-  for (int k = lane; k < NM; k += 32) {
-    double val = u[base + k];
-    if (v) val = fma(eps, v[base + k], val);
-    sA[w][k] = val;
-  }
-  __syncwarp();
-  double* src = sA[w];
-  double* dst = sC[w];
-  int stride = 1;
-#pragma unroll
-  for (int d = 0; d < DIM; ++d) {
-    for (int mm = lane; mm < NM; mm += 32) {
-      const int id = (mm / stride) % N;
-      const int m0 = mm - id * stride;
-      double a = 0.0;
-#pragma unroll
-      for (int k = 0; k < N; ++k) a = fma(st.T[id * N + k], src[m0 + k * stride], a);
-      dst[mm] = a;
-    }
-    __syncwarp();
-    double* tmp = src;
-    src = dst;
-    dst = tmp;
-    stride *= N;
-  }
-  double num = 0.0, den = 0.0, vol = 0.0;
-  for (int mm = lane; mm < NM; mm += 32) {
-    int r = mm;
-    double wgt = 1.0;
-    bool top = false;
-#pragma unroll
-    for (int d = 0; d < DIM; ++d) {
-      const int id = r % N;
-      r /= N;
-      wgt *= st.nrm[id];
-      top = top || id == P;
-    }
-    const double c2 = src[mm] * src[mm] * wgt;
-    den += c2;
-    if (top) num += c2;
-  }
-  if constexpr (CV) {
-    const double* wj = gg.vgeo + (long long)e * (DIM * DIM + 1) * NQ + DIM * DIM * NQ;
-    for (int q = lane; q < NQ; q += 32) vol += wj[q];
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    num += __shfl_xor_sync(0xffffffffu, num, o);
-    den += __shfl_xor_sync(0xffffffffu, den, o);
-    vol += __shfl_xor_sync(0xffffffffu, vol, o);
-  }
-  if (lane != 0) return;
-  if constexpr (!CV) vol = geo[e].detJ * (double)(1 << DIM);
-  const double h = DIM == 2 ? sqrt(vol) : cbrt(vol);
-  double S = 0.0;
-  if (num > 0.0 && den > 0.0) {
-    const double se = log10(num / den), s0 = -4.0 * log10((double)P), kap = ph.av_kappa;
-    if (se > s0 + kap)
-      S = 1.0;
-    else if (se >= s0 - kap)
-      S = 0.5 * (1.0 + sin(3.14159265358979323846 * (se - s0) / (2.0 * kap)));
-  }
-  avf[e] = ph.av_mu0 * S * h / (double)P;
-}
-
 // ---------------------------------------------------------------- launchers
 template <int DIM, int P, int Q, bool CV>
 static dg_status run_residual_g(dg_mesh_s* m, const EvalArgs& a, cudaStream_t s) {
@@ -756,14 +785,11 @@ static dg_status run_residual_g(dg_mesh_s* m, const EvalArgs& a, cudaStream_t s)
   DG_CUDA(cudaFuncSetAttribute(lift_kernel<DIM, P, Q, CV>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm));
   if (!a.skip_vol) {
-    if (m->phys.avf) {
-      DG_PROF(K_SENSOR, s, sensor_kernel<DIM, P, Q, CV><<<(m->E + SENSOR_WARPS - 1) / SENSOR_WARPS,
-                                                          32 * SENSOR_WARPS, 0, s>>>(
-          m->stab, m->phys, m->geo, gg, m->E, a.u, a.v, a.eps, m->avf));
-      DG_LAUNCHED(1);
-    }
+    // (with shock capturing the volume kernel also writes the elements'
+    // artificial-viscosity factors, which the face kernel reads)
     DG_PROF(K_VOL, s, vol_kernel<DIM, P, Q, CV><<<(m->E + vepb - 1) / vepb, vnt, vsm, s>>>(
-        m->tab, m->phys, m->geo, gg, m->E, a.u, a.v, a.eps, m->hbuf, m->tbuf, vepb));
+        m->tab, m->phys, m->geo, gg, m->E, a.u, a.v, a.eps, m->hbuf, m->tbuf, vepb, m->stab,
+        m->phys.avf ? m->avf : nullptr));
     DG_LAUNCHED(1);
     const int nfp = m->F * C::NF;
     if constexpr (CV) {
@@ -875,14 +901,14 @@ static dg_status run_sensor(dg_mesh_s* m, const double* u, double* out, cudaStre
   if (m->curved) {
     if constexpr (has_curved<DIM, P, Q>()) {
       DG_PROF(K_SENSOR, s, sensor_kernel<DIM, P, Q, true><<<nb, 32 * SENSOR_WARPS, 0, s>>>(
-          m->stab, m->phys, m->geo, gg, m->E, u, nullptr, nullptr, out));
+          m->stab, m->phys, m->geo, gg, m->E, u, out));
       DG_LAUNCHED(1);
       return DG_OK;
     }
     return DG_ERR_UNSUPPORTED;
   }
   DG_PROF(K_SENSOR, s, sensor_kernel<DIM, P, Q, false><<<nb, 32 * SENSOR_WARPS, 0, s>>>(
-      m->stab, m->phys, m->geo, gg, m->E, u, nullptr, nullptr, out));
+      m->stab, m->phys, m->geo, gg, m->E, u, out));
   DG_LAUNCHED(1);
   return DG_OK;
 }

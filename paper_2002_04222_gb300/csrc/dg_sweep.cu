@@ -10,7 +10,7 @@
 namespace dg {
 
 // columns of each chunk of the block prefetched to L2 at the start of a sweep
-constexpr int SWEEP_PREFETCH_COLS = 8;
+constexpr int SWEEP_PREFETCH_COLS = 16;
 
 // One whole relaxation sweep per element (Eq. precond-Jacobi, j >= 2):
 // y_e = q_e - (L+U)_e qprev is formed in shared memory by the off-diagonal
