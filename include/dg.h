@@ -19,7 +19,7 @@
  *    returning (their statistics are host values).
  *  - Errors: a dg_status is returned, nothing is thrown across the ABI.
  *    DG_ERR_ARG for invalid arguments, DG_ERR_UNSUPPORTED for a
- *    (dim, P, Q) or feature this build does not provide, DG_ERR_CUDA for a
+ *    (dim, P, Q) or feature the compiled library does not provide, DG_ERR_CUDA for a
  *    CUDA failure (sticky errors included), DG_ERR_OOM when device memory
  *    runs out, DG_ERR_NONFINITE when a norm is not finite,
  *    DG_ERR_NOT_CONVERGED when an iteration cap is hit (stats are filled and
@@ -129,8 +129,13 @@ typedef struct {
    * each volume point, h_e = |element|^(1/dim); on a face the mean of the
    * two sides' values from their traces (the interior side's on a boundary).
    * The residual recomputes S_e from its argument on every call; the BRJ
-   * preconditioner holds mu_av at its linearisation state.  av = 0 leaves
-   * the model unchanged. */
+   * preconditioner holds mu_av at its linearisation state.  av = 2 also
+   * multiplies mu_av at each point by Ducros' sensor
+   * (div u)^2 / ((div u)^2 + |curl u|^2 + 1e-6) of the point's velocity
+   * gradient (on a face: the face-average gradient at the mean trace state,
+   * the interior trace on a boundary), which keeps the viscosity out of
+   * vortical regions; dg_precond_build refuses full_jacobian with it.  av = 0
+   * leaves the model unchanged. */
   int av;
   double av_mu0, av_kappa;
 } dg_physics;

@@ -161,13 +161,28 @@ class DG:
             return np.zeros(self.E)
         return self.ph.av_mu0 * self.sensor(u) * self.h_elem / self.P
 
-    def face_av(self, g, fac, QL, QR):
+    def face_av(self, g, fac, QL, QR, dQa):
         """Artificial viscosity at the face points: the mean of the two sides'
-        values from their own traces (a boundary face: the interior side's)."""
+        values from their own traces (a boundary face: the interior side's);
+        with av = 2 times Ducros' sensor of the face-average gradient dQa at the
+        mean trace state (a boundary face: the interior trace)."""
         aL = phy.artificial_viscosity(QL, fac[g["eL"]][:, None], self.ph)
         if g["bctype"] is None:
-            return 0.5 * (aL + phy.artificial_viscosity(QR, fac[g["eR"]][:, None], self.ph))
-        return aL
+            a = 0.5 * (aL + phy.artificial_viscosity(QR, fac[g["eR"]][:, None], self.ph))
+            Qm = 0.5 * (QL + QR)
+        else:
+            a, Qm = aL, QL
+        if getattr(self.ph, "av", 0) == 2:
+            a = a * phy.ducros(Qm, dQa, self.ph)
+        return a
+
+    def volume_av(self, fac, Qv, dQ):
+        """Artificial viscosity at the volume points (av = 2: times Ducros'
+        sensor of the point's gradient)."""
+        a = phy.artificial_viscosity(Qv, fac[:, None], self.ph)
+        if getattr(self.ph, "av", 0) == 2:
+            a = a * phy.ducros(Qv, dQ, self.ph)
+        return a
 
     def face_flux(self, g, QL, QR, Qa, dQa, t, mu_av=None):
         """Numerical normal flux H^n = F^n - G^n and symmetric fluxes S_j on the
@@ -203,13 +218,13 @@ class DG:
         fac = self.av_factor(u) if av else None
         H = phy.euler_flux(Qv, ph)
         if ph.viscous:
-            mu_q = phy.artificial_viscosity(Qv, fac[:, None], ph) if av else None
+            mu_q = self.volume_av(fac, Qv, dQ) if av else None
             H = H - phy.viscous_flux(Qv, dQ, ph, mu_q)
         Ht = np.einsum("eqrj,eqjv->eqrv", self.ginv, H) * self.wJ[:, :, None, None]
         L = sum(np.einsum("qm,eqv->evm", self.D[r], Ht[:, :, r]) for r in range(self.dim))
         for g in (self.groups if faces else []):
             QL, QR, Qa, dQa, _, _ = self.face_states(g, u, t)
-            mu_f = self.face_av(g, fac, QL, QR) if av else None
+            mu_f = self.face_av(g, fac, QL, QR, dQa) if av else None
             Hh, S = self.face_flux(g, QL, QR, Qa, dQa, t, mu_f)
             wJ = g["wJ"]
             L[g["eL"]] -= np.einsum("pm,fpv->fvm", self.Bf[g["fL"]], Hh * wJ[..., None])

@@ -210,8 +210,7 @@ class BRJ:
         d, nv, nm, E = dg.dim, dg.nv, dg.nm, dg.E
         Qv = dg.values(u, dg.B)
         dQ = dg.gradients(u, dg.D, dg.ginv)
-        mu_q = (phy.artificial_viscosity(Qv, self.fac[:, None], ph)
-                if getattr(self, "av", 0) else None)
+        mu_q = dg.volume_av(self.fac, Qv, dQ) if getattr(self, "av", 0) else None
         h = 1e-30
         # A0[e,q,j,k,l] = dH_jk/dQ_l at fixed grad Q (complex step)
         A0 = np.zeros(Qv.shape[:2] + (d, nv, nv))
@@ -272,7 +271,7 @@ class BRJ:
         dg, ph = self.dg, self.dg.ph
         d, nv, nb = dg.dim, dg.nv, self.nb
         QL, QR, Qa, dQa, _, _ = dg.face_states(g, u, t)
-        mu_f = dg.face_av(g, self.fac, QL, QR) if self.av else None
+        mu_f = dg.face_av(g, self.fac, QL, QR, dQa) if self.av else None
         n, wJ = g["n"], g["wJ"]
         interior = g["bctype"] is None
         c_grad = 0.5 if interior else 1.0
@@ -327,7 +326,7 @@ class BRJ:
         dg = self.dg
         nv = dg.nv
         QL, QR, Qa, dQa, _, _ = dg.face_states(g, u, t)
-        mu_f = dg.face_av(g, self.fac, QL, QR) if self.av else None
+        mu_f = dg.face_av(g, self.fac, QL, QR, dQa) if self.av else None
         H0 = self._flux_only(g, QL, QR, dQa, t, mu_f)
         JL = np.zeros(QL.shape + (nv,))
         JR = np.zeros(QL.shape + (nv,))

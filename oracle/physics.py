@@ -62,6 +62,28 @@ def artificial_viscosity(U, factor, ph):
     return factor * rho * (c + np.sqrt(np.sum(vel * vel, axis=-1)))
 
 
+DUCROS_EPS = 1e-6    # squared velocity-gradient floor: below 1e-3 the flow counts as uniform
+
+
+def ducros(U, dU, ph):
+    """Ducros' sensor (Sec. 3.1.2 lists it beside the modal sensor):
+    (div u)^2 / ((div u)^2 + |curl u|^2 + eps) at each point, from the state U
+    and the gradient dU[..., j, v] of the conservative variables: 1 in a pure
+    compression or expansion, 0 in a rigid rotation or a shear layer."""
+    d = U.shape[-1] - 2
+    rho = U[..., 0]
+    vel = U[..., 1:1 + d] / rho[..., None]
+    # dv[..., j, k] = d u_k / d x_j
+    dv = (dU[..., 1:1 + d] - vel[..., None, :] * dU[..., :, 0:1]) / rho[..., None, None]
+    div = np.einsum("...jj->...", dv)
+    if d == 2:
+        curl2 = (dv[..., 0, 1] - dv[..., 1, 0]) ** 2
+    else:
+        curl2 = ((dv[..., 1, 2] - dv[..., 2, 1]) ** 2 + (dv[..., 2, 0] - dv[..., 0, 2]) ** 2
+                 + (dv[..., 0, 1] - dv[..., 1, 0]) ** 2)
+    return div * div / (div * div + curl2 + DUCROS_EPS)
+
+
 def viscous_flux(U, dU, ph, mu_av=None):
     """Diffusion flux G_i = (0, tau_i1..tau_id, u_j tau_ij - q_i) with the
     Stokes stress tau_ij = mu (du_i/dx_j + du_j/dx_i) - 2/3 mu div(u) delta_ij and

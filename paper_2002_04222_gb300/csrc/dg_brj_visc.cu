@@ -121,7 +121,10 @@ __global__ void __launch_bounds__(128) brj_visc_trace_kernel(
   const double cs = cg * ph.beta_s;
   double S0[DIM][NV], S1[DIM][NV], Qa[NV];
   // artificial viscosity held at the linearisation state's traces
-  const double mua = av_face<DIM>(ph, eL, eR, QL, QR);
+  // (the face-average gradient enters only with Ducros' sensor, which the
+  // build refuses together with these terms)
+  const double zgrad[DIM][DIM + 2] = {};
+  const double mua = av_face<DIM>(ph, eL, eR, QL, QR, zgrad);
   symmetric_flux<DIM>(QL, QR, bctype, x, t, n, ph, S0, Qa, mua);
   const bool adiabatic = bctype == DG_BC_ADIA_WALL;
   TJ* kl = Kd + (((long long)eL * 2 * DIM + fL) * NF + p) * NK;

@@ -337,7 +337,7 @@ dg_status dg_mesh_create(const dg_mesh_desc* md, const dg_physics* ph, void* str
   if (!supported(d, md->P, md->Q)) return DG_ERR_UNSUPPORTED;
   if (ph->n_bc < 0 || ph->n_bc > 8) return DG_ERR_ARG;
   if (ph->riemann < DG_RIEMANN_ROE || ph->riemann > DG_RIEMANN_AUSM) return DG_ERR_ARG;
-  if (ph->av != 0 && ph->av != 1) return DG_ERR_ARG;
+  if (ph->av < 0 || ph->av > 2) return DG_ERR_ARG;
   if (ph->av && (!ph->viscous || !(ph->av_mu0 >= 0.0) || !(ph->av_kappa > 0.0)))
     return DG_ERR_ARG;  // artificial viscosity enters through the diffusion flux
   cudaStream_t s = (cudaStream_t)stream;
@@ -455,6 +455,7 @@ dg_status dg_mesh_create(const dg_mesh_desc* md, const dg_physics* ph, void* str
     p.avf = m->avf;
     p.av_mu0 = ph->av_mu0;
     p.av_kappa = ph->av_kappa;
+    p.av_mode = ph->av;
     build_sensor_table(md->P, ph->av_kappa, m->tab, m->stab);
   }
   if (err != cudaSuccess) {

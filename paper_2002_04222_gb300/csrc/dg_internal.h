@@ -35,6 +35,7 @@ struct Phys {
   // passed to the residual (device, [E]; nullptr without shock capturing)
   double av_mu0, av_kappa;
   const double* avf;
+  int av_mode;  // 1: modal sensor; 2: modal sensor times Ducros' sensor at each point
 };
 
 // Modified-basis-to-Legendre transform of one direction for the modal sensor:

@@ -118,6 +118,39 @@ __device__ inline void viscous_flux(const T* U, const TG dU[D][D + 2], const Phy
 }
 
 // ------------------------------------------------------------ shock capturing
+// Ducros' sensor (div u)^2 / ((div u)^2 + |curl u|^2 + eps) from the velocity
+// gradient dv[j][k] = d u_k / d x_j (Sec. 3.1.2 lists it beside the modal
+// sensor; with av = 2 it multiplies the artificial viscosity at each point)
+constexpr double DUCROS_EPS = 1e-6;  // squared velocity-gradient floor (1e-3)
+template <int D>
+__device__ inline double ducros_ratio(const double dv[D][D]) {
+  double div = 0.0;
+#pragma unroll
+  for (int k = 0; k < D; ++k) div += dv[k][k];
+  double c2;
+  if constexpr (D == 2) {
+    const double w = dv[0][1] - dv[1][0];
+    c2 = w * w;
+  } else {
+    const double wx = dv[1][D - 1] - dv[D - 1][1], wy = dv[D - 1][0] - dv[0][D - 1];
+    const double wz = dv[0][1] - dv[1][0];
+    c2 = wx * wx + wy * wy + wz * wz;
+  }
+  return div * div / (div * div + c2 + DUCROS_EPS);
+}
+
+// the same from a state U and the gradient dU[j][v] of the conservative variables
+template <int D>
+__device__ inline double ducros(const double* U, const double dU[D][D + 2]) {
+  const double irho = 1.0 / U[0];
+  double dv[D][D];
+#pragma unroll
+  for (int j = 0; j < D; ++j)
+#pragma unroll
+    for (int k = 0; k < D; ++k) dv[j][k] = (dU[j][1 + k] - U[1 + k] * irho * dU[j][0]) * irho;
+  return ducros_ratio<D>(dv);
+}
+
 // Artificial viscosity at a point (Sec. 3.1.2): mu_av = f_e rho (c + |u|),
 // f_e = mu_0 S_e h_e / P the element factor of the modal sensor.
 template <int D>
@@ -134,14 +167,22 @@ __device__ inline double av_point(const double* U, const Phys& ph, double fe) {
 
 // Artificial viscosity on a face point: the mean of the two sides' values,
 // each from its own trace and element factor; the interior side's alone on a
-// boundary face (eR < 0).
+// boundary face (eR < 0); dQa is the face-average gradient (av = 2).
 template <int D>
 __device__ inline double av_face(const Phys& ph, int eL, int eR, const double* QL,
-                                 const double* QR) {
+                                 const double* QR, const double dQa[D][D + 2]) {
   if (!ph.avf) return 0.0;
-  const double a = av_point<D>(QL, ph, ph.avf[eL]);
-  if (eR < 0) return a;
-  return 0.5 * (a + av_point<D>(QR, ph, ph.avf[eR]));
+  double a = av_point<D>(QL, ph, ph.avf[eL]);
+  if (eR >= 0) a = 0.5 * (a + av_point<D>(QR, ph, ph.avf[eR]));
+  if (ph.av_mode == 2 && a != 0.0) {
+    // Ducros' sensor of the face-average gradient at the mean trace state
+    // (a boundary face: the interior trace)
+    double Qm[D + 2];
+#pragma unroll
+    for (int v = 0; v < D + 2; ++v) Qm[v] = eR >= 0 ? 0.5 * (QL[v] + QR[v]) : QL[v];
+    a *= ducros<D>(Qm, dQa);
+  }
+  return a;
 }
 
 // Normal Euler flux F(U).n
@@ -668,8 +709,6 @@ __device__ inline void ns_volume_flux(const double* U, const double dU[D][D + 2]
   if (!ph.viscous) return;
   const double temp = ph.gMa2 * p * irho;
   double mu = viscosity(temp, ph);
-  if (fe != 0.0) mu += fe * U[0] * (sqrt(ph.gamma * p * irho) + sqrt(ke * irho));
-  const double kap = mu * ph.kappa_fac;
   const double e = U[D + 1] * irho;
   double dvel[D][D], dT[D];
 #pragma unroll
@@ -685,6 +724,12 @@ __device__ inline void ns_volume_flux(const double* U, const double dU[D][D + 2]
   double div = 0.0;
 #pragma unroll
   for (int k = 0; k < D; ++k) div += dvel[k][k];
+  if (fe != 0.0) {
+    double a = fe * U[0] * (sqrt(ph.gamma * p * irho) + sqrt(ke * irho));
+    if (ph.av_mode == 2) a *= ducros_ratio<D>(dvel);
+    mu += a;
+  }
+  const double kap = mu * ph.kappa_fac;
   const double tt = (2.0 / 3.0) * mu * div;
 #pragma unroll
   for (int i = 0; i < D; ++i) {

@@ -118,7 +118,9 @@ __global__ void __launch_bounds__(256) brj_weights_kernel(const __grid_constant_
         }
       }
       // artificial viscosity held at the linearisation state (not differentiated)
-      const double mua = ph.avf ? av_point<DIM>(U, ph, ph.avf[e]) : 0.0;
+      const double mua = ph.avf ? av_point<DIM>(U, ph, ph.avf[e]) *
+                                     (ph.av_mode == 2 ? ducros<DIM>(U, dU) : 1.0)
+                             : 0.0;
       TW* Wq = W + (long long)el * NQ * NW + q;  // [(k NV + l) JA + ja][NQ]
       for (int l = 0; l < NV; ++l) {
         Dual Ud[NV];
@@ -199,7 +201,9 @@ __global__ void __launch_bounds__(256) brj_weights_kernel(const __grid_constant_
 #pragma unroll
       for (int r = 0; r < DIM; ++r) dU[r][v] = sG[(r * NV + v) * NQ + q] * rh[r];
     }
-    const double mua = ph.avf ? av_point<DIM>(U, ph, ph.avf[e]) : 0.0;
+    const double mua = ph.avf ? av_point<DIM>(U, ph, ph.avf[e]) *
+                                     (ph.av_mode == 2 ? ducros<DIM>(U, dU) : 1.0)
+                             : 0.0;
     TW* Wq = W + (long long)el * NQ * NW + q;  // [(k NV + l) JA + ja][NQ]
     for (int l = 0; l < NV; ++l) {
       Dual Ud[NV];
@@ -310,7 +314,7 @@ __global__ void __launch_bounds__(128) brj_tracejac_kernel(
   const double beta = (double)((P + 1) * (P + 1)) / hmin;
   double H0[NV], H1[NV], S[DIM][NV];
   // artificial viscosity held at the linearisation state's traces
-  const double mua = av_face<DIM>(ph, eL, eR, QL, QR);
+  const double mua = av_face<DIM>(ph, eL, eR, QL, QR, dQa);
   numerical_flux<DIM>(QL, QR, bctype, x, t, dQa, r, sgn, beta, ph, H0, S, mua);
   TJ* jdl = Jd + (((long long)eL * 2 * DIM + fL) * NF + p) * NV * NV;
   TJ* jol = Jo + ((long long)eL * 2 * DIM + fL) * NV * NV * NF + p;
@@ -393,7 +397,7 @@ __global__ void __launch_bounds__(128) brj_tracejac_gen_kernel(
     for (int v = 0; v < NV; ++v) QR[v] = 0.0;
   }
   double H0[NV], H1[NV], S[DIM][NV];
-  const double mua = av_face<DIM>(ph, eL, eR, QL, QR);
+  const double mua = av_face<DIM>(ph, eL, eR, QL, QR, dQa);
   numerical_flux_n<DIM>(QL, QR, bctype, x, t, dQa, n, beta, ph, H0, S, mua);
   TJ* jdl = Jd + (((long long)eL * 2 * DIM + fL) * NF + p) * NV * NV;
   TJ* jol = Jo + ((long long)eL * 2 * DIM + fL) * NV * NV * NF + p;
@@ -1467,7 +1471,9 @@ dg_status dg_precond_build(dg_mesh_t m, const double* u, double t, double dt_a,
   if (cfg->precision == DG_PREC_FP64 && m->curved && m->P > 2) return DG_ERR_UNSUPPORTED;
   // terms 4-5: viscous flows on axis-aligned elements, the two-kernel sweeps
   const int full = cfg->full_jacobian && m->phys.viscous;
-  if (full && (m->curved || cfg->fused || !visc_supported(d, m->P, m->Q))) return DG_ERR_UNSUPPORTED;
+  if (full && (m->curved || cfg->fused || !visc_supported(d, m->P, m->Q) ||
+               (m->phys.avf && m->phys.av_mode == 2)))
+    return DG_ERR_UNSUPPORTED;
   dg_precond_s* p = *inout;
   if (p && (p->mesh != m || p->precision != cfg->precision || p->full != full)) {
     free_precond(p);

@@ -424,7 +424,7 @@ __global__ void __launch_bounds__(128) face_kernel(const __grid_constant__ Table
   }
   double Hn[NV], S[DIM][NV];
   const double beta = (double)((P + 1) * (P + 1)) * 0.5 * rmax;  // (P+1)^2 / h
-  const double mua = av_face<DIM>(ph, eL, eR, QL, QR);
+  const double mua = av_face<DIM>(ph, eL, eR, QL, QR, dQa);
   if (r == 0)
     numerical_flux_axis<DIM, 0>(QL, QR, bctype, x, t, dQa, sgn, beta, ph, Hn, S, mua);
   else if (r == 1)
@@ -508,7 +508,7 @@ __global__ void __launch_bounds__(128) face_kernel_gen(const __grid_constant__ P
   }
   double Hn[NV], S[DIM][NV];
   numerical_flux_n<DIM>(QL, QR, bctype, x, t, dQa, n, gg.fbeta[f], ph, Hn, S,
-                        av_face<DIM>(ph, eL, eR, QL, QR));
+                        av_face<DIM>(ph, eL, eR, QL, QR, dQa));
   const double cs = ph.viscous ? cfac * ph.beta_s * wJf : 0.0;
 #pragma unroll
   for (int side = 0; side < 2; ++side) {

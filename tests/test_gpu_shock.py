@@ -26,7 +26,10 @@ values in the oracle); the residual is the method's residual plus the AV
 diffusion term dR, each held to the rule of the other residual parity tests,
 max(1e-12, 16 s) with s its own rounding floor at u (the oracle's relative
 change under a one-ulp perturbation of u), so that ||R_gpu - R_or|| <=
-max(1e-12, 16 s) ||R|| + max(1e-12, 16 s_av) ||dR||;
+max(1e-12, 16 s) ||R|| + max(1e-12, 16 s_av) ||dR||; with Ducros' sensor
+(av = 2) s_av also covers the rounding of the velocity gradients the ratio
+receives, at the level of the device's route to them (collocation derivative
+on the Gauss grid, then extrapolation to the faces);
 JFNK product by the residual difference at u + eps v over eps; BRJ apply
 1e-6 (FP64 blocks); SDIRK with equal Newton and GMRES counts and u^{n+1} to
 1e-9."""
@@ -115,6 +118,53 @@ STATES = {
     "bubble_wavy_P2_Q5_k0.5": lambda: bubble_state(w.wavy_box_case((2, 2, 2), P=2), 0.5, 1000.0),
 }
 PHYSICAL = sorted(k for k in STATES if not k.startswith("contact"))
+DUCROS = ["bubble_box_P3_k0.5", "bubble_vortex_P3_k0.5", "bubble_wavy_P2_Q5_k0.5", "shock50_P3"]
+
+
+def state(name, mode=1):
+    """A test state with the modal sensor alone (mode 1) or times Ducros'
+    sensor at each point (mode 2)."""
+    c, dg, u = STATES[name]()
+    c.phys.av = mode
+    return c, dg, u
+
+
+def tag(name, mode):
+    return name if mode == 1 else name + "_ducros"
+
+
+def gradient_rounding_gain(Q):
+    """Sum |l_k(1)| of the Lagrange extrapolation from the Q Gauss points to
+    the end point times the row-sum norm of the Gauss-point collocation
+    derivative: the factor by which the device's route to a face gradient
+    (collocation derivative, then extrapolation) can scale rounding."""
+    x, _ = np.polynomial.legendre.leggauss(Q)
+    lam = sum(abs(np.prod([(1.0 - x[j]) / (x[k] - x[j]) for j in range(Q) if j != k]))
+              for k in range(Q))
+    V = np.polynomial.legendre.legvander(x, Q - 1)
+    dV = np.stack([np.polynomial.legendre.legval(x, np.polynomial.legendre.legder(np.eye(Q)[k]))
+                   for k in range(Q)], 1)
+    return lam * np.abs(dV @ np.linalg.inv(V)).sum(axis=1).max()
+
+
+def ducros_floor(dg, u, R, dR, monkeypatch):
+    """Relative change of the AV term dR when the velocity gradients that
+    Ducros' ratio receives carry rounding at the level of the device's gradient
+    route (2^-52 x gradient_rounding_gain(Q) x the largest gradient entry of the
+    point): the ratio is non-linear in the gradient, so this rounding reaches R
+    through it and not only through the linear diffusion flux."""
+    gain = gradient_rounding_gain(dg.Q)
+    orig = phy.ducros
+    rng = np.random.default_rng(7)
+    out = 0.0
+    for _ in range(3):
+        def perturbed(U, dU, ph):
+            scale = np.abs(dU).max(axis=(-2, -1), keepdims=True)
+            return orig(U, dU + 2.0 ** -52 * gain * scale * rng.standard_normal(dU.shape), ph)
+        monkeypatch.setattr(phy, "ducros", perturbed)
+        out = max(out, np.linalg.norm(dg.residual(u) - R) / np.linalg.norm(dR))
+        monkeypatch.setattr(phy, "ducros", orig)
+    return out
 
 
 @pytest.mark.parametrize("beta,smooth", [(30.8, False), (50.0, False), (30.8, True)])
@@ -156,9 +206,9 @@ def test_sensor_factor_parity(dgl, name, parity_record):
         assert np.allclose(got[S == 1], c.phys.av_mu0 * h[S == 1] / c.P, rtol=1e-14)
 
 
-@pytest.mark.parametrize("name", PHYSICAL)
-def test_residual_parity_with_artificial_viscosity(dgl, name, parity_record):
-    c, dg, u = STATES[name]()
+@pytest.mark.parametrize("name,mode", [(n, 1) for n in PHYSICAL] + [(n, 2) for n in DUCROS])
+def test_residual_parity_with_artificial_viscosity(dgl, name, mode, parity_record, monkeypatch):
+    c, dg, u = state(name, mode)
     m = dgl.Mesh.from_case(c)
     R_ref = dg.residual(u, 0.0)
     R = m.residual(to_dev(u)).cpu().numpy()
@@ -174,21 +224,25 @@ def test_residual_parity_with_artificial_viscosity(dgl, name, parity_record):
         Rp, R0p = dg.residual(up), dg0.residual(up)
         s = max(s, rel(Rp, R_ref))
         s_av = max(s_av, rel(Rp - R0p, dR))
+    # with Ducros' sensor the AV term's floor also carries the gradient rounding
+    # the ratio amplifies
+    s_grad = ducros_floor(dg, u, R_ref, dR, monkeypatch) if mode == 2 else 0.0
     # R is the method's residual plus the AV diffusion term; each operator is
     # held to the residual rule max(1e-12, 16 s) with its own floor, and the
     # bound on R is the sum of the two parts' bounds
     tol = (max(R_TOL, 16.0 * s) * np.linalg.norm(R_ref)
-           + max(R_TOL, 16.0 * s_av) * np.linalg.norm(dR)) / np.linalg.norm(R_ref)
-    parity_record("residual_av", name, "||R_gpu-R_or||/||R_or||", rel(R, R_ref), tol, floor_s=s,
-                  floor_s_av=s_av, av_effect=rel(R_plain, R_ref))
+           + max(R_TOL, 16.0 * max(s_av, s_grad)) * np.linalg.norm(dR)) / np.linalg.norm(R_ref)
+    parity_record("residual_av", tag(name, mode), "||R_gpu-R_or||/||R_or||", rel(R, R_ref), tol, floor_s=s,
+                  floor_s_av=s_av, floor_s_grad=s_grad, av_effect=rel(R_plain, R_ref))
     assert rel(R_plain, R_ref) > 1e-6          # the test is not vacuous
     assert s < 1e-10 and s_av < 1e-10          # floors of FP64 evaluations
     assert rel(R, R_ref) < tol, (rel(R, R_ref), tol)
 
 
+@pytest.mark.parametrize("mode", [1, 2])
 @pytest.mark.parametrize("name", ["bubble_vortex_P3_k0.5", "bubble_box_P3_k0.5", "shock50_P3"])
-def test_jvp_parity_with_artificial_viscosity(dgl, name, parity_record):
-    c, dg, u = STATES[name]()
+def test_jvp_parity_with_artificial_viscosity(dgl, name, mode, parity_record):
+    c, dg, u = state(name, mode)
     m = dgl.Mesh.from_case(c)
     v = w.random_direction(u, 7)
     R = dg.residual(u)
@@ -200,16 +254,18 @@ def test_jvp_parity_with_artificial_viscosity(dgl, name, parity_record):
         ref = im.jvp(dg, u, R, 0.0, v, alpha, beta)
         got = m.jvp(ud, Rd, vd, 0.0, alpha, beta).cpu().numpy()
         bound = max(JVP_TOL, 4 * abs(beta) * dR / eps / np.linalg.norm(ref))
-        parity_record("jvp_av", f"{name}_alpha{alpha:g}", "||Jv_gpu-Jv_or||/||Jv_or||",
+        parity_record("jvp_av", f"{tag(name, mode)}_alpha{alpha:g}", "||Jv_gpu-Jv_or||/||Jv_or||",
                       rel(got, ref), bound)
         assert rel(got, ref) < bound, (rel(got, ref), bound)
 
 
-@pytest.mark.parametrize("name,full", [("bubble_vortex_P3_k0.5", False), ("shock50_P3", False),
-                                       ("bubble_box_P3_k0.5", False),
-                                       ("bubble_vortex_P2_k0.25", True)])
-def test_brj_apply_parity_with_frozen_artificial_viscosity(dgl, name, full, parity_record):
-    c, dg, u = STATES[name]()
+@pytest.mark.parametrize("name,full,mode", [("bubble_vortex_P3_k0.5", False, 1), ("shock50_P3", False, 1),
+                                            ("bubble_box_P3_k0.5", False, 1),
+                                            ("bubble_vortex_P2_k0.25", True, 1),
+                                            ("bubble_vortex_P3_k0.5", False, 2),
+                                            ("bubble_box_P3_k0.5", False, 2), ("shock50_P3", False, 2)])
+def test_brj_apply_parity_with_frozen_artificial_viscosity(dgl, name, full, mode, parity_record):
+    c, dg, u = state(name, mode)
     m = dgl.Mesh.from_case(c)
     dt_a = 0.002
     q = w.random_direction(u, 3)
@@ -220,7 +276,7 @@ def test_brj_apply_parity_with_frozen_artificial_viscosity(dgl, name, full, pari
     ph0 = copy.copy(c.phys)
     ph0.av = 0
     plain = im.BRJ(DG(c.mesh, c.P, c.Q, ph0), u, 0.0, dt_a, J=7, full=full).apply(q)
-    parity_record("brj_apply_av", f"{name}{'_full' if full else ''}",
+    parity_record("brj_apply_av", f"{tag(name, mode)}{'_full' if full else ''}",
                   "||P^-1q_gpu-P^-1q_or||/||P^-1q_or||", rel(got, ref), 1e-6,
                   av_effect=rel(plain, ref))
     assert rel(plain, ref) > 1e-5                   # mu_av is in the blocks
@@ -273,4 +329,15 @@ def test_shock_capturing_needs_the_diffusion_flux(dgl):
     m = dgl.Mesh.from_case(c)
     with pytest.raises(_lib.DGError) as ei:
         m.av_factor(m.project(0.0))
+    assert ei.value.code == -6
+
+
+def test_ducros_option_refuses_the_trace_gradient_terms(dgl):
+    """Terms 4-5 (full_jacobian) are not built with Ducros' sensor: the build
+    says so instead of holding a viscosity it cannot form."""
+    from paper_2002_04222_gb300 import _lib
+    c, dg, u = state("bubble_vortex_P2_k0.25", 2)
+    m = dgl.Mesh.from_case(c)
+    with pytest.raises(_lib.DGError) as ei:
+        dgl.Precond(m).build(to_dev(u), 0.0, 0.002, J=7, full_jacobian=True)
     assert ei.value.code == -6

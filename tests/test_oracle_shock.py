@@ -168,3 +168,89 @@ def test_shock_capturing_conserves_on_a_periodic_mesh():
     assert np.all(np.abs(tot) < 1e-11 * np.abs(L).sum(axis=(0, 2)))
     c.phys.av = 0
     assert not np.allclose(dg.rhs(u), L)
+
+
+def _state_and_gradient(vel, grad_vel, rho=1.3, drho=None, p=5.0, d=2):
+    """Conservative U and its gradient dU[j][v] at one point from the velocity,
+    its gradient grad_vel[j][k] = d u_k / d x_j and the density gradient."""
+    ph = w.Physics(Ma=0.3)
+    vel = np.asarray(vel, float)
+    G = np.asarray(grad_vel, float)
+    drho = np.zeros(d) if drho is None else np.asarray(drho, float)
+    U = phy.conservative(np.array([rho]), vel[None], np.array([p]), ph)[0]
+    dU = np.zeros((d, d + 2))
+    dU[:, 0] = drho
+    dU[:, 1:1 + d] = rho * G + np.outer(drho, vel)        # d(rho u_k)/dx_j
+    return ph, U, dU
+
+
+def test_ducros_sensor_limits_and_invariance():
+    """(div u)^2 / ((div u)^2 + |curl u|^2 + eps): 1 for a pure compression (up
+    to eps), 0 for a rigid rotation, 1/2 where (div u)^2 = |curl u|^2 (up to
+    eps); the velocity gradient alone counts (a density gradient changes
+    nothing); 3-D: each curl component counts (u = (0, 0, y) is a shear: 0);
+    gradients far below the floor sqrt(eps) count as uniform flow (0)."""
+    eps = phy.DUCROS_EPS
+    ph, U, dU = _state_and_gradient([0.4, -0.2], [[-1.0, 0.0], [0.0, -1.0]])
+    assert abs(phy.ducros(U, dU, ph) - 4.0 / (4.0 + eps)) < 1e-15
+    ph, U, dU = _state_and_gradient([0.4, -0.2], [[0.0, 1.0], [-1.0, 0.0]])
+    assert phy.ducros(U, dU, ph) == 0.0
+    # u = (-x - y, x - y): div = -2, curl = 2
+    ph, U, dU = _state_and_gradient([0.1, 0.7], [[-1.0, 1.0], [-1.0, -1.0]], drho=[0.3, -0.8])
+    assert abs(phy.ducros(U, dU, ph) - 4.0 / (8.0 + eps)) < 1e-15
+    ph, U2, dU2 = _state_and_gradient([0.1 * 7, 0.7 * 7], [[-7.0, 7.0], [-7.0, -7.0]])
+    assert abs(phy.ducros(U2, dU2, ph) - 196.0 / (392.0 + eps)) < 1e-15
+    ph, U, dU = _state_and_gradient([0.0, 0.0, 0.3], [[0, 0, 0], [0, 0, 1.0], [0, 0, 0]], d=3)
+    assert phy.ducros(U, dU, ph) == 0.0
+    ph, U, dU = _state_and_gradient([0.0, 0.0, 0.3], [[2.0, 0, 0], [0, 0, 1.0], [0, 0, 0]], d=3)
+    assert abs(phy.ducros(U, dU, ph) - 4.0 / (5.0 + eps)) < 1e-15     # div^2 = 4, curl^2 = 1
+    ph, U, dU = _state_and_gradient([0.4, -0.2], [[-1e-9, 0.0], [0.0, -1e-9]])
+    assert phy.ducros(U, dU, ph) < 1e-11
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        ph, U, dU = _state_and_gradient(rng.standard_normal(3), rng.standard_normal((3, 3)),
+                                        drho=rng.standard_normal(3), d=3)
+        assert 0.0 <= phy.ducros(U, dU, ph) <= 1.0
+
+
+def test_ducros_option_scales_the_artificial_viscosity_and_conserves():
+    """av = 2 multiplies the modal sensor's viscosity by Ducros' sensor at each
+    point.  A density jump (modal sensor active) carried by a compressing
+    stream u = (1 - x/2, 0.3) (no curl: Ducros 1) gives the residual of av = 1;
+    carried by a rotating stream u = (1 - y/2, 0.3 + x/2) (no divergence:
+    Ducros 0) the residual without artificial viscosity; on the uniform stream
+    too (its gradients are below the floor); and the residual stays
+    conservative on the periodic mesh with the option acting."""
+    c, dg = sensor_case(P=3, n=4)
+
+    def field(velf):
+        return lambda x: phy.conservative(np.where(x[..., 0] < 0.4, 1.0, 0.6), velf(x),
+                                          1.0 / (1.4 * 0.01) + 0 * x[..., 0], c.phys)
+
+    def residuals(u):
+        out = []
+        for av in (0, 1, 2):
+            c.phys.av = av
+            out.append(dg.rhs(u))
+        return out
+
+    n = np.linalg.norm
+    u = dg.project(field(lambda x: np.stack([1.0 - 0.5 * x[..., 0], 0.3 + 0 * x[..., 0]], -1)))
+    assert dg.sensor(u).max() > 0.0
+    L0, L1, L2 = residuals(u)
+    assert n(L1 - L0) > 1e-6 * n(L1)
+    assert n(L2 - L1) < 1e-5 * n(L1 - L0)     # div^2 = 1/4: Ducros = 1 - 4 eps
+    u = dg.project(field(lambda x: np.stack([1.0 - 0.5 * x[..., 1], 0.3 + 0.5 * x[..., 0]], -1)))
+    L0, L1, L2 = residuals(u)
+    assert n(L2 - L0) < 1e-12 * n(L1 - L0)
+    # a uniform stream: the projection leaves velocity gradients far below the
+    # floor, so the flow counts as uniform and no viscosity is added
+    u = dg.project(field(lambda x: np.stack([1.0 + 0 * x[..., 0], 0.3 + 0 * x[..., 0]], -1)))
+    L0, L1, L2 = residuals(u)
+    assert n(L2 - L0) < 1e-12 * n(L1 - L0)
+    # conservation with the option on, where it acts
+    u = dg.project(field(lambda x: np.stack([1.0 - 0.5 * x[..., 0], 0.3 + 0.2 * x[..., 1]], -1)))
+    L0, L1, L2 = residuals(u)
+    assert n(L2 - L0) > 1e-6 * n(L2)
+    tot = dg.integral(L2)
+    assert np.all(np.abs(tot) < 1e-11 * np.abs(L2).sum(axis=(0, 2)))

@@ -51,7 +51,7 @@ class Physics:
     # Poiseuille: theta, L, dpdx; uniform: rho, u, v, w, T)
     fpar: tuple = ()
     bc: list = dc_field(default_factory=list)   # bc[id] = type
-    av: int = 0                # shock capturing: artificial viscosity from the modal sensor
+    av: int = 0                # shock capturing: 1 modal sensor, 2 modal sensor x Ducros
     av_mu0: float = 0.25       # mu_0 of Sec. 3.1.2
     av_kappa: float = 1.0      # half-width of the sensor's ramp (decades)
 
