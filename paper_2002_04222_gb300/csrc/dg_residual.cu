@@ -833,7 +833,10 @@ static void tune_candidates(std::vector<int2>& vol, std::vector<int2>& lift) {
   using C = Cfg<DIM, P, Q>;
   const int epbs3[] = {1, 2, 3, 4};
   const int epbs2[] = {1, 2, 4, 8, 16, 32};
-  const int nts[] = {64, 128, 192, 256};
+  // every warp multiple up to the kernels' bound: a count just above the
+  // Gauss points of one or more elements (224 for 216 at Q = 6) gives the
+  // per-point flux stage one pass without idle lanes
+  const int nts[] = {64, 96, 128, 160, 192, 224, 256};
   const size_t cap = 200 * 1024;
   for (int e : (DIM == 3 ? std::vector<int>(epbs3, epbs3 + 4) : std::vector<int>(epbs2, epbs2 + 6)))
     for (int t : nts) {
