@@ -234,9 +234,12 @@ typedef struct {
  * (Sec. 4.2.2, Eq. Jacobian-matrix-form/-form2, numerical-Jac-on-traces):
  * element-volume Jacobians from the exact flux derivatives, trace flux
  * Jacobians by one-sided differences with chi_k = sqrt(2^-52)*||u_k||_2,
- * the trace-gradient and symmetric-flux terms neglected; the diagonal
- * blocks are inverted and stored, the trace Jacobians kept for the
- * off-diagonal product. */
+ * the trace-gradient and symmetric-flux terms neglected (kept with
+ * cfg->full_jacobian); the diagonal blocks are inverted in place (Gauss-
+ * Jordan with partial pivoting, in the blocks' precision; BF16 blocks are
+ * inverted in FP32 and rounded) and stored, the trace Jacobians kept for the
+ * off-diagonal product.  Returns DG_ERR_NONFINITE when the elimination of
+ * a block finds no non-zero pivot (a singular block). */
 dg_status dg_precond_build(dg_mesh_t m, const double* u, double t, double dt_a,
                            const dg_prec_cfg* cfg, dg_precond_t* inout, void* stream);
 /* FP64 blocks need 2 nm^2 doubles of shared memory per CTA (up to P = 3 in
